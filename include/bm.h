@@ -1,0 +1,196 @@
+/*
+ * bm.h - C ABI of the GB300 direct-indirect Burton-Miller solver for 2-D Helmholtz
+ * transmission problems (Matsumoto & Matsushima, "Efficient LU factorization exploiting
+ * direct-indirect Burton-Miller equation for Helmholtz transmission problems").
+ *
+ * The library assembles the Nystrom discretisation of either boundary integral system,
+ * factors it and solves it on one GPU (sm_103a):
+ *
+ *  - the 3N x 3N direct-indirect ("mixed") system of Eq. dis_mixedBM (section 4), stored as
+ *    its four dense blocks M13, M23, M31, M32 of Theorem thm:LU (section 4.1) - the two
+ *    identity and three zero blocks are never materialised;
+ *  - the 2N x 2N ordinary Burton-Miller system of Eq. dis_BM (section 4), the comparison.
+ *
+ * Factorisation of the mixed system follows Theorem thm:LU: U33 = -M31 M13 - M32 M23, then a
+ * dense complex LU with partial pivoting of U33.  Solves with arbitrary 3N right-hand sides
+ * follow Corollary lem:for_ssm_RHS.
+ *
+ * Conventions shared by every entry point:
+ *  - Complex numbers are bm_c64 (interleaved re, im; FP64).  Right-hand sides and solutions
+ *    are column-major with leading dimension >= the system size (3N mixed, 2N ordinary).
+ *    Mixed unknowns are ordered (u, q, phi), ordinary ones (u, q).
+ *  - Pointers flagged "on_device" are device pointers on the handle's device (for example
+ *    torch data_ptr()); otherwise they are host pointers and the call copies through them.
+ *  - The handle owns every device buffer it allocates (blocks, factors, pivots, workspace);
+ *    the caller owns B, X, angles and outputs.  All work is enqueued on the handle's stream
+ *    and calls return after the stream has finished the work they enqueued.
+ *  - A handle is not thread-safe: use one handle per host thread.
+ *  - Every function returns BM_OK (0) or an error code; bm_strerror names it and
+ *    bm_last_error returns a message with the details of the most recent failure.
+ */
+#ifndef BM_H
+#define BM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BM_OK = 0,
+    BM_EINVAL = 1,      /* invalid argument (size, pointer, leading dimension, enum value) */
+    BM_ENOMEM = 2,      /* request exceeds the handle's HBM budget, or a device allocation failed */
+    BM_ESINGULAR = 3,   /* exactly zero pivot; *info holds the 1-based column (LAPACK style) */
+    BM_ENOTCONV = 4,    /* iterative refinement did not reach refine_tol within refine_maxit */
+    BM_ENONFINITE = 5,  /* NaN or Inf in an input (right-hand side, wavenumber, curve data) */
+    BM_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+    BM_ESTATE = 7,      /* call order violated (solve before factor, factor before assemble) */
+    BM_ECUDA = 8        /* a CUDA runtime call failed; bm_last_error has its message */
+} bm_status;
+
+typedef enum { BM_MIXED = 0, BM_ORDINARY = 1 } bm_formulation;
+
+/* Arithmetic of the factorisation.
+ *  BM_FP64          : FP64 throughout (assembly, Schur GEMM, LU, solve).
+ *  BM_CF32_TF32_IR  : FP64 assembly; Schur GEMM and LU trailing updates in complex TF32 on the
+ *                     tensor cores (FP32 accumulation), panels and triangular solves in FP32;
+ *                     FP64 residuals and iterative refinement to refine_tol (backward error).
+ *  BM_CF32_3XTF32_IR: as above with each tensor-core product split hi/lo (3 TF32 products,
+ *                     about FP32 accuracy), which needs fewer refinement steps. */
+typedef enum { BM_FP64 = 0, BM_CF32_TF32_IR = 1, BM_CF32_3XTF32_IR = 2 } bm_precision;
+
+typedef struct { double re, im; } bm_c64;
+
+/* Curves, parametrised counter-clockwise over t in [0, 2 pi) (the normal nu = (y', -x')/|x'|
+ * then points into the exterior domain, section 2.1):
+ *  BM_CURVE_CIRCLE : p = {R, cx, cy, -}      x = (cx + R cos t, cy + R sin t)
+ *  BM_CURVE_ELLIPSE: p = {a, b, -, -}        x = (a cos t, b sin t)
+ *  BM_CURVE_STAR   : p = {r0, amp, lobes, -} x = (r0 + amp cos(lobes t)) (cos t, sin t)
+ *  BM_CURVE_KITE   : p = {c, b, -, -}        x = (cos t + c cos 2t - c, b sin t)
+ *  BM_CURVE_USER   : user = host array of 6N doubles, node-major
+ *                    {x, y, x', y', x'', y''} at t_j = 2 pi j / N. */
+typedef enum {
+    BM_CURVE_CIRCLE = 0, BM_CURVE_ELLIPSE = 1, BM_CURVE_STAR = 2, BM_CURVE_KITE = 3, BM_CURVE_USER = 4
+} bm_curve_kind;
+
+typedef struct {
+    int kind;
+    double p[4];
+    const double* user;
+} bm_curve;
+
+/* Options; pass NULL for the defaults.
+ *  eps0          : exterior material constant (default 1).
+ *  eps1, eps_set : interior material constant; if eps_set == 0 it is eps0 (k_in/k_out)^2,
+ *                  from k_i = omega sqrt(eps_i) (section 2.1) with omega = k_out / sqrt(eps0).
+ *  beta, beta_set: Burton-Miller constant (needs Im beta != 0, section 3.1); default i / k_out.
+ *  prec          : bm_precision (default BM_FP64).
+ *  refine_tol    : backward-error target of refinement (default 1e-9).
+ *  refine_maxit  : refinement iteration cap (default 30).
+ *  nb            : outer LU block size, a multiple of 32 in [32, 512] (0 = library default). */
+typedef struct {
+    double eps0;
+    bm_c64 eps1;
+    bm_c64 beta;
+    int eps_set;
+    int beta_set;
+    int prec;
+    double refine_tol;
+    int refine_maxit;
+    int nb;
+} bm_opts;
+
+/* Per-solve report.  Times are device times (CUDA events) of the solve's phases. */
+typedef struct {
+    int iterations;          /* refinement corrections applied (0 for BM_FP64) */
+    double backward_error;   /* max over columns of ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf),
+                                A the FP64 assembled system; computed on the device in FP64 */
+    double t_solve_ms;       /* whole bm_solve device time, including refinement */
+    double t_residual_ms;    /* part of it spent in FP64 residuals */
+} bm_solve_info;
+
+typedef struct bm_ctx bm_ctx;
+
+/* Create a handle on CUDA device `device`.  cuda_stream (a cudaStream_t, may be NULL) is the
+ * stream all work is enqueued on; NULL makes the handle create and own a non-blocking stream.
+ * hbm_budget_bytes bounds the device memory the handle may hold (0 = 90 % of free memory at
+ * creation).  The Hankel anchor table (about 0.4 MB) is built on first use and uploaded. */
+bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size_t hbm_budget_bytes);
+
+/* Assemble the Nystrom system (section 4, Eq. dis_mixedBM or Eq. dis_BM) for N nodes on the
+ * curve, exterior/interior wavenumbers k_out = k0, k_in = k1 (complex; the principal branch is
+ * used, Re k > 0 required).  Kernels of section 2.2 off the diagonal; the one-point
+ * zeta-corrected diagonal of section 4 on it.  The right-hand side of a plane wave is made by
+ * bm_rhs_plane_wave.  Replaces any previous system and factorisation of the handle.
+ * Errors: BM_EINVAL (N < 8, N > 65536, bad kind/params, Re k <= 0, |arg k| > 60 degrees),
+ * BM_ENONFINITE, BM_ENOMEM (admission: the bytes the system and its factorisation need
+ * exceed the budget; nothing is allocated then). */
+bm_status bm_assemble(bm_ctx* ctx, const bm_curve* curve, int N, bm_c64 k_out, bm_c64 k_in,
+                      bm_formulation formulation, const bm_opts* opts);
+
+/* Factor the assembled system.  Mixed: U33 = -M31 M13 - M32 M23 (Theorem thm:LU), then
+ * P U33 = L U with partial pivoting (pivot = first index of max |Re|+|Im|).  Ordinary: P A = L U
+ * of the 2N matrix.  The assembled FP64 operator is kept for residuals.
+ * *info (may be NULL) is 0, or the 1-based column of the first exactly zero pivot, in which
+ * case BM_ESINGULAR is returned and bm_solve refuses to run.  Errors: BM_ESTATE. */
+bm_status bm_factor(bm_ctx* ctx, int* info);
+
+/* Right-hand sides of plane waves exp(i k0 (cos a, sin a).x) for nrhs incidence angles
+ * (host array, radians): b3 = -u_in - beta du_in/dnu placed as (0, 0, b3) for the mixed
+ * system (Theorem thm:LU) or (b3, 0) for the ordinary one (Eq. dis_BM).  B has ldb >= the
+ * system size. */
+bm_status bm_rhs_plane_wave(bm_ctx* ctx, const double* angles, int nrhs, bm_c64* B, int ldb,
+                            int on_device);
+
+/* Solve A X = B for nrhs right-hand sides (any 3N or 2N data; Corollary lem:for_ssm_RHS for
+ * the mixed system).  FP64: one factored solve.  CF32 precisions: x0 from the FP32 factors,
+ * then x += A^{-1}_{fp32} (b - A x) with the residual in FP64 until the backward error (as in
+ * bm_solve_info) is <= refine_tol; BM_ENOTCONV if refine_maxit corrections do not get there
+ * (X then holds the last iterate).  X may not alias B.  info may be NULL.
+ * Errors: BM_ESTATE (not factored or singular), BM_EINVAL, BM_ENONFINITE (B not finite). */
+bm_status bm_solve(bm_ctx* ctx, int nrhs, const bm_c64* B, int ldb, bm_c64* X, int ldx,
+                   int on_device, bm_solve_info* info);
+
+/* Far-field pattern of solutions X (nrhs columns, as returned by bm_solve) at M observation
+ * angles: u_inf(xhat) = e^{i pi/4}/sqrt(8 pi k0) sum_j w_j [-i k0 (xhat.nu_j) u_j - eps0 q_j]
+ * exp(-i k0 xhat.x_j), from the exterior Green representation of the total field
+ * (section 3.1), normalised so that u_sc ~ e^{i k0 r} r^{-1/2} u_inf.  Uinf is M x nrhs,
+ * column-major, ldu >= M.  angles is a host array. */
+bm_status bm_far_field(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const double* angles,
+                       int M, bm_c64* Uinf, int ldu, int on_device);
+
+/* Copy one assembled FP64 block to dst (column-major, ldd >= rows).
+ * Mixed: which = 0..3 selects M13, M23, M31, M32 (N x N).
+ * Ordinary: which = 0 selects the whole 2N x 2N matrix. */
+bm_status bm_copy_block(bm_ctx* ctx, int which, bm_c64* dst, int ldd, int on_device);
+
+/* Evaluate the device special functions H0^(1)(z), H1^(1)(z) used by assembly at n points
+ * (section 2.2 kernels; principal branch, Re z > 0).  All arrays are device arrays when
+ * on_device, else host arrays. */
+bm_status bm_hankel01(bm_ctx* ctx, const bm_c64* z, int n, bm_c64* h0, bm_c64* h1, int on_device);
+
+/* Host copy of the anchor table the device Taylor zone of bm_hankel01 expands from:
+ * H0^(1)(z0), H1^(1)(z0) at z0 = re0 + ix*step + i (im0 + iy*step), stored as
+ * out[4*(iy*nx + ix) + {0,1,2,3}] = {Re H0, Im H0, Re H1, Im H1}; anchors outside the annulus
+ * 2.5 <= |z0| <= 21 are zero.  Built once per process on the host (no GPU needed); out may be
+ * NULL to query the sizes, else it must hold cap_anchors >= nx*ny anchors. */
+bm_status bm_hankel_anchor_table(double* out, int cap_anchors, int* nx, int* ny, double* re0, double* im0,
+                                 double* step);
+
+/* Device bytes the handle currently holds, and its budget. */
+bm_status bm_memory(bm_ctx* ctx, size_t* held_bytes, size_t* budget_bytes);
+
+/* Release every device buffer and the handle (the stream too, if the handle created it). */
+bm_status bm_destroy(bm_ctx* ctx);
+
+const char* bm_strerror(bm_status s);
+
+/* Details of the most recent failure on this host thread (empty string if none). */
+const char* bm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BM_H */

@@ -1,0 +1,247 @@
+"""Python binding of the C ABI in include/bm.h (ctypes; argument marshalling only).
+
+Every function has the name of its C entry point and forwards to libbm.so; all computation
+happens in the library's CUDA kernels.  There is no fallback: if libbm.so is missing or a call
+fails, a BMError is raised.
+
+Arrays: complex matrices are column-major complex128.  Host arrays are numpy arrays
+(Fortran order); device arrays are torch complex128 CUDA tensors whose first dimension is
+contiguous (``t.stride(0) == 1``), e.g. ``torch.empty((ncols, rows), dtype=torch.complex128,
+device='cuda').t()``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbm.so")
+
+BM_OK, BM_EINVAL, BM_ENOMEM, BM_ESINGULAR, BM_ENOTCONV, BM_ENONFINITE, BM_ETIMEOUT, BM_ESTATE, BM_ECUDA = range(9)
+BM_MIXED, BM_ORDINARY = 0, 1
+BM_FP64, BM_CF32_TF32_IR, BM_CF32_3XTF32_IR = 0, 1, 2
+BM_CURVE_CIRCLE, BM_CURVE_ELLIPSE, BM_CURVE_STAR, BM_CURVE_KITE, BM_CURVE_USER = range(5)
+
+
+class bm_c64(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class bm_curve(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 4), ("user", C.POINTER(C.c_double))]
+
+
+class bm_opts(C.Structure):
+    _fields_ = [("eps0", C.c_double), ("eps1", bm_c64), ("beta", bm_c64), ("eps_set", C.c_int),
+                ("beta_set", C.c_int), ("prec", C.c_int), ("refine_tol", C.c_double), ("refine_maxit", C.c_int),
+                ("nb", C.c_int)]
+
+
+class bm_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("backward_error", C.c_double), ("t_solve_ms", C.c_double),
+                ("t_residual_ms", C.c_double)]
+
+
+class BMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        L = lib()
+        super().__init__(f"{where}: {L.bm_strerror(status).decode()} ({L.bm_last_error().decode()})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libbm.so (built in-tree by paper_2512_14193_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run paper_2512_14193_gb300.build.build() first")
+    L = C.CDLL(LIB_PATH)
+    P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    L.bm_create.argtypes = [C.POINTER(P), I, P, S]
+    L.bm_assemble.argtypes = [P, C.POINTER(bm_curve), I, bm_c64, bm_c64, I, C.POINTER(bm_opts)]
+    L.bm_factor.argtypes = [P, C.POINTER(I)]
+    L.bm_rhs_plane_wave.argtypes = [P, C.POINTER(D), I, P, I, I]
+    L.bm_solve.argtypes = [P, I, P, I, P, I, I, C.POINTER(bm_solve_info)]
+    L.bm_far_field.argtypes = [P, P, I, I, C.POINTER(D), I, P, I, I]
+    L.bm_copy_block.argtypes = [P, I, P, I, I]
+    L.bm_hankel01.argtypes = [P, P, I, P, P, I]
+    L.bm_hankel_anchor_table.argtypes = [C.POINTER(D), I, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(D),
+                                         C.POINTER(D)]
+    L.bm_memory.argtypes = [P, C.POINTER(S), C.POINTER(S)]
+    L.bm_destroy.argtypes = [P]
+    L.bm_strerror.argtypes = [I]
+    L.bm_strerror.restype = C.c_char_p
+    L.bm_last_error.argtypes = []
+    L.bm_last_error.restype = C.c_char_p
+    for name in ("bm_create", "bm_assemble", "bm_factor", "bm_rhs_plane_wave", "bm_solve", "bm_far_field",
+                 "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_memory", "bm_destroy"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str, ok=(BM_OK,)):
+    if st not in ok:
+        raise BMError(st, where)
+    return st
+
+
+def _c64(z) -> bm_c64:
+    z = complex(z)
+    return bm_c64(z.real, z.imag)
+
+
+# --------------------------------------------------------------------------------------------
+# array marshalling: (pointer, leading dimension, ncols, on_device)
+# --------------------------------------------------------------------------------------------
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _colmajor(a, rows_min: int, writable: bool):
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.complex128 or not a.is_cuda:
+            raise TypeError("device arrays must be torch complex128 CUDA tensors")
+        if a.dim() == 1:
+            a = a.unsqueeze(1)
+        if a.stride(0) != 1:
+            raise ValueError("device arrays must be column-major (stride(0) == 1)")
+        ld = a.stride(1) if a.shape[1] > 1 else max(a.shape[0], 1)
+        torch.cuda.current_stream(a.device).synchronize()
+        return C.c_void_p(a.data_ptr()), int(ld), int(a.shape[1]), 1, a
+    arr = np.asarray(a)
+    if arr.ndim == 1:
+        arr = arr.reshape(-1, 1, order="F")
+    if arr.dtype != np.complex128 or not arr.flags.f_contiguous:
+        if writable:
+            raise ValueError("host output arrays must be Fortran-ordered complex128")
+        arr = np.asfortranarray(arr, dtype=np.complex128)
+    return C.c_void_p(arr.ctypes.data), int(arr.shape[0]), int(arr.shape[1]), 0, arr
+
+
+# --------------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# --------------------------------------------------------------------------------------------
+def bm_create(device: int = 0, stream: int | None = None, budget_bytes: int = 0):
+    h = C.c_void_p()
+    _check(lib().bm_create(C.byref(h), int(device), C.c_void_p(stream or 0), int(budget_bytes)), "bm_create")
+    return h
+
+
+def bm_destroy(h) -> None:
+    _check(lib().bm_destroy(h), "bm_destroy")
+
+
+def make_opts(prec: int = BM_FP64, eps0: float = 1.0, eps1=None, beta=None, refine_tol: float = 1e-9,
+              refine_maxit: int = 30, nb: int = 0) -> bm_opts:
+    o = bm_opts()
+    o.eps0 = float(eps0)
+    o.prec = int(prec)
+    o.refine_tol = float(refine_tol)
+    o.refine_maxit = int(refine_maxit)
+    o.nb = int(nb)
+    if eps1 is not None:
+        o.eps1 = _c64(eps1)
+        o.eps_set = 1
+    if beta is not None:
+        o.beta = _c64(beta)
+        o.beta_set = 1
+    return o
+
+
+def bm_assemble(h, kind: int, params, N: int, k_out, k_in, formulation: int = BM_MIXED, opts: bm_opts | None = None,
+                user: np.ndarray | None = None) -> None:
+    cv = bm_curve()
+    cv.kind = int(kind)
+    p = list(params) + [0.0] * (4 - len(params))
+    for i in range(4):
+        cv.p[i] = float(p[i])
+    keep = None
+    if user is not None:
+        keep = np.ascontiguousarray(user, dtype=np.float64)
+        cv.user = keep.ctypes.data_as(C.POINTER(C.c_double))
+    _check(lib().bm_assemble(h, C.byref(cv), int(N), _c64(k_out), _c64(k_in), int(formulation),
+                             C.byref(opts) if opts is not None else None), "bm_assemble")
+
+
+def bm_factor(h) -> int:
+    info = C.c_int(0)
+    st = lib().bm_factor(h, C.byref(info))
+    _check(st, "bm_factor", ok=(BM_OK, BM_ESINGULAR))
+    return int(info.value)
+
+
+def bm_rhs_plane_wave(h, angles, B) -> None:
+    ang = np.ascontiguousarray(angles, dtype=np.float64)
+    ptr, ld, ncols, dev, _keep = _colmajor(B, 0, writable=True)
+    _check(lib().bm_rhs_plane_wave(h, ang.ctypes.data_as(C.POINTER(C.c_double)), int(ang.size), ptr, ld, dev),
+           "bm_rhs_plane_wave")
+
+
+def bm_solve(h, B, X, raise_on_notconv: bool = True) -> bm_solve_info:
+    pb, ldb, nb, devb, _kb = _colmajor(B, 0, writable=False)
+    px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=True)
+    if devb != devx or nb != nx:
+        raise ValueError("B and X must live on the same side and have the same number of columns")
+    info = bm_solve_info()
+    st = lib().bm_solve(h, nb, pb, ldb, px, ldx, devb, C.byref(info))
+    _check(st, "bm_solve", ok=(BM_OK,) if raise_on_notconv else (BM_OK, BM_ENOTCONV))
+    return info
+
+
+def bm_far_field(h, X, angles, U) -> None:
+    px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=False)
+    pu, ldu, nu, devu, _ku = _colmajor(U, 0, writable=True)
+    ang = np.ascontiguousarray(angles, dtype=np.float64)
+    _check(lib().bm_far_field(h, px, ldx, nx, ang.ctypes.data_as(C.POINTER(C.c_double)), int(ang.size), pu, ldu,
+                              devx), "bm_far_field")
+
+
+def bm_copy_block(h, which: int, dst) -> None:
+    p, ld, _n, dev, _k = _colmajor(dst, 0, writable=True)
+    _check(lib().bm_copy_block(h, int(which), p, ld, dev), "bm_copy_block")
+
+
+def bm_hankel01(h, z):
+    """H0^(1), H1^(1) at complex points z (numpy, evaluated on the device)."""
+    zz = np.ascontiguousarray(z, dtype=np.complex128).ravel()
+    h0 = np.empty_like(zz)
+    h1 = np.empty_like(zz)
+    _check(lib().bm_hankel01(h, C.c_void_p(zz.ctypes.data), int(zz.size), C.c_void_p(h0.ctypes.data),
+                             C.c_void_p(h1.ctypes.data), 0), "bm_hankel01")
+    return h0, h1
+
+
+def bm_hankel_anchor_table():
+    """(table[ny, nx, 2] complex: H0, H1 at anchors, re0, im0, step) - host-built, no GPU needed."""
+    nx, ny = C.c_int(), C.c_int()
+    re0, im0, step = C.c_double(), C.c_double(), C.c_double()
+    L = lib()
+    _check(L.bm_hankel_anchor_table(None, 0, C.byref(nx), C.byref(ny), C.byref(re0), C.byref(im0), C.byref(step)),
+           "bm_hankel_anchor_table")
+    out = np.zeros(4 * nx.value * ny.value, dtype=np.float64)
+    _check(L.bm_hankel_anchor_table(out.ctypes.data_as(C.POINTER(C.c_double)), nx.value * ny.value, None, None,
+                                    None, None, None), "bm_hankel_anchor_table")
+    t = out.view(np.complex128).reshape(ny.value, nx.value, 2)
+    return t, re0.value, im0.value, step.value
+
+
+def bm_memory(h):
+    held, budget = C.c_size_t(), C.c_size_t()
+    _check(lib().bm_memory(h, C.byref(held), C.byref(budget)), "bm_memory")
+    return held.value, budget.value
+
+
+def bm_strerror(status: int) -> str:
+    return lib().bm_strerror(int(status)).decode()
+
+
+def bm_last_error() -> str:
+    return lib().bm_last_error().decode()

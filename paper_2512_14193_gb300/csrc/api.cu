@@ -1,0 +1,810 @@
+// C ABI of the library (include/bm.h): handle management, admission, and the orchestration of
+// assembly -> factorisation -> solve -> far field on the handle's stream.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void bm_set_error(const std::string& msg) { g_last_error = msg; }
+
+extern "C" const char* bm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* bm_strerror(bm_status s) {
+    switch (s) {
+        case BM_OK: return "BM_OK";
+        case BM_EINVAL: return "BM_EINVAL: invalid argument";
+        case BM_ENOMEM: return "BM_ENOMEM: HBM budget exceeded or allocation failed";
+        case BM_ESINGULAR: return "BM_ESINGULAR: exactly zero pivot";
+        case BM_ENOTCONV: return "BM_ENOTCONV: refinement did not converge";
+        case BM_ENONFINITE: return "BM_ENONFINITE: non-finite input";
+        case BM_ETIMEOUT: return "BM_ETIMEOUT: device wait timed out";
+        case BM_ESTATE: return "BM_ESTATE: call order violated";
+        case BM_ECUDA: return "BM_ECUDA: CUDA runtime error";
+    }
+    return "unknown bm_status";
+}
+
+// ------------------------------------------------------------------------------------------------
+// allocation with budget accounting
+// ------------------------------------------------------------------------------------------------
+bm_status ctx_alloc(bm_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return BM_OK;
+    if (c->held + bytes > c->budget) {
+        bm_set_error("allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
+        return BM_ENOMEM;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        bm_set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return BM_ENOMEM;
+    }
+    c->allocs[*p] = bytes;
+    c->held += bytes;
+    return BM_OK;
+}
+
+void ctx_free(bm_ctx* c, void* p) {
+    if (p == nullptr) return;
+    auto it = c->allocs.find(p);
+    if (it != c->allocs.end()) {
+        c->held -= it->second;
+        c->allocs.erase(it);
+    }
+    cudaFree(p);
+}
+
+namespace {
+
+template <class T>
+bm_status alloc_t(bm_ctx* c, T** p, size_t bytes) {
+    void* q = nullptr;
+    bm_status s = ctx_alloc(c, &q, bytes);
+    *p = reinterpret_cast<T*>(q);
+    return s;
+}
+
+#define FREE(ptr)              \
+    do {                       \
+        ctx_free(c, (ptr));    \
+        (ptr) = nullptr;       \
+    } while (0)
+
+void drop_graphs(bm_ctx* c) {
+    if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
+    c->g_factor = nullptr;
+    for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);
+    c->g_solve.clear();
+}
+
+void free_solve_ws(bm_ctx* c) {
+    FREE(c->d_X);
+    FREE(c->d_R);
+    FREE(c->d_Bw);
+    FREE(c->d_Wr);
+    FREE(c->d_Wi);
+    FREE(c->d_W2r);
+    FREE(c->d_W2i);
+    FREE(c->d_Y64);
+    FREE(c->d_Y64b);
+    c->ws_nrhs = 0;
+    for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);
+    c->g_solve.clear();
+}
+
+void free_problem(bm_ctx* c) {
+    drop_graphs(c);
+    free_solve_ws(c);
+    FREE(c->d_geom);
+    FREE(c->d_Mtop);
+    FREE(c->d_Mbot);
+    FREE(c->d_A);
+    FREE(c->d_F64);
+    FREE(c->d_F32r);
+    FREE(c->d_F32i);
+    FREE(c->d_ipiv);
+    FREE(c->d_perm);
+    FREE(c->d_dinvL);
+    FREE(c->d_dinvU);
+    FREE(c->d_Ap_r);
+    FREE(c->d_Ap_i);
+    FREE(c->d_Bp_r);
+    FREE(c->d_Bp_i);
+    FREE(c->d_Lp_r);
+    FREE(c->d_Lp_i);
+    FREE(c->d_Up_r);
+    FREE(c->d_Up_i);
+    c->assembled = c->factored = c->singular = false;
+    c->tm_ok = false;
+}
+
+bool finite_c(bm_c64 z) { return std::isfinite(z.re) && std::isfinite(z.im); }
+double2 d2(bm_c64 z) { return make_double2(z.re, z.im); }
+
+long round_up(long a, long b) { return (a + b - 1) / b * b; }
+
+struct Plan {
+    long ldtop = 0, ldbot = 0, ldA = 0, ldF = 0, ldk_schur = 0, ldk_lu = 0;
+    int n = 0, nsys = 0, nb = 0, kseg = 0, nblk = 0;
+    size_t bytes = 0;
+};
+
+Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
+    Plan p;
+    const bool c32 = prec != BM_FP64;
+    const bool split = prec == BM_CF32_3XTF32_IR;
+    p.n = (form == BM_MIXED) ? N : 2 * N;
+    p.nsys = (form == BM_MIXED) ? 3 * N : 2 * N;
+    p.nb = nb_user > 0 ? nb_user : (c32 ? 128 : 64);
+    p.ldF = pad32(p.n);
+    size_t b = 7 * (size_t)N * 8;
+    if (form == BM_MIXED) {
+        p.ldtop = pad32(2L * N);
+        p.ldbot = pad32(N);
+        b += (size_t)p.ldtop * N * 16 + (size_t)p.ldbot * 2 * N * 16;
+    } else {
+        p.ldA = pad32(2L * N);
+        b += (size_t)p.ldA * 2 * N * 16;
+    }
+    if (!c32) {
+        b += (size_t)p.ldF * p.n * 16;
+    } else {
+        b += (size_t)p.ldF * p.n * 8;
+        if (form == BM_MIXED) {
+            p.kseg = 2 * N;
+            long kext = split ? 3L * p.kseg : p.kseg;
+            p.ldk_schur = round_up(kext, 32);
+            b += 2 * (size_t)N * p.ldk_schur * 8;
+        }
+        long kl = split ? 3L * p.nb : p.nb;
+        p.ldk_lu = round_up(kl, 32);
+        b += 2 * (size_t)p.n * p.ldk_lu * 8;
+    }
+    p.nblk = ceil_div(p.n, bs);
+    b += 2 * (size_t)p.n * 4;
+    b += 2 * (size_t)p.nblk * bs * bs * (c32 ? 8 : 16);
+    p.bytes = b;
+    return p;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+extern "C" bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size_t hbm_budget_bytes) {
+    if (out == nullptr) return BM_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        bm_set_error("no CUDA device is available");
+        return BM_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return BM_EINVAL;
+    BM_CUDA_TRY(cudaSetDevice(device));
+    bm_ctx* c = new bm_ctx();
+    c->device = device;
+    if (cuda_stream) {
+        c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            bm_set_error(cudaGetErrorString(e));
+            return BM_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+    int nx, ny;
+    double re0, im0, step;
+    const std::vector<double2>& tab = hankel_anchor_host(nx, ny, re0, im0, step);
+    bm_status s = alloc_t(c, &c->d_htab, tab.size() * sizeof(double2));
+    if (s == BM_OK) s = alloc_t(c, &c->d_normA, 4 * sizeof(double));
+    if (s == BM_OK) s = alloc_t(c, &c->d_info, 64 * sizeof(int));
+    if (s == BM_OK) s = alloc_t(c, &c->d_maps, 2 * swap_map_bytes());
+    if (s != BM_OK) {
+        bm_destroy(c);
+        return s;
+    }
+    c->d_err = c->d_info + 1;
+    cudaMemcpy(c->d_htab, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    c->htab = HankelTable{c->d_htab, nx, ny, re0, im0, step, 1.0 / step};
+    *out = c;
+    return BM_OK;
+}
+
+extern "C" bm_status bm_destroy(bm_ctx* c) {
+    if (c == nullptr) return BM_EINVAL;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_problem(c);
+    FREE(c->d_htab);
+    FREE(c->d_normA);
+    FREE(c->d_info);
+    FREE(c->d_maps);
+    for (auto& kv : c->allocs) cudaFree(kv.first);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return BM_OK;
+}
+
+extern "C" bm_status bm_memory(bm_ctx* c, size_t* held, size_t* budget) {
+    if (c == nullptr) return BM_EINVAL;
+    if (held) *held = c->held;
+    if (budget) *budget = c->budget;
+    return BM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64 k_out, bm_c64 k_in,
+                                 bm_formulation form, const bm_opts* opts) {
+    if (c == nullptr || curve == nullptr) return BM_EINVAL;
+    if (N < 8 || N > 65536) {
+        bm_set_error("N must be in [8, 65536]");
+        return BM_EINVAL;
+    }
+    if (form != BM_MIXED && form != BM_ORDINARY) return BM_EINVAL;
+    if (curve->kind < BM_CURVE_CIRCLE || curve->kind > BM_CURVE_USER) return BM_EINVAL;
+    if (curve->kind == BM_CURVE_USER && curve->user == nullptr) return BM_EINVAL;
+    for (int i = 0; i < 4; ++i)
+        if (!std::isfinite(curve->p[i])) return BM_ENONFINITE;
+    if (!finite_c(k_out) || !finite_c(k_in)) return BM_ENONFINITE;
+    const double deg = 180.0 / M_PI;
+    for (bm_c64 k : {k_out, k_in}) {
+        if (!(k.re > 0)) {
+            bm_set_error("wavenumbers need Re k > 0");
+            return BM_EINVAL;
+        }
+        if (std::fabs(std::atan2(k.im, k.re)) * deg > 60.0 + 1e-9 && k.im > 0) {
+            bm_set_error("wavenumbers need arg k <= 60 degrees");
+            return BM_EINVAL;
+        }
+        if (std::atan2(k.im, k.re) * deg < -89.0) {
+            bm_set_error("wavenumbers need arg k > -89 degrees");
+            return BM_EINVAL;
+        }
+    }
+    if ((curve->kind == BM_CURVE_CIRCLE && !(curve->p[0] > 0)) ||
+        (curve->kind == BM_CURVE_ELLIPSE && !(curve->p[0] > 0 && curve->p[1] > 0)) ||
+        (curve->kind == BM_CURVE_STAR && !(curve->p[0] > std::fabs(curve->p[1]))) ||
+        (curve->kind == BM_CURVE_KITE && !(curve->p[1] != 0))) {
+        bm_set_error("curve parameters do not describe a simple closed curve");
+        return BM_EINVAL;
+    }
+    int prec = opts ? opts->prec : BM_FP64;
+    if (prec < BM_FP64 || prec > BM_CF32_3XTF32_IR) return BM_EINVAL;
+    int nb = opts ? opts->nb : 0;
+    if (nb != 0 && (nb % 32 != 0 || nb < 32 || nb > 256)) {
+        bm_set_error("nb must be a multiple of 32 in [32, 256]");
+        return BM_EINVAL;
+    }
+    double eps0 = (opts && opts->eps0 != 0.0) ? opts->eps0 : 1.0;
+    double2 k0 = d2(k_out), k1 = d2(k_in);
+    double2 eps1, beta;
+    if (opts && opts->eps_set) {
+        if (!finite_c(opts->eps1)) return BM_ENONFINITE;
+        eps1 = d2(opts->eps1);
+    } else {
+        double2 r = cdiv(k1, k0);
+        eps1 = cscale(cmul(r, r), eps0);
+    }
+    if (opts && opts->beta_set) {
+        if (!finite_c(opts->beta)) return BM_ENONFINITE;
+        beta = d2(opts->beta);
+    } else {
+        beta = cmuli(cinv(k0));
+    }
+
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStreamSynchronize(c->stream);
+    free_problem(c);
+    c->bs_solve = 64;
+    Plan p = make_plan(N, form, prec, nb, c->bs_solve);
+    if (c->held + p.bytes > c->budget) {
+        bm_set_error("admission: system needs " + std::to_string(p.bytes) + " bytes, budget leaves " +
+                     std::to_string(c->budget - c->held));
+        return BM_ENOMEM;
+    }
+    c->N = N;
+    c->n = p.n;
+    c->nsys = p.nsys;
+    c->form = form;
+    c->prec = prec;
+    c->nb = p.nb;
+    c->k0 = k0;
+    c->k1 = k1;
+    c->eps0 = make_double2(eps0, 0.0);
+    c->eps1 = eps1;
+    c->beta = beta;
+    c->refine_tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : 1e-9;
+    c->refine_maxit = (opts && opts->refine_maxit > 0) ? opts->refine_maxit : 30;
+    c->ldtop = p.ldtop;
+    c->ldbot = p.ldbot;
+    c->ldA = p.ldA;
+    c->ldF = p.ldF;
+    c->ldk_schur = p.ldk_schur;
+    c->kseg_schur = p.kseg;
+    c->ldk_lu = p.ldk_lu;
+    const bool c32 = prec != BM_FP64;
+    bm_status s = alloc_t(c, &c->d_geom, 7 * (size_t)N * 8);
+    if (s == BM_OK && form == BM_MIXED) {
+        s = alloc_t(c, &c->d_Mtop, (size_t)p.ldtop * N * 16);
+        if (s == BM_OK) s = alloc_t(c, &c->d_Mbot, (size_t)p.ldbot * 2 * N * 16);
+    } else if (s == BM_OK) {
+        s = alloc_t(c, &c->d_A, (size_t)p.ldA * 2 * N * 16);
+    }
+    if (s == BM_OK && !c32) s = alloc_t(c, &c->d_F64, (size_t)p.ldF * p.n * 16);
+    if (s == BM_OK && c32) {
+        s = alloc_t(c, &c->d_F32r, (size_t)p.ldF * p.n * 4);
+        if (s == BM_OK) s = alloc_t(c, &c->d_F32i, (size_t)p.ldF * p.n * 4);
+        if (s == BM_OK && form == BM_MIXED) {
+            size_t pb = (size_t)N * p.ldk_schur * 4;
+            if (s == BM_OK) s = alloc_t(c, &c->d_Ap_r, pb);
+            if (s == BM_OK) s = alloc_t(c, &c->d_Ap_i, pb);
+            if (s == BM_OK) s = alloc_t(c, &c->d_Bp_r, pb);
+            if (s == BM_OK) s = alloc_t(c, &c->d_Bp_i, pb);
+        }
+        size_t lb = (size_t)p.n * p.ldk_lu * 4;
+        if (s == BM_OK) s = alloc_t(c, &c->d_Lp_r, lb);
+        if (s == BM_OK) s = alloc_t(c, &c->d_Lp_i, lb);
+        if (s == BM_OK) s = alloc_t(c, &c->d_Up_r, lb);
+        if (s == BM_OK) s = alloc_t(c, &c->d_Up_i, lb);
+    }
+    if (s == BM_OK) s = alloc_t(c, &c->d_ipiv, (size_t)p.n * 4);
+    if (s == BM_OK) s = alloc_t(c, &c->d_perm, (size_t)p.n * 4);
+    size_t dinv = (size_t)p.nblk * c->bs_solve * c->bs_solve * (c32 ? 8 : 16);
+    if (s == BM_OK) s = alloc_t(c, &c->d_dinvL, dinv);
+    if (s == BM_OK) s = alloc_t(c, &c->d_dinvU, dinv);
+    if (s != BM_OK) {
+        free_problem(c);
+        return s;
+    }
+    cudaStream_t st = c->stream;
+    if (c32) {
+        size_t lb = (size_t)p.n * p.ldk_lu * 4;
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_Lp_r, 0, lb, st));
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_Lp_i, 0, lb, st));
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_Up_r, 0, lb, st));
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_Up_i, 0, lb, st));
+    }
+    double* d_user = nullptr;
+    if (curve->kind == BM_CURVE_USER) {
+        for (long i = 0; i < 6L * N; ++i)
+            if (!std::isfinite(curve->user[i])) {
+                free_problem(c);
+                return BM_ENONFINITE;
+            }
+        s = alloc_t(c, &d_user, 6 * (size_t)N * 8);
+        if (s != BM_OK) {
+            free_problem(c);
+            return s;
+        }
+        BM_CUDA_TRY(cudaMemcpyAsync(d_user, curve->user, 6 * (size_t)N * 8, cudaMemcpyHostToDevice, st));
+    }
+    BM_CUDA_TRY(launch_geometry(st, curve->kind, curve->p, N, d_user, c->d_geom));
+    BM_CUDA_TRY(launch_assemble(st, c));
+    BM_CUDA_TRY(launch_normA(st, c));
+    if (c32) {
+        if (form == BM_MIXED) BM_CUDA_TRY(launch_pack_schur(st, c, prec == BM_CF32_3XTF32_IR));
+    }
+    BM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (d_user) ctx_free(c, d_user);
+    BM_TRY(lu_setup(c));
+    if (c32) {
+        const bool split = prec == BM_CF32_3XTF32_IR;
+        if (form == BM_MIXED) {
+            long kext = split ? 3L * p.kseg : p.kseg;
+            BM_TRY(tc_make_map(c->tm_schur[0], c->d_Ap_r, N, kext, p.ldk_schur, TC_BM));
+            BM_TRY(tc_make_map(c->tm_schur[1], c->d_Ap_i, N, kext, p.ldk_schur, TC_BM));
+            BM_TRY(tc_make_map(c->tm_schur[2], c->d_Bp_r, N, kext, p.ldk_schur, TC_BN));
+            BM_TRY(tc_make_map(c->tm_schur[3], c->d_Bp_i, N, kext, p.ldk_schur, TC_BN));
+        }
+        long klu = p.ldk_lu;
+        BM_TRY(tc_make_map(c->tm_lu[0], c->d_Lp_r, p.n, klu, p.ldk_lu, TC_BM));
+        BM_TRY(tc_make_map(c->tm_lu[1], c->d_Lp_i, p.n, klu, p.ldk_lu, TC_BM));
+        BM_TRY(tc_make_map(c->tm_lu[2], c->d_Up_r, p.n, klu, p.ldk_lu, TC_BN));
+        BM_TRY(tc_make_map(c->tm_lu[3], c->d_Up_i, p.n, klu, p.ldk_lu, TC_BN));
+        c->tm_ok = true;
+    }
+    c->assembled = true;
+    return BM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+// Everything bm_factor enqueues: prepare the matrix to factor, then the LU.
+bm_status factor_sequence(bm_ctx* c) {
+    cudaStream_t s = c->stream;
+    BM_CUDA_TRY(cudaMemsetAsync(c->d_info, 0, 2 * sizeof(int), s));
+    if (c->prec == BM_FP64) {
+        Z64 F{c->d_F64, c->ldF};
+        if (c->form == BM_MIXED) {
+            // U33 = -[M31 M32] [M13; M23]
+            BM_CUDA_TRY(gemm_z64(s, c->N, c->N, 2 * c->N, -1.0, Z64{c->d_Mbot, c->ldbot}, false,
+                                 Z64{c->d_Mtop, c->ldtop}, 0.0, F));
+        } else {
+            BM_CUDA_TRY(launch_copy_z64(s, c->d_A, c->ldA, c->n, c->n, c->d_F64, c->ldF));
+        }
+    } else {
+        if (c->form == BM_MIXED) {
+            long kext = (c->prec == BM_CF32_3XTF32_IR) ? 3L * c->kseg_schur : c->kseg_schur;
+            BM_CUDA_TRY(gemm_tc(s, c->tm_schur[0], c->tm_schur[1], c->tm_schur[2], c->tm_schur[3], c->d_F32r,
+                                c->d_F32i, c->ldF, c->N, c->N, (int)kext, -1.0f, 0.0f, c->d_err));
+        } else {
+            BM_CUDA_TRY(launch_to_c32(s, c->d_A, c->ldA, c->n, c->n, c->d_F32r, c->d_F32i, c->ldF));
+        }
+    }
+    return lu_factor_enqueue(c);
+}
+
+bool graphs_enabled() {
+    const char* e = getenv("BM_NO_GRAPHS");
+    return !(e && e[0] == '1');
+}
+
+// Run `fn` through a cached CUDA graph (captured on first use), or eagerly if graphs are off.
+template <class Fn>
+bm_status run_captured(bm_ctx* c, cudaGraphExec_t* slot, Fn fn) {
+    if (!graphs_enabled()) return fn();
+    if (*slot == nullptr) {
+        cudaGraph_t g = nullptr;
+        BM_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        bm_status s = fn();
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (s != BM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) {
+            bm_set_error(std::string("stream capture: ") + cudaGetErrorString(e));
+            return BM_ECUDA;
+        }
+        e = cudaGraphInstantiate(slot, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            *slot = nullptr;
+            bm_set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+            return BM_ECUDA;
+        }
+    }
+    BM_CUDA_TRY(cudaGraphLaunch(*slot, c->stream));
+    return BM_OK;
+}
+
+}  // namespace
+
+extern "C" bm_status bm_factor(bm_ctx* c, int* info) {
+    if (c == nullptr) return BM_EINVAL;
+    if (info) *info = 0;
+    if (!c->assembled) {
+        bm_set_error("bm_factor before bm_assemble");
+        return BM_ESTATE;
+    }
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    BM_TRY(run_captured(c, &c->g_factor, [&]() { return factor_sequence(c); }));
+    int h[2] = {0, 0};
+    BM_CUDA_TRY(cudaMemcpyAsync(h, c->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (h[1] != 0) {
+        bm_set_error("tensor-core GEMM: a bounded wait timed out");
+        c->factored = false;
+        return BM_ETIMEOUT;
+    }
+    c->factored = true;
+    c->singular = h[0] != 0;
+    if (info) *info = h[0];
+    if (c->singular) {
+        bm_set_error("zero pivot in column " + std::to_string(h[0]));
+        return BM_ESINGULAR;
+    }
+    return BM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+bm_status ensure_ws(bm_ctx* c, int nrhs) {
+    if (nrhs <= c->ws_nrhs) return BM_OK;
+    free_solve_ws(c);
+    int w = std::max(nrhs, 8);
+    size_t zb = (size_t)c->nsys * w * 16;
+    BM_TRY(alloc_t(c, &c->d_X, zb));
+    BM_TRY(alloc_t(c, &c->d_R, zb));
+    BM_TRY(alloc_t(c, &c->d_Bw, zb));
+    size_t yb = (size_t)c->n * w * 16;
+    BM_TRY(alloc_t(c, &c->d_Y64, yb));
+    BM_TRY(alloc_t(c, &c->d_Y64b, yb));
+    if (c->prec != BM_FP64) {
+        size_t fb = (size_t)c->nsys * w * 4;
+        BM_TRY(alloc_t(c, &c->d_Wr, fb));
+        BM_TRY(alloc_t(c, &c->d_Wi, fb));
+        size_t vb = (size_t)c->n * w * 4;
+        BM_TRY(alloc_t(c, &c->d_W2r, vb));
+        BM_TRY(alloc_t(c, &c->d_W2i, vb));
+    }
+    c->ws_nrhs = w;
+    return BM_OK;
+}
+
+bm_status read_eta(bm_ctx* c, double* eta, bool* nonfinite) {
+    double h[2];
+    BM_CUDA_TRY(cudaMemcpyAsync(h, c->d_normA + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *eta = h[0];
+    if (nonfinite) *nonfinite = h[1] != 0.0;
+    return BM_OK;
+}
+
+}  // namespace
+
+extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_c64* X, int ldx, int on_device,
+                              bm_solve_info* info) {
+    if (c == nullptr) return BM_EINVAL;
+    if (info) std::memset(info, 0, sizeof(*info));
+    if (!c->factored || c->singular) {
+        bm_set_error(c->singular ? "bm_solve on a singular factorisation" : "bm_solve before bm_factor");
+        return BM_ESTATE;
+    }
+    if (nrhs < 1 || B == nullptr || X == nullptr || ldb < c->nsys || ldx < c->nsys) return BM_EINVAL;
+    if ((const void*)B == (const void*)X) return BM_EINVAL;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    BM_TRY(ensure_ws(c, nrhs));
+    cudaStream_t s = c->stream;
+    const long ld = c->nsys;
+    cudaEvent_t e0, e1, r0, r1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&r0);
+    cudaEventCreate(&r1);
+    auto cleanup = [&]() {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(r0);
+        cudaEventDestroy(r1);
+    };
+    cudaEventRecord(e0, s);
+    cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t ce = cudaMemcpy2DAsync(c->d_Bw, ld * 16, B, (size_t)ldb * 16, (size_t)c->nsys * 16, nrhs, kin, s);
+    if (ce != cudaSuccess) {
+        cleanup();
+        bm_set_error(std::string("copy of B: ") + cudaGetErrorString(ce));
+        return BM_ECUDA;
+    }
+    double* d_eta = c->d_normA + 2;
+    double eta = 0.0;
+    bool nonfinite = false;
+    int iters = 0;
+    float t_res = 0.f;
+    bm_status st = BM_OK;
+    if (c->prec == BM_FP64) {
+        st = solve_fp64(c, c->d_Bw, c->d_X, ld, nrhs);
+        if (st == BM_OK && info) {
+            cudaEventRecord(r0, s);
+            st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
+            cudaEventRecord(r1, s);
+            if (st == BM_OK) st = backward_error(c, c->d_R, c->d_X, c->d_Bw, ld, nrhs, d_eta);
+            if (st == BM_OK) st = read_eta(c, &eta, &nonfinite);
+            cudaEventElapsedTime(&t_res, r0, r1);
+        }
+    } else {
+        // x0 = 0, r0 = b: the first correction is the plain FP32 solve
+        cudaMemsetAsync(c->d_X, 0, (size_t)ld * nrhs * 16, s);
+        cudaMemcpyAsync(c->d_R, c->d_Bw, (size_t)ld * nrhs * 16, cudaMemcpyDeviceToDevice, s);
+        for (int it = 0;; ++it) {
+            if (it > 0) {
+                cudaEventRecord(r0, s);
+                st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
+                cudaEventRecord(r1, s);
+                if (st != BM_OK) break;
+            }
+            st = backward_error(c, c->d_R, c->d_X, c->d_Bw, ld, nrhs, d_eta);
+            if (st == BM_OK) st = read_eta(c, &eta, &nonfinite);
+            if (st != BM_OK) break;
+            if (it > 0) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, r0, r1);
+                t_res += ms;
+            }
+            if (nonfinite) {
+                st = BM_ENONFINITE;
+                break;
+            }
+            if (eta <= c->refine_tol) break;
+            if (it >= c->refine_maxit) {
+                bm_set_error("refinement stopped at backward error " + std::to_string(eta));
+                st = BM_ENOTCONV;
+                break;
+            }
+            cudaGraphExec_t& slot = c->g_solve[nrhs];
+            st = run_captured(c, &slot, [&]() { return correction_c32(c, c->d_R, c->d_X, ld, nrhs); });
+            if (st != BM_OK) break;
+            ++iters;
+        }
+    }
+    if (st == BM_OK || st == BM_ENOTCONV) {
+        if (c->prec == BM_FP64 && nonfinite) st = BM_ENONFINITE;
+        cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        ce = cudaMemcpy2DAsync(X, (size_t)ldx * 16, c->d_X, ld * 16, (size_t)c->nsys * 16, nrhs, kout, s);
+        if (ce != cudaSuccess) {
+            cleanup();
+            bm_set_error(std::string("copy of X: ") + cudaGetErrorString(ce));
+            return BM_ECUDA;
+        }
+    }
+    cudaEventRecord(e1, s);
+    cudaError_t se = cudaStreamSynchronize(s);
+    float t_all = 0.f;
+    cudaEventElapsedTime(&t_all, e0, e1);
+    cleanup();
+    if (se != cudaSuccess) {
+        bm_set_error(std::string("solve: ") + cudaGetErrorString(se));
+        return BM_ECUDA;
+    }
+    if (info) {
+        info->iterations = iters;
+        info->backward_error = eta;
+        info->t_solve_ms = t_all;
+        info->t_residual_ms = t_res;
+    }
+    return st;
+}
+
+// ------------------------------------------------------------------------------------------------
+extern "C" bm_status bm_rhs_plane_wave(bm_ctx* c, const double* angles, int nrhs, bm_c64* B, int ldb, int on_device) {
+    if (c == nullptr || angles == nullptr || B == nullptr || nrhs < 1) return BM_EINVAL;
+    if (!c->assembled) return BM_ESTATE;
+    if (ldb < c->nsys) return BM_EINVAL;
+    for (int i = 0; i < nrhs; ++i)
+        if (!std::isfinite(angles[i])) return BM_ENONFINITE;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    double* d_ang = nullptr;
+    BM_TRY(alloc_t(c, &d_ang, (size_t)nrhs * 8));
+    double2* dB = nullptr;
+    if (!on_device) {
+        bm_status st = alloc_t(c, &dB, (size_t)c->nsys * nrhs * 16);
+        if (st != BM_OK) {
+            ctx_free(c, d_ang);
+            return st;
+        }
+    }
+    double2* out = on_device ? reinterpret_cast<double2*>(B) : dB;
+    long ldo = on_device ? ldb : c->nsys;
+    cudaMemcpyAsync(d_ang, angles, (size_t)nrhs * 8, cudaMemcpyHostToDevice, s);
+    cudaError_t e = launch_plane_wave(s, c, d_ang, nrhs, out, ldo);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpy2DAsync(B, (size_t)ldb * 16, dB, (size_t)c->nsys * 16, (size_t)c->nsys * 16, nrhs,
+                              cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    ctx_free(c, d_ang);
+    if (dB) ctx_free(c, dB);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        bm_set_error(std::string("plane wave: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return BM_ECUDA;
+    }
+    return BM_OK;
+}
+
+extern "C" bm_status bm_far_field(bm_ctx* c, const bm_c64* X, int ldx, int nrhs, const double* angles, int M,
+                                  bm_c64* Uinf, int ldu, int on_device) {
+    if (c == nullptr || X == nullptr || angles == nullptr || Uinf == nullptr || nrhs < 1 || M < 1) return BM_EINVAL;
+    if (!c->assembled) return BM_ESTATE;
+    if (ldx < c->nsys || ldu < M) return BM_EINVAL;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    double* d_ang = nullptr;
+    double2 *dX = nullptr, *dU = nullptr;
+    bm_status st = alloc_t(c, &d_ang, (size_t)M * 8);
+    if (st == BM_OK && !on_device) st = alloc_t(c, &dX, (size_t)2 * c->N * nrhs * 16);
+    if (st == BM_OK && !on_device) st = alloc_t(c, &dU, (size_t)M * nrhs * 16);
+    if (st != BM_OK) {
+        ctx_free(c, d_ang);
+        ctx_free(c, dX);
+        return st;
+    }
+    const double2* xin = on_device ? reinterpret_cast<const double2*>(X) : dX;
+    long ldxi = on_device ? ldx : 2L * c->N;
+    double2* uo = on_device ? reinterpret_cast<double2*>(Uinf) : dU;
+    long ldo = on_device ? ldu : M;
+    cudaMemcpyAsync(d_ang, angles, (size_t)M * 8, cudaMemcpyHostToDevice, s);
+    if (!on_device)
+        cudaMemcpy2DAsync(dX, (size_t)2 * c->N * 16, X, (size_t)ldx * 16, (size_t)2 * c->N * 16, nrhs,
+                          cudaMemcpyHostToDevice, s);
+    cudaError_t e = launch_far_field(s, c, xin, ldxi, nrhs, d_ang, M, uo, ldo);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpy2DAsync(Uinf, (size_t)ldu * 16, dU, (size_t)M * 16, (size_t)M * 16, nrhs,
+                              cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    ctx_free(c, d_ang);
+    ctx_free(c, dX);
+    ctx_free(c, dU);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        bm_set_error(std::string("far field: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return BM_ECUDA;
+    }
+    return BM_OK;
+}
+
+extern "C" bm_status bm_copy_block(bm_ctx* c, int which, bm_c64* dst, int ldd, int on_device) {
+    if (c == nullptr || dst == nullptr) return BM_EINVAL;
+    if (!c->assembled) return BM_ESTATE;
+    const double2* src;
+    long lds;
+    int rows, cols;
+    const long N = c->N;
+    if (c->form == BM_MIXED) {
+        if (which < 0 || which > 3) return BM_EINVAL;
+        rows = cols = (int)N;
+        if (which == 0) {
+            src = c->d_Mtop;
+            lds = c->ldtop;
+        } else if (which == 1) {
+            src = c->d_Mtop + N;
+            lds = c->ldtop;
+        } else if (which == 2) {
+            src = c->d_Mbot;
+            lds = c->ldbot;
+        } else {
+            src = c->d_Mbot + N * c->ldbot;
+            lds = c->ldbot;
+        }
+    } else {
+        if (which != 0) return BM_EINVAL;
+        rows = cols = (int)(2 * N);
+        src = c->d_A;
+        lds = c->ldA;
+    }
+    if (ldd < rows) return BM_EINVAL;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    BM_CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)ldd * 16, src, (size_t)lds * 16, (size_t)rows * 16, cols,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return BM_OK;
+}
+
+extern "C" bm_status bm_hankel01(bm_ctx* c, const bm_c64* z, int n, bm_c64* h0, bm_c64* h1, int on_device) {
+    if (c == nullptr || z == nullptr || h0 == nullptr || h1 == nullptr || n < 1) return BM_EINVAL;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    double2 *dz = nullptr, *d0 = nullptr, *d1 = nullptr;
+    if (!on_device) {
+        bm_status st = alloc_t(c, &dz, (size_t)n * 16);
+        if (st == BM_OK) st = alloc_t(c, &d0, (size_t)n * 16);
+        if (st == BM_OK) st = alloc_t(c, &d1, (size_t)n * 16);
+        if (st != BM_OK) {
+            ctx_free(c, dz);
+            ctx_free(c, d0);
+            return st;
+        }
+        cudaMemcpyAsync(dz, z, (size_t)n * 16, cudaMemcpyHostToDevice, s);
+    }
+    const double2* zi = on_device ? reinterpret_cast<const double2*>(z) : dz;
+    double2* o0 = on_device ? reinterpret_cast<double2*>(h0) : d0;
+    double2* o1 = on_device ? reinterpret_cast<double2*>(h1) : d1;
+    cudaError_t e = launch_hankel_probe(s, c, zi, n, o0, o1);
+    if (e == cudaSuccess && !on_device) {
+        cudaMemcpyAsync(h0, d0, (size_t)n * 16, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(h1, d1, (size_t)n * 16, cudaMemcpyDeviceToHost, s);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    ctx_free(c, dz);
+    ctx_free(c, d0);
+    ctx_free(c, d1);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        bm_set_error(std::string("hankel probe: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return BM_ECUDA;
+    }
+    return BM_OK;
+}

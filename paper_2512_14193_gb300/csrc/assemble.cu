@@ -1,0 +1,544 @@
+// Nystrom assembly of the direct-indirect (Eq. dis_mixedBM) and ordinary (Eq. dis_BM) systems,
+// and the small O(N) / O(N M) kernels around it: node geometry, plane-wave right-hand sides,
+// ||A||_inf, far field, the Hankel probe, and the FP32 operand packs for the tensor cores.
+//
+// Kernels of section 2.2 with d = x_i - y_j, r = |d|, w_j = h |x'(t_j)| (row i target, column j
+// source):
+//   S  = (i/4) H0(kr) w_j             D  = (ik/4) H1(kr) (d.nu_j)/r w_j
+//   D* = -(ik/4) H1(kr) (d.nu_i)/r w_j
+//   N  = (ik/4)[k H0 (d.nu_i)(d.nu_j)/r^2 - 2 H1 (d.nu_i)(d.nu_j)/r^3 + H1 (nu_i.nu_j)/r] w_j
+// r is symmetric in (i, j), so one Hankel evaluation per wavenumber serves both (i, j) and
+// (j, i): the swapped entry flips the sign of d and swaps which normal is the target's.
+// Diagonal: the one-point zeta-corrected trapezoid rule of section 4 -
+//   S_ii = w_i [i/4 - (ln(k/2) + gamma)/(2 pi) - ln(w_i/(2 pi))/(2 pi)]
+//   D_ii = D*_ii = -kappa_i w_i/(4 pi)
+//   N_ii = -pi/(6 h |x'_i|) - (k^2/(4 pi)) ln(h/(2 pi)) w_i
+// Blocks (Theorem thm:LU): M13 = -S1, M23 = -(D*1 + I/2)/eps1, M31 = D0 - I/2 + beta N0,
+// M32 = -eps0 (S0 + beta (D*0 + I/2)); ordinary (Eq. dis_BM, (2,2) block -eps1 S1):
+// [M31, M32; D1 + I/2, -eps1 S1].
+#include "common.cuh"
+#include "hankel.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846264338327950288;
+
+__global__ void geom_kernel(int kind, double p0, double p1, double p2, int N, const double* __restrict__ user,
+                            double* __restrict__ g) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double h = 2.0 * PI / N;
+    double t = h * j;
+    double x, y, dx, dy, ddx, ddy;
+    if (kind == BM_CURVE_USER) {
+        x = user[6 * j + 0];
+        y = user[6 * j + 1];
+        dx = user[6 * j + 2];
+        dy = user[6 * j + 3];
+        ddx = user[6 * j + 4];
+        ddy = user[6 * j + 5];
+    } else {
+        double s, c;
+        sincos(t, &s, &c);
+        if (kind == BM_CURVE_CIRCLE) {
+            x = p1 + p0 * c;
+            y = p2 + p0 * s;
+            dx = -p0 * s;
+            dy = p0 * c;
+            ddx = -p0 * c;
+            ddy = -p0 * s;
+        } else if (kind == BM_CURVE_ELLIPSE) {
+            x = p0 * c;
+            y = p1 * s;
+            dx = -p0 * s;
+            dy = p1 * c;
+            ddx = -p0 * c;
+            ddy = -p1 * s;
+        } else if (kind == BM_CURVE_STAR) {
+            double sm, cm;
+            sincos(p2 * t, &sm, &cm);
+            double r = p0 + p1 * cm, dr = -p1 * p2 * sm, ddr = -p1 * p2 * p2 * cm;
+            x = r * c;
+            y = r * s;
+            dx = dr * c - r * s;
+            dy = dr * s + r * c;
+            ddx = ddr * c - 2.0 * dr * s - r * c;
+            ddy = ddr * s + 2.0 * dr * c - r * s;
+        } else {  // kite
+            double s2, c2;
+            sincos(2.0 * t, &s2, &c2);
+            x = c + p0 * c2 - p0;
+            y = p1 * s;
+            dx = -s - 2.0 * p0 * s2;
+            dy = p1 * c;
+            ddx = -c - 4.0 * p0 * c2;
+            ddy = -p1 * s;
+        }
+    }
+    double sp = hypot(dx, dy);
+    g[0 * N + j] = x;
+    g[1 * N + j] = y;
+    g[2 * N + j] = dy / sp;   // nu = (y', -x')/|x'|
+    g[3 * N + j] = -dx / sp;
+    g[4 * N + j] = sp;
+    g[5 * N + j] = (dx * ddy - dy * ddx) / (sp * sp * sp);
+    g[6 * N + j] = h * sp;
+}
+
+struct AsmArgs {
+    int N;
+    double h;
+    double2 k0, k1, eps0, eps1, beta;
+    HankelTable T;
+    const double* g;
+    double2* o[4];  // output quadrants (see header comment)
+    long ld[4];
+};
+
+struct PairVals {
+    // per wavenumber: cS = (i/4) H0, cD = (ik/4) H1 / r, B = N bracket (without weight)
+    double2 cS0, cD0, B0, cS1, cD1;
+};
+
+__device__ __forceinline__ void pair_vals(const AsmArgs& a, double dx, double dy, double dni, double dnj, double ninj,
+                                          PairVals& v) {
+    double r = sqrt(dx * dx + dy * dy);
+    double ir = 1.0 / r;
+    double2 h0, h1;
+    hk::hankel01(cscale(a.k0, r), a.T, h0, h1);
+    double2 ik0 = cscale(cmuli(a.k0), 0.25);  // i k0 / 4
+    v.cS0 = cscale(cmuli(h0), 0.25);
+    v.cD0 = cscale(cmul(ik0, h1), ir);
+    // N bracket: k H0 dni dnj / r^2 - 2 H1 dni dnj / r^3 + H1 ninj / r
+    double pp = dni * dnj * ir * ir;
+    double2 br = cscale(cmul(a.k0, h0), pp);
+    br = cadd(br, cscale(h1, (ninj - 2.0 * pp) * ir));
+    v.B0 = cmul(ik0, br);
+    hk::hankel01(cscale(a.k1, r), a.T, h0, h1);
+    double2 ik1 = cscale(cmuli(a.k1), 0.25);
+    v.cS1 = cscale(cmuli(h0), 0.25);
+    v.cD1 = cscale(cmul(ik1, h1), ir);
+}
+
+// Entries of the four output quadrants for an ordered pair with given target/source normal
+// projections (dn_t = d.nu_target, dn_s = d.nu_source) and source weight ws.
+template <int FORM>
+__device__ __forceinline__ void outputs(const AsmArgs& a, const PairVals& v, double dn_t, double dn_s, double ws,
+                                        double2 out[4]) {
+    double2 S0 = cscale(v.cS0, ws);
+    double2 D0 = cscale(v.cD0, dn_s * ws);
+    double2 Ds0 = cscale(v.cD0, -dn_t * ws);
+    double2 N0 = cscale(v.B0, ws);
+    double2 S1 = cscale(v.cS1, ws);
+    double2 M31 = cadd(D0, cmul(a.beta, N0));
+    double2 M32 = cneg(cmul(a.eps0, cadd(S0, cmul(a.beta, Ds0))));
+    if (FORM == BM_MIXED) {
+        double2 Ds1 = cscale(v.cD1, -dn_t * ws);
+        out[0] = cneg(S1);                      // M13
+        out[1] = cneg(cdiv(Ds1, a.eps1));       // M23
+        out[2] = M31;
+        out[3] = M32;
+    } else {
+        double2 D1 = cscale(v.cD1, dn_s * ws);
+        out[0] = M31;
+        out[1] = M32;
+        out[2] = D1;
+        out[3] = cneg(cmul(a.eps1, S1));
+    }
+}
+
+template <int FORM>
+__device__ __forceinline__ void diag_outputs(const AsmArgs& a, int i, double2 out[4]) {
+    const double* g = a.g;
+    int N = a.N;
+    double sp = g[4 * N + i], ka = g[5 * N + i], w = g[6 * N + i];
+    const double g_e = hk::EULER_GAMMA;
+    auto Sd = [&](double2 k) {
+        double2 hk2 = cscale(k, 0.5);
+        double2 L = hk::clog(hk2);
+        double re = -(L.x + g_e) / (2.0 * PI) - log(w / (2.0 * PI)) / (2.0 * PI);
+        double im = 0.25 - L.y / (2.0 * PI);
+        return make_double2(w * re, w * im);
+    };
+    double Dd = -ka * w / (4.0 * PI);
+    double lh = log(a.h / (2.0 * PI));
+    double2 k0sq = cmul(a.k0, a.k0);
+    double2 Nd = cadd(make_double2(-PI / (6.0 * a.h * sp), 0.0), cscale(k0sq, -lh * w / (4.0 * PI)));
+    double2 S0 = Sd(a.k0), S1 = Sd(a.k1);
+    double2 M31 = cadd(make_double2(Dd - 0.5, 0.0), cmul(a.beta, Nd));
+    double2 M32 = cneg(cmul(a.eps0, cadd(S0, cmul(a.beta, make_double2(Dd + 0.5, 0.0)))));
+    if (FORM == BM_MIXED) {
+        out[0] = cneg(S1);
+        out[1] = cneg(cdiv(make_double2(Dd + 0.5, 0.0), a.eps1));
+        out[2] = M31;
+        out[3] = M32;
+    } else {
+        out[0] = M31;
+        out[1] = M32;
+        out[2] = make_double2(Dd + 0.5, 0.0);
+        out[3] = cneg(cmul(a.eps1, S1));
+    }
+}
+
+constexpr int AT = 32;  // assembly tile
+constexpr int AY = 8;   // threads in y
+
+template <int FORM>
+__global__ void __launch_bounds__(AT* AY) assemble_kernel(AsmArgs a) {
+    extern __shared__ double2 st[];  // [4][AT][AT+1] staging of the transposed tile
+    // decode the upper-triangular tile pair (I <= J) from the linear block index
+    long idx = blockIdx.x;
+    long J = (long)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+    while (J * (J + 1) / 2 > idx) --J;
+    while ((J + 1) * (J + 2) / 2 <= idx) ++J;
+    long I = idx - J * (J + 1) / 2;
+    const int N = a.N;
+    const double* g = a.g;
+    int tx = threadIdx.x, ty = threadIdx.y;
+    int i = (int)I * AT + tx;
+    bool diag_tile = (I == J);
+    double xi = 0, yi = 0, nxi = 0, nyi = 0, wi = 0;
+    if (i < N) {
+        xi = g[i];
+        yi = g[N + i];
+        nxi = g[2 * N + i];
+        nyi = g[3 * N + i];
+        wi = g[6 * N + i];
+    }
+#pragma unroll 1
+    for (int q = 0; q < AT / AY; ++q) {
+        int jl = ty + AY * q;
+        int j = (int)J * AT + jl;
+        bool valid = (i < N) && (j < N);
+        double2 o1[4], o2[4];
+        if (valid) {
+            if (i == j) {
+                diag_outputs<FORM>(a, i, o1);
+            } else {
+                double xj = g[j], yj = g[N + j], nxj = g[2 * N + j], nyj = g[3 * N + j], wj = g[6 * N + j];
+                double dx = xi - xj, dy = yi - yj;
+                double dni = dx * nxi + dy * nyi, dnj = dx * nxj + dy * nyj, ninj = nxi * nxj + nyi * nyj;
+                PairVals v;
+                pair_vals(a, dx, dy, dni, dnj, ninj, v);
+                // (i, j): target i, source j
+                outputs<FORM>(a, v, dni, dnj, wj, o1);
+                if (!diag_tile) {
+                    // (j, i): d -> -d, target j (d.nu_j -> -dnj), source i (-dni)
+                    outputs<FORM>(a, v, -dnj, -dni, wi, o2);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) a.o[b][(long)i + (long)j * a.ld[b]] = o1[b];
+        }
+        if (!diag_tile) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) st[(b * AT + jl) * (AT + 1) + tx] = valid ? o2[b] : make_double2(0, 0);
+        }
+    }
+    if (diag_tile) return;
+    __syncthreads();
+    // write the transposed tile: entry (row j, col i); lanes run over j for coalescing
+#pragma unroll 1
+    for (int q = 0; q < AT / AY; ++q) {
+        int il = ty + AY * q;
+        int ii = (int)I * AT + il;
+        int jj = (int)J * AT + tx;
+        if (ii < N && jj < N) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) a.o[b][(long)jj + (long)ii * a.ld[b]] = st[(b * AT + tx) * (AT + 1) + il];
+        }
+    }
+}
+
+// row sums of |A| for ||A||_inf; rows of an m x ncols column-major block, plus `add` per row
+__device__ __forceinline__ void atomic_max_pos(double* p, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
+}
+__global__ void rownorm_kernel(const double2* __restrict__ A, long ld, int m, int ncols, double add, double* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (i < m) {
+        s = add;
+        for (int j = 0; j < ncols; ++j) {
+            double2 v = A[i + (long)j * ld];
+            s += hypot(v.x, v.y);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0 && s > 0) atomic_max_pos(out, s);
+}
+
+__global__ void plane_wave_kernel(const double* __restrict__ g, int N, double2 k0, double2 beta,
+                                  const double* __restrict__ ang, int nrhs, int form, double2* B, long ldb) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    int nsys = (form == BM_MIXED) ? 3 * N : 2 * N;
+    if (r >= nsys || c >= nrhs) return;
+    int off = (form == BM_MIXED) ? 2 * N : 0;
+    double2 val = make_double2(0.0, 0.0);
+    if (r >= off && r < off + N) {
+        int j = r - off;
+        double sa, ca;
+        sincos(ang[c], &sa, &ca);
+        double s = ca * g[j] + sa * g[N + j];
+        double dn = ca * g[2 * N + j] + sa * g[3 * N + j];
+        // u = exp(i k0 s), q = i k0 dn u
+        double e = exp(-k0.y * s), sn, cs;
+        sincos(k0.x * s, &sn, &cs);
+        double2 u = make_double2(e * cs, e * sn);
+        double2 q = cscale(cmul(cmuli(k0), u), dn);
+        val = cneg(cadd(u, cmul(beta, q)));
+    }
+    B[r + (long)c * ldb] = val;
+}
+
+// far field: one block per (angle m, column c)
+__global__ void far_field_kernel(const double* __restrict__ g, int N, double2 k0, double2 eps0,
+                                 const double2* __restrict__ X, long ldx, const double* __restrict__ ang, int M,
+                                 double2* U, long ldu) {
+    int m = blockIdx.x, c = blockIdx.y;
+    double sa, ca;
+    sincos(ang[m], &sa, &ca);
+    const double2* u = X + (long)c * ldx;
+    const double2* q = u + N;
+    double2 acc = make_double2(0, 0);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        double s = ca * g[j] + sa * g[N + j];
+        double xn = ca * g[2 * N + j] + sa * g[3 * N + j];
+        double w = g[6 * N + j];
+        // e = exp(-i k0 s)
+        double e = exp(k0.y * s), sn, cs;
+        sincos(-k0.x * s, &sn, &cs);
+        double2 ph = make_double2(e * cs, e * sn);
+        double2 t = cscale(cmul(cmuli(k0), u[j]), -xn);      // -i k0 (xhat.nu) u
+        t = csub(t, cmul(eps0, q[j]));
+        acc = cadd(acc, cscale(cmul(t, ph), w));
+    }
+    __shared__ double2 red[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        acc = lane < nw ? red[lane] : make_double2(0, 0);
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) {
+            // c0 = e^{i pi/4} / sqrt(8 pi k0)
+            double2 kk = hk::csqrt(cscale(k0, 8.0 * PI));
+            double2 c0 = cmul(make_double2(0.70710678118654752440, 0.70710678118654752440), cinv(kk));
+            U[m + (long)c * ldu] = cmul(c0, acc);
+        }
+    }
+}
+
+__global__ void hankel_probe_kernel(const double2* __restrict__ z, int n, HankelTable T, double2* h0, double2* h1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 a, b;
+    hk::hankel01(z[i], T, a, b);
+    h0[i] = a;
+    h1[i] = b;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Schur A operand: Mbot (N x 2N col-major FP64) -> row-major [N][ldk] planar FP32, segments
+// (3xTF32: [hi | hi | lo]); B operand: Mtop (2N x N) -> [N][ldk] with column n of Mtop as row n
+// (3xTF32: [hi | lo | hi]).  Padding columns [nseg*K, ldk) are zeroed.
+__global__ void pack_rowmajor_kernel(const double2* __restrict__ M, long ldm, int rows, int K, int split,
+                                     float* __restrict__ Pr, float* __restrict__ Pi, long ldk) {
+    __shared__ float2 t[32][33];
+    int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int q = ty; q < 32; q += 8) {
+        int r = r0 + tx, k = k0 + q;
+        double2 v = (r < rows && k < K) ? M[r + (long)k * ldm] : make_double2(0, 0);
+        t[q][tx] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
+    for (int q = ty; q < 32; q += 8) {
+        int r = r0 + q, k = k0 + tx;
+        if (r >= rows || k >= K) continue;
+        float2 v = t[tx][q];
+        long o = (long)r * ldk + k;
+        if (!split) {
+            Pr[o] = v.x;
+            Pi[o] = v.y;
+        } else {
+            float hr = tf32_rna(v.x), hi = tf32_rna(v.y);
+            Pr[o] = hr;
+            Pi[o] = hi;
+            Pr[o + K] = hr;
+            Pi[o + K] = hi;
+            Pr[o + 2 * K] = v.x - hr;
+            Pi[o + 2 * K] = v.y - hi;
+        }
+    }
+}
+
+__global__ void pack_colmajor_kernel(const double2* __restrict__ M, long ldm, int K, int cols, int split,
+                                     float* __restrict__ Pr, float* __restrict__ Pi, long ldk) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long kext = split ? 3L * K : (long)K;
+    long total = (long)cols * ldk;
+    if (idx >= total) return;
+    int n = (int)(idx / ldk);
+    long kk = idx - (long)n * ldk;
+    float vr = 0.f, vi = 0.f;
+    if (kk < kext) {
+        long k = kk % K;
+        int seg = (int)(kk / K);
+        double2 v = M[k + (long)n * ldm];
+        float fr = (float)v.x, fi = (float)v.y;
+        if (!split) {
+            vr = fr;
+            vi = fi;
+        } else {
+            float hr = tf32_rna(fr), hi = tf32_rna(fi);
+            if (seg == 1) {
+                vr = fr - hr;
+                vi = fi - hi;
+            } else {
+                vr = hr;
+                vi = hi;
+            }
+        }
+    }
+    Pr[idx] = vr;
+    Pi[idx] = vi;
+}
+
+__global__ void pad_zero_rows_kernel(float* Pr, float* Pi, long ldk, int rows, long kext) {
+    // zero the K padding [kext, ldk) of each row of a row-major pack
+    long pad = ldk - kext;
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pad <= 0 || idx >= (long)rows * pad) return;
+    long r = idx / pad, c = kext + idx % pad;
+    Pr[r * ldk + c] = 0.f;
+    Pi[r * ldk + c] = 0.f;
+}
+
+__global__ void to_c32_kernel(const double2* __restrict__ A, long lda, int m, int n, float* Fr, float* Fi, long ldf) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)m * n) return;
+    int j = (int)(idx / m), i = (int)(idx % m);
+    double2 v = A[i + (long)j * lda];
+    Fr[i + (long)j * ldf] = (float)v.x;
+    Fi[i + (long)j * ldf] = (float)v.y;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+cudaError_t launch_geometry(cudaStream_t s, int kind, const double p[4], int N, const double* d_user, double* d_geom) {
+    geom_kernel<<<ceil_div(N, 256), 256, 0, s>>>(kind, p[0], p[1], p[2], N, d_user, d_geom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c) {
+    AsmArgs a{};
+    a.N = c->N;
+    a.h = 2.0 * PI / c->N;
+    a.k0 = c->k0;
+    a.k1 = c->k1;
+    a.eps0 = c->eps0;
+    a.eps1 = c->eps1;
+    a.beta = c->beta;
+    a.T = c->htab;
+    a.g = c->d_geom;
+    long N = c->N;
+    if (c->form == BM_MIXED) {
+        a.o[0] = c->d_Mtop;
+        a.o[1] = c->d_Mtop + N;
+        a.o[2] = c->d_Mbot;
+        a.o[3] = c->d_Mbot + N * c->ldbot;
+        a.ld[0] = a.ld[1] = c->ldtop;
+        a.ld[2] = a.ld[3] = c->ldbot;
+    } else {
+        a.o[0] = c->d_A;
+        a.o[1] = c->d_A + N * c->ldA;
+        a.o[2] = c->d_A + N;
+        a.o[3] = c->d_A + N + N * c->ldA;
+        a.ld[0] = a.ld[1] = a.ld[2] = a.ld[3] = c->ldA;
+    }
+    long T = ceil_div(N, AT);
+    long nblk = T * (T + 1) / 2;
+    size_t smem = 4 * AT * (AT + 1) * sizeof(double2);
+    dim3 blk(AT, AY);
+    cudaError_t e;
+    if (c->form == BM_MIXED) {
+        e = cudaFuncSetAttribute(assemble_kernel<BM_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        assemble_kernel<BM_MIXED><<<(unsigned)nblk, blk, smem, s>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(assemble_kernel<BM_ORDINARY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        assemble_kernel<BM_ORDINARY><<<(unsigned)nblk, blk, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normA(cudaStream_t s, const bm_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->d_normA, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    if (c->form == BM_MIXED) {
+        rownorm_kernel<<<ceil_div(2 * c->N, 256), 256, 0, s>>>(c->d_Mtop, c->ldtop, 2 * c->N, c->N, 1.0, c->d_normA);
+        rownorm_kernel<<<ceil_div(c->N, 256), 256, 0, s>>>(c->d_Mbot, c->ldbot, c->N, 2 * c->N, 0.0, c->d_normA);
+    } else {
+        rownorm_kernel<<<ceil_div(2 * c->N, 256), 256, 0, s>>>(c->d_A, c->ldA, 2 * c->N, 2 * c->N, 0.0, c->d_normA);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane_wave(cudaStream_t s, const bm_ctx* c, const double* d_ang, int nrhs, double2* B, long ldb) {
+    dim3 grid(ceil_div(c->nsys, 256), nrhs);
+    plane_wave_kernel<<<grid, 256, 0, s>>>(c->d_geom, c->N, c->k0, c->beta, d_ang, nrhs, c->form, B, ldb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_far_field(cudaStream_t s, const bm_ctx* c, const double2* X, long ldx, int nrhs, const double* d_ang,
+                             int M, double2* U, long ldu) {
+    dim3 grid(M, nrhs);
+    far_field_kernel<<<grid, 256, 0, s>>>(c->d_geom, c->N, c->k0, c->eps0, X, ldx, d_ang, M, U, ldu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hankel_probe(cudaStream_t s, const bm_ctx* c, const double2* z, int n, double2* h0, double2* h1) {
+    hankel_probe_kernel<<<ceil_div(n, 128), 128, 0, s>>>(z, n, c->htab, h0, h1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_schur(cudaStream_t s, const bm_ctx* c, int split) {
+    int N = c->N;
+    int K = 2 * N;
+    dim3 blk(32, 8);
+    dim3 grid(ceil_div(K, 32), ceil_div(N, 32));
+    pack_rowmajor_kernel<<<grid, blk, 0, s>>>(c->d_Mbot, c->ldbot, N, K, split, c->d_Ap_r, c->d_Ap_i, c->ldk_schur);
+    long kext = split ? 3L * K : (long)K;
+    long padn = (long)N * (c->ldk_schur - kext);
+    if (padn > 0) pad_zero_rows_kernel<<<ceil_div(padn, 256), 256, 0, s>>>(c->d_Ap_r, c->d_Ap_i, c->ldk_schur, N, kext);
+    long total = (long)N * c->ldk_schur;
+    pack_colmajor_kernel<<<ceil_div(total, 256), 256, 0, s>>>(c->d_Mtop, c->ldtop, K, N, split, c->d_Bp_r, c->d_Bp_i,
+                                                               c->ldk_schur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_c32(cudaStream_t s, const double2* A, long lda, int m, int n, float* Fr, float* Fi, long ldf) {
+    long total = (long)m * n;
+    to_c32_kernel<<<ceil_div(total, 256), 256, 0, s>>>(A, lda, m, n, Fr, Fi, ldf);
+    return cudaGetLastError();
+}

@@ -1,0 +1,238 @@
+// Shared internals of the GB300 Burton-Miller library: complex helpers, matrix accessors,
+// launch helpers and the handle layout.  Not part of the public ABI (include/bm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+#include <map>
+
+#include "../../include/bm.h"
+
+#ifndef BM_HD
+#define BM_HD __host__ __device__ __forceinline__
+#endif
+
+// ---------------------------------------------------------------------------------------------
+// Complex arithmetic on double2 / float2 (interleaved re, im)
+// ---------------------------------------------------------------------------------------------
+BM_HD double2 cmk(double a, double b) { return make_double2(a, b); }
+BM_HD double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+BM_HD double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+BM_HD double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+BM_HD double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+BM_HD double2 cneg(double2 a) { return make_double2(-a.x, -a.y); }
+BM_HD double2 cmuli(double2 a) { return make_double2(-a.y, a.x); }  // i * a
+BM_HD double cnorm1(double2 a) { return fabs(a.x) + fabs(a.y); }
+BM_HD double2 cinv(double2 a) {
+    // 1/a with scaling (Smith's method)
+    if (fabs(a.x) >= fabs(a.y)) {
+        double r = a.y / a.x, d = a.x + a.y * r;
+        return make_double2(1.0 / d, -r / d);
+    } else {
+        double r = a.x / a.y, d = a.y + a.x * r;
+        return make_double2(r / d, -1.0 / d);
+    }
+}
+BM_HD double2 cdiv(double2 a, double2 b) { return cmul(a, cinv(b)); }
+// a += b * c
+BM_HD void cfma(double2& a, double2 b, double2 c) {
+    a.x = fma(b.x, c.x, fma(-b.y, c.y, a.x));
+    a.y = fma(b.x, c.y, fma(b.y, c.x, a.y));
+}
+
+BM_HD float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+BM_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+BM_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+BM_HD float cnorm1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+BM_HD float2 cinv(float2 a) {
+    if (fabsf(a.x) >= fabsf(a.y)) {
+        float r = a.y / a.x, d = a.x + a.y * r;
+        return make_float2(1.0f / d, -r / d);
+    } else {
+        float r = a.x / a.y, d = a.y + a.x * r;
+        return make_float2(r / d, -1.0f / d);
+    }
+}
+BM_HD void cfma(float2& a, float2 b, float2 c) {
+    a.x = fmaf(b.x, c.x, fmaf(-b.y, c.y, a.x));
+    a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
+}
+
+template <class R> struct cplx_of;
+template <> struct cplx_of<double> { using type = double2; };
+template <> struct cplx_of<float> { using type = float2; };
+template <class R> using cplx_t = typename cplx_of<R>::type;
+
+template <class R> BM_HD cplx_t<R> czero();
+template <> BM_HD double2 czero<double>() { return make_double2(0.0, 0.0); }
+template <> BM_HD float2 czero<float>() { return make_float2(0.f, 0.f); }
+
+// ---------------------------------------------------------------------------------------------
+// Column-major complex matrix views.
+//   Z64: FP64 interleaved (double2), element (i, j) at p[i + j*ld]
+//   C32: FP32 planar, element (i, j) at re[i + j*ld], im[i + j*ld]
+// Both expose get/set and a pointer offset to a sub-block.
+// ---------------------------------------------------------------------------------------------
+struct Z64 {
+    using real = double;
+    using cv = double2;
+    double2* p;
+    long ld;
+    BM_HD cv get(long i, long j) const { return p[i + j * ld]; }
+    BM_HD void set(long i, long j, cv v) const { p[i + j * ld] = v; }
+    BM_HD Z64 sub(long i, long j) const { return Z64{p + i + j * ld, ld}; }
+};
+struct C32 {
+    using real = float;
+    using cv = float2;
+    float* re;
+    float* im;
+    long ld;
+    BM_HD cv get(long i, long j) const { return make_float2(re[i + j * ld], im[i + j * ld]); }
+    BM_HD void set(long i, long j, cv v) const {
+        re[i + j * ld] = v.x;
+        im[i + j * ld] = v.y;
+    }
+    BM_HD C32 sub(long i, long j) const { return C32{re + i + j * ld, im + i + j * ld, ld}; }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Error handling
+// ---------------------------------------------------------------------------------------------
+void bm_set_error(const std::string& msg);
+#define BM_CUDA_TRY(expr)                                                                        \
+    do {                                                                                         \
+        cudaError_t _e = (expr);                                                                 \
+        if (_e != cudaSuccess) {                                                                 \
+            bm_set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                    \
+            return BM_ECUDA;                                                                     \
+        }                                                                                        \
+    } while (0)
+#define BM_TRY(expr)                                                                             \
+    do {                                                                                         \
+        bm_status _s = (expr);                                                                   \
+        if (_s != BM_OK) return _s;                                                              \
+    } while (0)
+
+static inline long pad32(long n) { return (n + 31) / 32 * 32; }
+static inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------------------------
+// Hankel anchor table (built on the host in double-double, see hankel_table.cpp)
+// ---------------------------------------------------------------------------------------------
+struct HankelTable {
+    const double2* h;  // [iy * nx + ix] -> {H0, H1} pairs (2 entries per anchor)
+    int nx, ny;
+    double re0, im0, step, inv_step;
+};
+// Builds (once per process) the host copy of the anchor table.
+const std::vector<double2>& hankel_anchor_host(int& nx, int& ny, double& re0, double& im0, double& step);
+
+// ---------------------------------------------------------------------------------------------
+// The handle
+// ---------------------------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct bm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    size_t held = 0;
+    std::map<void*, size_t> allocs;
+
+    HankelTable htab{};
+    double2* d_htab = nullptr;
+
+    // problem
+    bool assembled = false;
+    bool factored = false;
+    bool singular = false;
+    int N = 0;
+    int n = 0;          // system size factored by the dense LU: N (mixed, U33) or 2N (ordinary)
+    int nsys = 0;       // rows of the full system: 3N or 2N
+    int form = BM_MIXED;
+    int prec = BM_FP64;
+    double2 k0{}, k1{}, eps0{}, eps1{}, beta{};
+    double refine_tol = 1e-9;
+    int refine_maxit = 30;
+    int nb = 0;
+
+    // geometry (device, SoA of N each): x, y, nx, ny, speed, kappa, w
+    double* d_geom = nullptr;
+
+    // FP64 operator
+    //  mixed:    Mtop = [M13; M23] (2N x N, ld ldtop), Mbot = [M31 M32] (N x 2N, ld ldbot)
+    //  ordinary: A (2N x 2N, ld ldA)
+    double2* d_Mtop = nullptr;
+    double2* d_Mbot = nullptr;
+    long ldtop = 0, ldbot = 0;
+    double2* d_A = nullptr;
+    long ldA = 0;
+    double* d_normA = nullptr;  // ||A||_inf (device scalar)
+
+    // factorisation storage
+    double2* d_F64 = nullptr;  // FP64 LU (n x n, ld ldF)
+    float* d_F32r = nullptr;   // FP32 planar LU
+    float* d_F32i = nullptr;
+    long ldF = 0;
+    int* d_ipiv = nullptr;
+    int* d_perm = nullptr;
+    int* d_info = nullptr;
+    int* d_err = nullptr;
+    void* d_maps = nullptr;    // two row-interchange maps used by the factorisation
+    // inverted diagonal blocks of L and U (getrs), bs x bs each, n/bs blocks
+    void* d_dinvL = nullptr;
+    void* d_dinvU = nullptr;
+    int bs_solve = 64;
+
+    // tensor-core operand packs (FP32 planar, K-major, segments for 3xTF32)
+    float* d_Ap_r = nullptr;  // Schur A operand [M31 M32] (N rows x Kext)
+    float* d_Ap_i = nullptr;
+    float* d_Bp_r = nullptr;  // Schur B operand [M13; M23]^T rows (N rows x Kext)
+    float* d_Bp_i = nullptr;
+    long ldk_schur = 0;
+    int kseg_schur = 0;       // K of one segment (2N)
+    float* d_Lp_r = nullptr;  // LU trailing-update packs
+    float* d_Lp_i = nullptr;
+    float* d_Up_r = nullptr;
+    float* d_Up_i = nullptr;
+    long ldk_lu = 0;
+    float* d_O32r = nullptr;  // ordinary: FP32 copy of A is the LU buffer (d_F32*)
+
+    // solve workspace (sized for the largest nrhs seen)
+    int ws_nrhs = 0;
+    double2* d_X = nullptr;   // nsys x nrhs FP64 iterate
+    double2* d_R = nullptr;   // nsys x nrhs FP64 residual
+    double2* d_Bw = nullptr;  // nsys x nrhs FP64 copy of B
+    float* d_Wr = nullptr;    // FP32 planar work (nsys x nrhs) x 2
+    float* d_Wi = nullptr;
+    float* d_W2r = nullptr;
+    float* d_W2i = nullptr;
+    double2* d_Y64 = nullptr; // FP64 work for the FP64 solve
+    double2* d_Y64b = nullptr;
+    double* d_colred = nullptr;  // per-column reductions (4 x nrhs)
+
+    // cached graphs
+    cudaGraphExec_t g_factor = nullptr;
+    std::map<int, cudaGraphExec_t> g_solve;   // keyed by nrhs
+    std::map<int, cudaGraphExec_t> g_resid;
+
+    // tensor maps (opaque bytes, built on the host)
+    alignas(64) unsigned char tm_schur[4][128];
+    alignas(64) unsigned char tm_lu[4][128];
+    bool tm_ok = false;
+
+    // panel launch configuration
+    int panel_cluster = 0;   // max cluster size the device allows for the panel kernel
+};
+
+// allocation helpers (api.cu)
+bm_status ctx_alloc(bm_ctx* c, void** p, size_t bytes);
+void ctx_free(bm_ctx* c, void* p);

@@ -1,0 +1,308 @@
+// Complex GEMM on the 5th-generation tensor cores (sm_103a): C = beta C + alpha A B^T with
+// A (m x K) and B (n x K) given as K-major planar FP32 packs, computed in TF32 with FP32
+// accumulation in tensor memory.  This is the contraction of Theorem thm:LU
+// (U33 = -[M31 M32][M13; M23]) and of every LU trailing update A22 -= L21 U12.
+//
+// Complex product with four real products ("4M") on planar operands:
+//     Dr = Ar Br^T - Ai Bi^T,  Di = Ar Bi^T + Ai Br^T
+// Two TMEM accumulators (128 lanes x 128 columns each); the minus sign uses the A-negate bit of
+// the instruction descriptor.  The 3xTF32 variant needs no kernel change: its packs repeat the
+// K range as [A_hi | A_hi | A_lo] and [B_hi | B_lo | B_hi], so one K-extended product sums
+// A_hi B_hi + A_hi B_lo + A_lo B_hi.
+//
+// CTA tile 128 x 128, K step 32 (128-byte rows), 3-stage TMA -> shared-memory pipeline with
+// mbarriers.  Warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues tcgen05.mma; all four warps
+// then read the accumulators (tcgen05.ld 32x32b, warp w owns TMEM lanes 32w..32w+31 = rows)
+// and update C with coalesced column-major stores.  Every mbarrier wait is bounded (2 s by the
+// global timer); a timeout sets *err, skips the epilogue, waits for issued copies and frees TMEM.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+namespace {
+
+constexpr int BM = TC_BM, BN = TC_BN;
+constexpr int BKE = 32;  // K elements per stage (fp32: 128-byte rows, one swizzle span)
+constexpr int STAGES = 3;
+constexpr int TILE_A = BM * BKE * 4;
+constexpr int TILE_B = BN * BKE * 4;
+constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; returns false on timeout or when another thread already gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive fp32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M = 128, N = BN.
+__host__ __device__ constexpr uint32_t idesc_tf32(uint32_t neg_a) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (neg_a << 13) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmAr, const __grid_constant__ CUtensorMap tmAi,
+                    const __grid_constant__ CUtensorMap tmBr, const __grid_constant__ CUtensorMap tmBi,
+                    float* __restrict__ Cr, float* __restrict__ Ci, long ldc, int m, int n, int kext, float alpha,
+                    float beta, int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tm = blockIdx.x, tn = blockIdx.y;
+    const int nkb = (kext + BKE - 1) / BKE;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t Dr = tmem, Di = tmem + BN;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int issued = 0;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag)) break;
+            uint8_t* st = smem + s * STAGE_BYTES;
+            const uint32_t fb = full0 + 8 * s;
+            mbar_expect_tx(fb, STAGE_BYTES);
+            const int kx = kb * BKE;
+            tma_load_2d(smem_u32(st), &tmAr, fb, kx, tm * BM);
+            tma_load_2d(smem_u32(st + TILE_A), &tmAi, fb, kx, tm * BM);
+            tma_load_2d(smem_u32(st + 2 * TILE_A), &tmBr, fb, kx, tn * BN);
+            tma_load_2d(smem_u32(st + 2 * TILE_A + TILE_B), &tmBi, fb, kx, tn * BN);
+            issued = kb + 1;
+        }
+        if (*abort_flag) {
+            // let copies already in flight land before shared memory is released
+            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+                const uint64_t t0 = gtimer();
+                while (!mbar_try(full0 + 8 * (kb % STAGES), (uint32_t)(kb / STAGES) & 1u) && gtimer() - t0 < WAIT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idp = idesc_tf32(0), idn = idesc_tf32(1);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(full0 + 8 * s, ph, abort_flag)) break;
+            fence_after();
+            const uint32_t ar = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t ai = ar + TILE_A, br = ar + 2 * TILE_A, bi = br + TILE_B;
+#pragma unroll
+            for (int kk = 0; kk < BKE / 8; ++kk) {
+                const uint32_t off = kk * 32;  // 8 tf32 = 32 bytes along K inside the swizzle span
+                const uint64_t dar = desc_sw128(ar + off), dai = desc_sw128(ai + off);
+                const uint64_t dbr = desc_sw128(br + off), dbi = desc_sw128(bi + off);
+                const uint32_t acc = (kb | kk) ? 1u : 0u;
+                mma_tf32(Dr, dar, dbr, idp, acc);
+                mma_tf32(Dr, dai, dbi, idn, 1u);
+                mma_tf32(Di, dar, dbi, idp, acc);
+                mma_tf32(Di, dai, dbr, idp, 1u);
+            }
+            mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(done);
+    }
+    __syncwarp();
+    // ---------------- epilogue: all four warps ----------------
+    mbar_wait(done, 0, abort_flag);
+    fence_before();
+    __syncthreads();  // the abort decision below must be uniform: tcgen05.ld is warp-synchronous
+    fence_after();
+    if (!*abort_flag) {
+        const long row = (long)tm * BM + warp * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float vr[16], vi[16];
+            tmem_ld16(Dr + lane_off + c0, vr);
+            tmem_ld16(Di + lane_off + c0, vi);
+            if (row < m) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const long col = (long)tn * BN + c0 + q;
+                    if (col < n) {
+                        const long o = row + col * ldc;
+                        float r = alpha * vr[q], im = alpha * vi[q];
+                        if (beta != 0.f) {
+                            r += beta * Cr[o];
+                            im += beta * Ci[o];
+                        }
+                        Cr[o] = r;
+                        Ci[o] = im;
+                    }
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (fn == nullptr) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+// 2-D tensor map over a row-major [rows][ldk] FP32 pack: dims {kext, rows}, box {32, box_rows},
+// 128-byte swizzle; reads outside {kext, rows} return zeros.
+bm_status tc_make_map(void* tmap, const float* base, long rows, long kext, long ldk, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
+    if (enc == nullptr) {
+        bm_set_error("cuTensorMapEncodeTiled is unavailable from the driver");
+        return BM_ECUDA;
+    }
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ldk * 4) % 16 != 0) {
+        bm_set_error("tensor map: base or stride not 16-byte aligned");
+        return BM_EINVAL;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)kext, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ldk * 4};
+    cuuint32_t box[2] = {(cuuint32_t)BKE, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap*>(tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base),
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        bm_set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+        return BM_ECUDA;
+    }
+    return BM_OK;
+}
+
+cudaError_t gemm_tc(cudaStream_t s, const void* tAr, const void* tAi, const void* tBr, const void* tBi, float* Cr,
+                    float* Ci, long ldc, int m, int n, int kext, float alpha, float beta, int* d_err) {
+    if (m <= 0 || n <= 0 || kext <= 0) return cudaSuccess;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid(ceil_div(m, BM), ceil_div(n, BN));
+    cgemm_tc_kernel<<<grid, 128, SMEM_BYTES, s>>>(*reinterpret_cast<const CUtensorMap*>(tAr),
+                                                  *reinterpret_cast<const CUtensorMap*>(tAi),
+                                                  *reinterpret_cast<const CUtensorMap*>(tBr),
+                                                  *reinterpret_cast<const CUtensorMap*>(tBi), Cr, Ci, ldc, m, n, kext,
+                                                  alpha, beta, d_err);
+    return cudaGetLastError();
+}

@@ -1,0 +1,142 @@
+// Device evaluation of the Hankel functions H0^(1)(z), H1^(1)(z) for complex z, Re z > 0
+// (principal branch), in FP64.  These build every kernel of section 2.2:
+// G = (i/4) H0^(1)(k r) and its normal derivatives (H0' = -H1).
+//
+// Three zones by |z|, each accurate to about 1e-14 relative in |H|:
+//  * |z| < 3    : ascending series of J0, J1, Y0, Y1 (16 terms; (|z|^2/4)^m/(m!)^2 < 1e-18).
+//  * 3 <= |z| < 20 : Taylor expansion about the nearest anchor z0 of a grid with spacing 1/4
+//    (|z - z0| <= 0.177).  The Taylor coefficients of H0 about z0 follow from Bessel's equation
+//    z^2 y'' + z y' + z^2 y = 0 written in delta = z - z0:
+//       z0^2 (k+1)(k+2) a_{k+2} = -[ z0 (k+1)(2k+1) a_{k+1} + (k^2 + z0^2) a_k
+//                                    + 2 z0 a_{k-1} + a_{k-2} ],
+//    a_0 = H0(z0), a_1 = -H1(z0); H1(z) = -H0'(z) is the differentiated series.  The anchors
+//    come from the table built on the host (ODE integration in double-double).
+//  * |z| >= 20  : Hankel's asymptotic expansion
+//       H_nu(z) ~ sqrt(2/(pi z)) e^{i(z - nu pi/2 - pi/4)} sum_k i^k a_k(nu) / z^k,
+//       a_k(nu) = prod_{j=1..k} (4nu^2 - (2j-1)^2) / (k! 8^k),
+//    summed until the terms fall below 1e-17 (at most 40 terms; about 20 at |z| = 20).
+#pragma once
+#include "common.cuh"
+
+namespace hk {
+
+constexpr double R_SERIES = 3.0;
+constexpr double R_ASYM = 20.0;
+constexpr double EULER_GAMMA = 0.57721566490153286060651209008240243;
+constexpr double TWO_OVER_PI = 0.63661977236758134307553505349005745;
+constexpr double ONE_OVER_PI = 0.31830988618379067153776752674502872;
+constexpr double PI_4 = 0.78539816339744830961566084581987572;
+
+__device__ __forceinline__ double2 clog(double2 z) {
+    return make_double2(log(hypot(z.x, z.y)), atan2(z.y, z.x));
+}
+
+// principal square root
+__device__ __forceinline__ double2 csqrt(double2 w) {
+    double m = hypot(w.x, w.y);
+    if (m == 0.0) return make_double2(0.0, 0.0);
+    double s = sqrt(0.5 * (m + fabs(w.x)));
+    if (w.x >= 0.0) return make_double2(s, w.y / (2.0 * s));
+    return make_double2(fabs(w.y) / (2.0 * s), copysign(s, w.y));
+}
+
+__device__ __forceinline__ void series(double2 z, double2& h0, double2& h1) {
+    // w = -z^2/4; t0_m = w^m/(m!)^2, t1_m = w^m/(m!(m+1)!)
+    double2 w = cscale(cmul(z, z), -0.25);
+    double2 t0 = make_double2(1.0, 0.0), t1 = make_double2(1.0, 0.0);
+    double2 J0 = t0, J1 = t1;
+    double2 S0 = make_double2(0.0, 0.0);                      // sum H_m t0_m
+    double2 S1 = cscale(t1, -2.0 * EULER_GAMMA + 1.0);        // sum (psi(m+1)+psi(m+2)) t1_m, m = 0 term
+    double Hm = 0.0;
+#pragma unroll
+    for (int m = 1; m < 16; ++m) {
+        double dm = (double)m;
+        t0 = cscale(cmul(t0, w), 1.0 / (dm * dm));
+        t1 = cscale(cmul(t1, w), 1.0 / (dm * (dm + 1.0)));
+        Hm += 1.0 / dm;
+        J0 = cadd(J0, t0);
+        J1 = cadd(J1, t1);
+        S0 = cadd(S0, cscale(t0, Hm));
+        S1 = cadd(S1, cscale(t1, -2.0 * EULER_GAMMA + 2.0 * Hm + 1.0 / (dm + 1.0)));
+    }
+    double2 zh = cscale(z, 0.5);
+    J1 = cmul(J1, zh);
+    double2 L = clog(zh);
+    // Y0 = (2/pi)(ln(z/2) + gamma) J0 - (2/pi) S0
+    double2 Y0 = csub(cscale(cmul(make_double2(L.x + EULER_GAMMA, L.y), J0), TWO_OVER_PI), cscale(S0, TWO_OVER_PI));
+    // Y1 = -2/(pi z) + (2/pi) ln(z/2) J1 - (1/pi)(z/2) S1
+    double2 Y1 = cscale(cinv(z), -TWO_OVER_PI);
+    Y1 = cadd(Y1, cscale(cmul(L, J1), TWO_OVER_PI));
+    Y1 = csub(Y1, cscale(cmul(zh, S1), ONE_OVER_PI));
+    h0 = make_double2(J0.x - Y0.y, J0.y + Y0.x);  // J0 + i Y0
+    h1 = make_double2(J1.x - Y1.y, J1.y + Y1.x);
+}
+
+__device__ __forceinline__ void taylor(double2 z, const HankelTable& T, double2& h0, double2& h1) {
+    int ix = __double2int_rn((z.x - T.re0) * T.inv_step);
+    int iy = __double2int_rn((z.y - T.im0) * T.inv_step);
+    ix = min(max(ix, 0), T.nx - 1);
+    iy = min(max(iy, 0), T.ny - 1);
+    double2 z0 = make_double2(T.re0 + ix * T.step, T.im0 + iy * T.step);
+    const double2* a = T.h + 2 * ((long)iy * T.nx + ix);
+    double2 a0 = __ldg(a), H1z0 = __ldg(a + 1);
+    double2 d = csub(z, z0);
+    double2 z0sq = cmul(z0, z0);
+    double2 iz2 = cinv(z0sq);
+    double2 am2 = make_double2(0.0, 0.0), am1 = make_double2(0.0, 0.0);
+    double2 ak = a0, ak1 = cneg(H1z0);
+    double2 s0 = cadd(a0, cmul(ak1, d));     // H0 partial sum
+    double2 s1 = ak1;                         // H0' partial sum
+    double2 dk = d;                           // d^(k+1)
+    for (int k = 0; k < 40; ++k) {
+        double dk_ = (double)k;
+        // bracket = z0 (k+1)(2k+1) a_{k+1} + (k^2 + z0^2) a_k + 2 z0 a_{k-1} + a_{k-2}
+        double2 br = cscale(cmul(z0, ak1), (dk_ + 1.0) * (2.0 * dk_ + 1.0));
+        br = cadd(br, cmul(make_double2(z0sq.x + dk_ * dk_, z0sq.y), ak));
+        br = cadd(br, cscale(cmul(z0, am1), 2.0));
+        br = cadd(br, am2);
+        double2 an = cscale(cmul(br, iz2), -1.0 / ((dk_ + 1.0) * (dk_ + 2.0)));
+        double2 t1 = cscale(cmul(an, dk), dk_ + 2.0);   // (k+2) a_{k+2} d^(k+1)
+        dk = cmul(dk, d);                                // d^(k+2)
+        double2 t0 = cmul(an, dk);
+        s0 = cadd(s0, t0);
+        s1 = cadd(s1, t1);
+        am2 = am1;
+        am1 = ak;
+        ak = ak1;
+        ak1 = an;
+        if (cnorm1(t0) <= 1e-17 * cnorm1(s0) && cnorm1(t1) <= 1e-17 * cnorm1(s1)) break;
+    }
+    h0 = s0;
+    h1 = cneg(s1);
+}
+
+__device__ __forceinline__ void asym(double2 z, double2& h0, double2& h1) {
+    double2 w = cmuli(cinv(z));  // i/z
+    double2 t0 = make_double2(1.0, 0.0), t1 = t0, s0 = t0, s1 = t0;
+    for (int k = 1; k < 40; ++k) {
+        double o = (double)(2 * k - 1);
+        t0 = cscale(cmul(t0, w), (0.0 - o * o) / (8.0 * k));
+        t1 = cscale(cmul(t1, w), (4.0 - o * o) / (8.0 * k));
+        s0 = cadd(s0, t0);
+        s1 = cadd(s1, t1);
+        if (cnorm1(t0) <= 1e-17 * cnorm1(s0) && cnorm1(t1) <= 1e-17 * cnorm1(s1)) break;
+    }
+    // c = sqrt(2/(pi z)) * exp(i (z - pi/4))
+    double2 c = csqrt(cscale(cinv(z), TWO_OVER_PI));
+    double sn, cs;
+    sincos(z.x - PI_4, &sn, &cs);
+    double e = exp(-z.y);
+    c = cmul(c, make_double2(e * cs, e * sn));
+    h0 = cmul(c, s0);
+    h1 = cneg(cmuli(cmul(c, s1)));  // -i c s1
+}
+
+__device__ __forceinline__ void hankel01(double2 z, const HankelTable& T, double2& h0, double2& h1) {
+    double r = hypot(z.x, z.y);
+    if (r < R_SERIES) series(z, h0, h1);
+    else if (r < R_ASYM) taylor(z, T, h0, h1);
+    else asym(z, h0, h1);
+}
+
+}  // namespace hk

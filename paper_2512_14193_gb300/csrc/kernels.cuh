@@ -1,0 +1,44 @@
+// Launchers shared between the library's translation units (internal).
+#pragma once
+#include "common.cuh"
+
+// assemble.cu
+cudaError_t launch_geometry(cudaStream_t s, int kind, const double p[4], int N, const double* d_user, double* d_geom);
+cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c);
+cudaError_t launch_normA(cudaStream_t s, const bm_ctx* c);
+cudaError_t launch_plane_wave(cudaStream_t s, const bm_ctx* c, const double* d_ang, int nrhs, double2* B, long ldb);
+cudaError_t launch_far_field(cudaStream_t s, const bm_ctx* c, const double2* X, long ldx, int nrhs, const double* d_ang,
+                             int M, double2* U, long ldu);
+cudaError_t launch_hankel_probe(cudaStream_t s, const bm_ctx* c, const double2* z, int n, double2* h0, double2* h1);
+cudaError_t launch_pack_schur(cudaStream_t s, const bm_ctx* c, int split);
+cudaError_t launch_to_c32(cudaStream_t s, const double2* A, long lda, int m, int n, float* Fr, float* Fi, long ldf);
+
+// gemm_simt.cu
+cudaError_t gemm_z64(cudaStream_t s, int m, int n, int k, double alpha, Z64 A, bool a_trans, Z64 B, double beta, Z64 C);
+cudaError_t gemm_c32(cudaStream_t s, int m, int n, int k, float alpha, C32 A, bool a_trans, C32 B, float beta, C32 C);
+
+// gemm_tc.cu (tensor maps are CUtensorMap, passed as opaque 128-byte blobs)
+bm_status tc_make_map(void* tmap, const float* base, long rows, long kext, long ldk, int box_rows);
+cudaError_t gemm_tc(cudaStream_t s, const void* tAr, const void* tAi, const void* tBr, const void* tBi, float* Cr,
+                    float* Ci, long ldc, int m, int n, int kext, float alpha, float beta, int* d_err);
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 128;
+
+// lu.cu
+bm_status lu_setup(bm_ctx* c);
+bm_status lu_factor_enqueue(bm_ctx* c);       // factor d_F64 / d_F32 in place (stream-ordered)
+size_t swap_map_bytes();
+bm_status getrs_z64(bm_ctx* c, double2* Y, long ldy, int nrhs);   // in place; Y holds P B (rows gathered by perm)
+bm_status getrs_c32(bm_ctx* c, float* Yr, float* Yi, long ldy, int nrhs);
+cudaError_t launch_gather_rows_z64(cudaStream_t s, const int* perm, int n, int nrhs, const double2* B, long ldb,
+                                   double2* Y, long ldy);
+cudaError_t launch_gather_rows_c32(cudaStream_t s, const int* perm, int n, int nrhs, const float* Br, const float* Bi,
+                                   long ldb, float* Yr, float* Yi, long ldy);
+
+// solve.cu
+bm_status solve_fp64(bm_ctx* c, const double2* B, double2* X, long ld, int nrhs);
+bm_status residual_fp64(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs);
+bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const double2* B, long ld, int nrhs,
+                         double* d_eta);
+bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int nrhs);
+cudaError_t launch_copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd);

@@ -1,0 +1,241 @@
+// Solves with the factored system, FP64 residuals and iterative refinement.
+//
+// Mixed system, arbitrary 3N right-hand sides (Corollary lem:for_ssm_RHS):
+//     z3 = U33^{-1} (b3 - M31 b1 - M32 b2),  x1 = b1 - M13 z3,  x2 = b2 - M23 z3,  x3 = z3
+// with [M31 M32] and [M13; M23] each applied as one product (K = 2N and M = 2N).
+// Ordinary system: x = A^{-1} b by the LU of the 2N matrix.
+//
+// CF32 precisions: the correction solve above runs in FP32 with the FP32 factors and the FP32
+// operand packs; the residual r = b - A x uses the FP64 assembled operator (structured for the
+// mixed system: r1 = b1 - x1 - M13 x3, r2 = b2 - x2 - M23 x3, r3 = b3 - M31 x1 - M32 x2) and
+// x += A32^{-1} r repeats until the normwise backward error
+//     eta = max_c ||r_c||_inf / (||A||_inf ||x_c||_inf + ||b_c||_inf)
+// is at most refine_tol.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace {
+
+__global__ void resid_init_kernel(const double2* __restrict__ B, const double2* __restrict__ X, long ld, int nsys,
+                                  int nsub, int nrhs, double2* __restrict__ R) {
+    // R = B - X on rows [0, nsub) (identity blocks), R = B elsewhere
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nsys * nrhs) return;
+    int c = (int)(idx / nsys), i = (int)(idx % nsys);
+    long o = i + (long)c * ld;
+    double2 v = B[o];
+    if (i < nsub) v = csub(v, X[o]);
+    R[o] = v;
+}
+
+__device__ __forceinline__ void atomic_max_pos(double* p, double v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
+}
+
+// per column: eta_c = max|R| / (normA max|X| + max|B|); out[0] = max_c eta_c, out[1] = 1 if any
+// non-finite value was seen in B (the input check)
+__global__ void eta_kernel(const double2* __restrict__ R, const double2* __restrict__ X,
+                           const double2* __restrict__ B, long ld, int nsys, const double* __restrict__ normA,
+                           double* out) {
+    int c = blockIdx.x;
+    double r = 0, x = 0, b = 0;
+    bool bad = false;
+    for (int i = threadIdx.x; i < nsys; i += blockDim.x) {
+        long o = i + (long)c * ld;
+        double2 bv = B[o];
+        if (!isfinite(bv.x) || !isfinite(bv.y)) bad = true;
+        r = fmax(r, hypot(R[o].x, R[o].y));
+        x = fmax(x, hypot(X[o].x, X[o].y));
+        b = fmax(b, hypot(bv.x, bv.y));
+    }
+    __shared__ double sr[32], sx[32], sb[32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (bad) sbad = 1;
+    for (int o = 16; o > 0; o >>= 1) {
+        r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+        x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sr[w] = r;
+        sx[w] = x;
+        sb[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = blockDim.x >> 5;
+        for (int q = 1; q < nw; ++q) {
+            r = fmax(r, sr[q]);
+            x = fmax(x, sx[q]);
+            b = fmax(b, sb[q]);
+        }
+        r = fmax(r, sr[0]);
+        x = fmax(x, sx[0]);
+        b = fmax(b, sb[0]);
+        double den = (*normA) * x + b;
+        double eta = (den > 0) ? r / den : (r > 0 ? 1.0 : 0.0);
+        if (!isfinite(eta)) eta = 1e300;
+        atomic_max_pos(out, eta);
+        if (sbad) out[1] = 1.0;
+    }
+}
+
+__global__ void to_c32_kernel(const double2* __restrict__ A, long lda, int m, int n, float* __restrict__ Fr,
+                              float* __restrict__ Fi, long ldf) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)m * n) return;
+    int j = (int)(idx / m), i = (int)(idx % m);
+    double2 v = A[i + (long)j * lda];
+    Fr[i + (long)j * ldf] = (float)v.x;
+    Fi[i + (long)j * ldf] = (float)v.y;
+}
+
+// X[r0 + i, c] += D[i, c]
+__global__ void add_c32_kernel(double2* __restrict__ X, long ldx, int r0, int m, int n, const float* __restrict__ Dr,
+                               const float* __restrict__ Di, long ldd) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)m * n) return;
+    int j = (int)(idx / m), i = (int)(idx % m);
+    double2& x = X[r0 + i + (long)j * ldx];
+    x.x += (double)Dr[i + (long)j * ldd];
+    x.y += (double)Di[i + (long)j * ldd];
+}
+
+__global__ void copy_z64_kernel(const double2* __restrict__ S, long lds, int m, int n, double2* __restrict__ D,
+                                long ldd) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)m * n) return;
+    int j = (int)(idx / m), i = (int)(idx % m);
+    D[i + (long)j * ldd] = S[i + (long)j * lds];
+}
+
+#define SV_CUDA(expr)                                                                                  \
+    do {                                                                                               \
+        cudaError_t _e = (expr);                                                                       \
+        if (_e != cudaSuccess) {                                                                       \
+            bm_set_error(std::string("solve: ") + #expr + ": " + cudaGetErrorString(_e));              \
+            return BM_ECUDA;                                                                           \
+        }                                                                                              \
+    } while (0)
+
+cudaError_t copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd) {
+    long t = (long)m * n;
+    if (t == 0) return cudaSuccess;
+    copy_z64_kernel<<<ceil_div(t, 256), 256, 0, s>>>(S, lds, m, n, D, ldd);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Direct FP64 solve: X = A^{-1} B (B, X: nsys x nrhs with leading dimension ld, device).
+bm_status solve_fp64(bm_ctx* c, const double2* B, double2* X, long ld, int nrhs) {
+    cudaStream_t s = c->stream;
+    const int N = c->N;
+    const long ldy = c->n;
+    if (c->form == BM_MIXED) {
+        // t3 = b3 - [M31 M32] [b1; b2]
+        SV_CUDA(copy_z64(s, B + 2 * N, ld, N, nrhs, c->d_Y64b, ldy));
+        SV_CUDA(gemm_z64(s, N, nrhs, 2 * N, -1.0, Z64{c->d_Mbot, c->ldbot}, false, Z64{const_cast<double2*>(B), ld},
+                         1.0, Z64{c->d_Y64b, ldy}));
+        SV_CUDA(launch_gather_rows_z64(s, c->d_perm, N, nrhs, c->d_Y64b, ldy, c->d_Y64, ldy));
+        BM_TRY(getrs_z64(c, c->d_Y64, ldy, nrhs));
+        SV_CUDA(copy_z64(s, c->d_Y64, ldy, N, nrhs, X + 2 * N, ld));
+        // [x1; x2] = [b1; b2] - [M13; M23] z3
+        SV_CUDA(copy_z64(s, B, ld, 2 * N, nrhs, X, ld));
+        SV_CUDA(gemm_z64(s, 2 * N, nrhs, N, -1.0, Z64{c->d_Mtop, c->ldtop}, false, Z64{X + 2 * N, ld}, 1.0,
+                         Z64{X, ld}));
+    } else {
+        SV_CUDA(launch_gather_rows_z64(s, c->d_perm, c->n, nrhs, B, ld, c->d_Y64, ldy));
+        BM_TRY(getrs_z64(c, c->d_Y64, ldy, nrhs));
+        SV_CUDA(copy_z64(s, c->d_Y64, ldy, c->n, nrhs, X, ld));
+    }
+    return BM_OK;
+}
+
+// R = B - A X with the FP64 assembled operator.
+bm_status residual_fp64(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs) {
+    cudaStream_t s = c->stream;
+    const int N = c->N;
+    long t = (long)c->nsys * nrhs;
+    int nsub = (c->form == BM_MIXED) ? 2 * N : 0;
+    resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
+    SV_CUDA(cudaGetLastError());
+    if (c->form == BM_MIXED) {
+        SV_CUDA(gemm_z64(s, 2 * N, nrhs, N, -1.0, Z64{c->d_Mtop, c->ldtop}, false,
+                         Z64{const_cast<double2*>(X) + 2 * N, ld}, 1.0, Z64{R, ld}));
+        SV_CUDA(gemm_z64(s, N, nrhs, 2 * N, -1.0, Z64{c->d_Mbot, c->ldbot}, false, Z64{const_cast<double2*>(X), ld},
+                         1.0, Z64{R + 2 * N, ld}));
+    } else {
+        SV_CUDA(gemm_z64(s, 2 * N, nrhs, 2 * N, -1.0, Z64{c->d_A, c->ldA}, false, Z64{const_cast<double2*>(X), ld},
+                         1.0, Z64{R, ld}));
+    }
+    return BM_OK;
+}
+
+// d_eta[0] = backward error (max over columns), d_eta[1] = non-finite flag of B
+bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const double2* B, long ld, int nrhs,
+                         double* d_eta) {
+    SV_CUDA(cudaMemsetAsync(d_eta, 0, 2 * sizeof(double), c->stream));
+    eta_kernel<<<nrhs, 256, 0, c->stream>>>(R, X, B, ld, c->nsys, c->d_normA, d_eta);
+    SV_CUDA(cudaGetLastError());
+    return BM_OK;
+}
+
+// X += A32^{-1} R (FP32 correction solve with the FP32 factors and packs).
+bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int nrhs) {
+    cudaStream_t s = c->stream;
+    const int N = c->N;
+    const long ldw = c->nsys;
+    float* Wr = c->d_Wr;
+    float* Wi = c->d_Wi;
+    float* Vr = c->d_W2r;
+    float* Vi = c->d_W2i;
+    const long ldv = c->n;
+    long t = (long)c->nsys * nrhs;
+    to_c32_kernel<<<ceil_div(t, 256), 256, 0, s>>>(R, ld, c->nsys, nrhs, Wr, Wi, ldw);
+    SV_CUDA(cudaGetLastError());
+    const bool split = (c->prec == BM_CF32_3XTF32_IR);
+    if (c->form == BM_MIXED) {
+        const int K = 2 * N;
+        // W3 -= [M31 M32] [W1; W2]   (A operand pack is row-major: pass it as its transpose)
+        C32 Ahi{c->d_Ap_r, c->d_Ap_i, c->ldk_schur};
+        C32 W12{Wr, Wi, ldw};
+        C32 W3{Wr + 2 * N, Wi + 2 * N, ldw};
+        SV_CUDA(gemm_c32(s, N, nrhs, K, -1.0f, Ahi, true, W12, 1.0f, W3));
+        if (split) {
+            C32 Alo{c->d_Ap_r + 2 * K, c->d_Ap_i + 2 * K, c->ldk_schur};
+            SV_CUDA(gemm_c32(s, N, nrhs, K, -1.0f, Alo, true, W12, 1.0f, W3));
+        }
+        SV_CUDA(launch_gather_rows_c32(s, c->d_perm, N, nrhs, Wr + 2 * N, Wi + 2 * N, ldw, Vr, Vi, ldv));
+        BM_TRY(getrs_c32(c, Vr, Vi, ldv, nrhs));
+        // [W1; W2] -= [M13; M23] z3 (B operand pack is column-major [M13; M23])
+        C32 Bhi{c->d_Bp_r, c->d_Bp_i, c->ldk_schur};
+        C32 Z{Vr, Vi, ldv};
+        SV_CUDA(gemm_c32(s, K, nrhs, N, -1.0f, Bhi, false, Z, 1.0f, W12));
+        if (split) {
+            C32 Blo{c->d_Bp_r + K, c->d_Bp_i + K, c->ldk_schur};
+            SV_CUDA(gemm_c32(s, K, nrhs, N, -1.0f, Blo, false, Z, 1.0f, W12));
+        }
+        long t2 = (long)K * nrhs;
+        add_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(X, ld, 0, K, nrhs, Wr, Wi, ldw);
+        long t3 = (long)N * nrhs;
+        add_c32_kernel<<<ceil_div(t3, 256), 256, 0, s>>>(X, ld, 2 * N, N, nrhs, Vr, Vi, ldv);
+        SV_CUDA(cudaGetLastError());
+    } else {
+        SV_CUDA(launch_gather_rows_c32(s, c->d_perm, c->n, nrhs, Wr, Wi, ldw, Vr, Vi, ldv));
+        BM_TRY(getrs_c32(c, Vr, Vi, ldv, nrhs));
+        long t2 = (long)c->n * nrhs;
+        add_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(X, ld, 0, c->n, nrhs, Vr, Vi, ldv);
+        SV_CUDA(cudaGetLastError());
+    }
+    return BM_OK;
+}
+
+cudaError_t launch_copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd) {
+    return copy_z64(s, S, lds, m, n, D, ldd);
+}
