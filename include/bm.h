@@ -178,6 +178,21 @@ bm_status bm_hankel01(bm_ctx* ctx, const bm_c64* z, int n, bm_c64* h0, bm_c64* h
 bm_status bm_hankel_anchor_table(double* out, int cap_anchors, int* nx, int* ny, double* re0, double* im0,
                                  double* step);
 
+/* Timing probe: enqueue `reps` launches of one hot kernel on the handle's stream and return
+ * without synchronising, so a caller can bracket them with its own events on that stream.
+ *  which = BM_PROBE_SCHUR   : the Schur-complement product U33 = -[M31 M32][M13; M23] of
+ *                             Theorem thm:LU (mixed system; tensor cores for the CF32 precisions,
+ *                             FP64 CUDA cores for BM_FP64).  It overwrites U33, so the handle
+ *                             returns to the assembled-but-not-factored state.
+ *  which = BM_PROBE_RESIDUAL: the FP64 residual r = b - A x of the last bm_solve (same nrhs).
+ * Errors: BM_ESTATE (nothing assembled / solved yet), BM_EINVAL. */
+enum { BM_PROBE_SCHUR = 0, BM_PROBE_RESIDUAL = 1 };
+bm_status bm_enqueue_probe(bm_ctx* ctx, int which, int reps);
+
+/* Number of CUDA kernels this handle has launched so far (kernel nodes of every replayed CUDA
+ * graph plus kernels launched outside graphs). */
+bm_status bm_kernel_launches(bm_ctx* ctx, unsigned long long* count);
+
 /* Device bytes the handle currently holds, and its budget. */
 bm_status bm_memory(bm_ctx* ctx, size_t* held_bytes, size_t* budget_bytes);
 

@@ -23,6 +23,7 @@ BM_OK, BM_EINVAL, BM_ENOMEM, BM_ESINGULAR, BM_ENOTCONV, BM_ENONFINITE, BM_ETIMEO
 BM_MIXED, BM_ORDINARY = 0, 1
 BM_FP64, BM_CF32_TF32_IR, BM_CF32_3XTF32_IR = 0, 1, 2
 BM_CURVE_CIRCLE, BM_CURVE_ELLIPSE, BM_CURVE_STAR, BM_CURVE_KITE, BM_CURVE_USER = range(5)
+BM_PROBE_SCHUR, BM_PROBE_RESIDUAL = 0, 1
 
 
 class bm_c64(C.Structure):
@@ -74,13 +75,16 @@ def lib():
     L.bm_hankel_anchor_table.argtypes = [C.POINTER(D), I, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(D),
                                          C.POINTER(D)]
     L.bm_memory.argtypes = [P, C.POINTER(S), C.POINTER(S)]
+    L.bm_kernel_launches.argtypes = [P, C.POINTER(C.c_ulonglong)]
+    L.bm_enqueue_probe.argtypes = [P, I, I]
     L.bm_destroy.argtypes = [P]
     L.bm_strerror.argtypes = [I]
     L.bm_strerror.restype = C.c_char_p
     L.bm_last_error.argtypes = []
     L.bm_last_error.restype = C.c_char_p
     for name in ("bm_create", "bm_assemble", "bm_factor", "bm_rhs_plane_wave", "bm_solve", "bm_far_field",
-                 "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_memory", "bm_destroy"):
+                 "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_memory", "bm_destroy",
+                 "bm_kernel_launches", "bm_enqueue_probe"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -107,15 +111,17 @@ def _is_torch(a) -> bool:
 def _colmajor(a, rows_min: int, writable: bool):
     if _is_torch(a):
         import torch
-        if a.dtype != torch.complex128 or not a.is_cuda:
-            raise TypeError("device arrays must be torch complex128 CUDA tensors")
+        if a.dtype != torch.complex128:
+            raise TypeError("torch arrays must be complex128")
         if a.dim() == 1:
             a = a.unsqueeze(1)
         if a.stride(0) != 1:
-            raise ValueError("device arrays must be column-major (stride(0) == 1)")
+            raise ValueError("torch arrays must be column-major (stride(0) == 1)")
         ld = a.stride(1) if a.shape[1] > 1 else max(a.shape[0], 1)
-        torch.cuda.current_stream(a.device).synchronize()
-        return C.c_void_p(a.data_ptr()), int(ld), int(a.shape[1]), 1, a
+        if a.is_cuda:
+            torch.cuda.current_stream(a.device).synchronize()
+        # CPU tensors (e.g. pinned host buffers) are passed as host pointers
+        return C.c_void_p(a.data_ptr()), int(ld), int(a.shape[1]), 1 if a.is_cuda else 0, a
     arr = np.asarray(a)
     if arr.ndim == 1:
         arr = arr.reshape(-1, 1, order="F")
@@ -237,6 +243,16 @@ def bm_memory(h):
     held, budget = C.c_size_t(), C.c_size_t()
     _check(lib().bm_memory(h, C.byref(held), C.byref(budget)), "bm_memory")
     return held.value, budget.value
+
+
+def bm_enqueue_probe(h, which: int, reps: int) -> None:
+    _check(lib().bm_enqueue_probe(h, int(which), int(reps)), "bm_enqueue_probe")
+
+
+def bm_kernel_launches(h) -> int:
+    n = C.c_ulonglong(0)
+    _check(lib().bm_kernel_launches(h, C.byref(n)), "bm_kernel_launches")
+    return int(n.value)
 
 
 def bm_strerror(status: int) -> str:

@@ -79,11 +79,22 @@ bm_status alloc_t(bm_ctx* c, T** p, size_t bytes) {
         (ptr) = nullptr;       \
     } while (0)
 
-void drop_graphs(bm_ctx* c) {
-    if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
-    c->g_factor = nullptr;
-    for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);
+void drop_slot(bm_ctx::GraphSlot& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.kernels = 0;
+}
+
+void drop_solve_graphs(bm_ctx* c) {
+    for (auto& kv : c->g_solve) drop_slot(kv.second);
     c->g_solve.clear();
+    for (auto& kv : c->g_fp64) drop_slot(kv.second);
+    c->g_fp64.clear();
+}
+
+void drop_graphs(bm_ctx* c) {
+    drop_slot(c->g_factor);
+    drop_solve_graphs(c);
 }
 
 void free_solve_ws(bm_ctx* c) {
@@ -97,8 +108,8 @@ void free_solve_ws(bm_ctx* c) {
     FREE(c->d_Y64);
     FREE(c->d_Y64b);
     c->ws_nrhs = 0;
-    for (auto& kv : c->g_solve) cudaGraphExecDestroy(kv.second);
-    c->g_solve.clear();
+    c->last_nrhs = 0;
+    drop_solve_graphs(c);
 }
 
 void free_problem(bm_ctx* c) {
@@ -236,6 +247,45 @@ extern "C" bm_status bm_destroy(bm_ctx* c) {
     for (auto& kv : c->allocs) cudaFree(kv.first);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
+    return BM_OK;
+}
+
+extern "C" bm_status bm_enqueue_probe(bm_ctx* c, int which, int reps) {
+    if (c == nullptr || reps < 1) return BM_EINVAL;
+    if (!c->assembled) return BM_ESTATE;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    if (which == BM_PROBE_SCHUR) {
+        if (c->form != BM_MIXED) return BM_EINVAL;
+        c->factored = false;
+        drop_slot(c->g_factor);
+        for (int r = 0; r < reps; ++r) {
+            if (c->prec == BM_FP64) {
+                BM_CUDA_TRY(gemm_z64(s, c->N, c->N, 2 * c->N, -1.0, Z64{c->d_Mbot, c->ldbot}, false,
+                                     Z64{c->d_Mtop, c->ldtop}, 0.0, Z64{c->d_F64, c->ldF}));
+            } else {
+                long kext = (c->prec == BM_CF32_3XTF32_IR) ? 3L * c->kseg_schur : c->kseg_schur;
+                BM_CUDA_TRY(gemm_tc(s, c->tm_schur[0], c->tm_schur[1], c->tm_schur[2], c->tm_schur[3], c->d_F32r,
+                                    c->d_F32i, c->ldF, c->N, c->N, (int)kext, -1.0f, 0.0f, c->d_err));
+            }
+            c->launches += 1;
+        }
+        return BM_OK;
+    }
+    if (which == BM_PROBE_RESIDUAL) {
+        if (c->last_nrhs < 1) return BM_ESTATE;
+        for (int r = 0; r < reps; ++r) {
+            BM_TRY(residual_fp64(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
+            c->launches += (c->form == BM_MIXED) ? 3 : 2;
+        }
+        return BM_OK;
+    }
+    return BM_EINVAL;
+}
+
+extern "C" bm_status bm_kernel_launches(bm_ctx* c, unsigned long long* count) {
+    if (c == nullptr || count == nullptr) return BM_EINVAL;
+    *count = c->launches;
     return BM_OK;
 }
 
@@ -395,8 +445,12 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     BM_CUDA_TRY(launch_geometry(st, curve->kind, curve->p, N, d_user, c->d_geom));
     BM_CUDA_TRY(launch_assemble(st, c));
     BM_CUDA_TRY(launch_normA(st, c));
+    c->launches += (form == BM_MIXED) ? 4 : 3;
     if (c32) {
-        if (form == BM_MIXED) BM_CUDA_TRY(launch_pack_schur(st, c, prec == BM_CF32_3XTF32_IR));
+        if (form == BM_MIXED) {
+            BM_CUDA_TRY(launch_pack_schur(st, c, prec == BM_CF32_3XTF32_IR));
+            c->launches += 3;
+        }
     }
     BM_CUDA_TRY(cudaStreamSynchronize(st));
     if (d_user) ctx_free(c, d_user);
@@ -454,11 +508,24 @@ bool graphs_enabled() {
     return !(e && e[0] == '1');
 }
 
+int count_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
+
 // Run `fn` through a cached CUDA graph (captured on first use), or eagerly if graphs are off.
 template <class Fn>
-bm_status run_captured(bm_ctx* c, cudaGraphExec_t* slot, Fn fn) {
+bm_status run_captured(bm_ctx* c, bm_ctx::GraphSlot* slot, Fn fn) {
     if (!graphs_enabled()) return fn();
-    if (*slot == nullptr) {
+    if (slot->exec == nullptr) {
         cudaGraph_t g = nullptr;
         BM_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         bm_status s = fn();
@@ -471,15 +538,17 @@ bm_status run_captured(bm_ctx* c, cudaGraphExec_t* slot, Fn fn) {
             bm_set_error(std::string("stream capture: ") + cudaGetErrorString(e));
             return BM_ECUDA;
         }
-        e = cudaGraphInstantiate(slot, g, 0);
+        slot->kernels = count_kernel_nodes(g);
+        e = cudaGraphInstantiate(&slot->exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
-            *slot = nullptr;
+            slot->exec = nullptr;
             bm_set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
             return BM_ECUDA;
         }
     }
-    BM_CUDA_TRY(cudaGraphLaunch(*slot, c->stream));
+    BM_CUDA_TRY(cudaGraphLaunch(slot->exec, c->stream));
+    c->launches += (unsigned long long)slot->kernels;
     return BM_OK;
 }
 
@@ -561,6 +630,7 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
     if ((const void*)B == (const void*)X) return BM_EINVAL;
     BM_CUDA_TRY(cudaSetDevice(c->device));
     BM_TRY(ensure_ws(c, nrhs));
+    c->last_nrhs = nrhs;
     cudaStream_t s = c->stream;
     const long ld = c->nsys;
     cudaEvent_t e0, e1, r0, r1;
@@ -588,12 +658,14 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
     int iters = 0;
     float t_res = 0.f;
     bm_status st = BM_OK;
+    const unsigned long long k_res = (c->form == BM_MIXED) ? 3 : 2;  // kernels per residual
     if (c->prec == BM_FP64) {
-        st = solve_fp64(c, c->d_Bw, c->d_X, ld, nrhs);
+        st = run_captured(c, &c->g_fp64[nrhs], [&]() { return solve_fp64(c, c->d_Bw, c->d_X, ld, nrhs); });
         if (st == BM_OK && info) {
             cudaEventRecord(r0, s);
             st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
             cudaEventRecord(r1, s);
+            c->launches += k_res + 1;
             if (st == BM_OK) st = backward_error(c, c->d_R, c->d_X, c->d_Bw, ld, nrhs, d_eta);
             if (st == BM_OK) st = read_eta(c, &eta, &nonfinite);
             cudaEventElapsedTime(&t_res, r0, r1);
@@ -607,9 +679,11 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
                 cudaEventRecord(r0, s);
                 st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
                 cudaEventRecord(r1, s);
+                c->launches += k_res;
                 if (st != BM_OK) break;
             }
             st = backward_error(c, c->d_R, c->d_X, c->d_Bw, ld, nrhs, d_eta);
+            c->launches += 1;
             if (st == BM_OK) st = read_eta(c, &eta, &nonfinite);
             if (st != BM_OK) break;
             if (it > 0) {
@@ -627,8 +701,7 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
                 st = BM_ENOTCONV;
                 break;
             }
-            cudaGraphExec_t& slot = c->g_solve[nrhs];
-            st = run_captured(c, &slot, [&]() { return correction_c32(c, c->d_R, c->d_X, ld, nrhs); });
+            st = run_captured(c, &c->g_solve[nrhs], [&]() { return correction_c32(c, c->d_R, c->d_X, ld, nrhs); });
             if (st != BM_OK) break;
             ++iters;
         }
@@ -684,6 +757,7 @@ extern "C" bm_status bm_rhs_plane_wave(bm_ctx* c, const double* angles, int nrhs
     long ldo = on_device ? ldb : c->nsys;
     cudaMemcpyAsync(d_ang, angles, (size_t)nrhs * 8, cudaMemcpyHostToDevice, s);
     cudaError_t e = launch_plane_wave(s, c, d_ang, nrhs, out, ldo);
+    c->launches += 1;
     if (e == cudaSuccess && !on_device)
         e = cudaMemcpy2DAsync(B, (size_t)ldb * 16, dB, (size_t)c->nsys * 16, (size_t)c->nsys * 16, nrhs,
                               cudaMemcpyDeviceToHost, s);
@@ -723,6 +797,7 @@ extern "C" bm_status bm_far_field(bm_ctx* c, const bm_c64* X, int ldx, int nrhs,
         cudaMemcpy2DAsync(dX, (size_t)2 * c->N * 16, X, (size_t)ldx * 16, (size_t)2 * c->N * 16, nrhs,
                           cudaMemcpyHostToDevice, s);
     cudaError_t e = launch_far_field(s, c, xin, ldxi, nrhs, d_ang, M, uo, ldo);
+    c->launches += 1;
     if (e == cudaSuccess && !on_device)
         e = cudaMemcpy2DAsync(Uinf, (size_t)ldu * 16, dU, (size_t)M * 16, (size_t)M * 16, nrhs,
                               cudaMemcpyDeviceToHost, s);
@@ -794,6 +869,7 @@ extern "C" bm_status bm_hankel01(bm_ctx* c, const bm_c64* z, int n, bm_c64* h0, 
     double2* o0 = on_device ? reinterpret_cast<double2*>(h0) : d0;
     double2* o1 = on_device ? reinterpret_cast<double2*>(h1) : d1;
     cudaError_t e = launch_hankel_probe(s, c, zi, n, o0, o1);
+    c->launches += 1;
     if (e == cudaSuccess && !on_device) {
         cudaMemcpyAsync(h0, d0, (size_t)n * 16, cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(h1, d1, (size_t)n * 16, cudaMemcpyDeviceToHost, s);

@@ -208,6 +208,7 @@ struct bm_ctx {
 
     // solve workspace (sized for the largest nrhs seen)
     int ws_nrhs = 0;
+    int last_nrhs = 0;        // nrhs of the last bm_solve (its B, X stay in the workspace)
     double2* d_X = nullptr;   // nsys x nrhs FP64 iterate
     double2* d_R = nullptr;   // nsys x nrhs FP64 residual
     double2* d_Bw = nullptr;  // nsys x nrhs FP64 copy of B
@@ -219,10 +220,15 @@ struct bm_ctx {
     double2* d_Y64b = nullptr;
     double* d_colred = nullptr;  // per-column reductions (4 x nrhs)
 
-    // cached graphs
-    cudaGraphExec_t g_factor = nullptr;
-    std::map<int, cudaGraphExec_t> g_solve;   // keyed by nrhs
-    std::map<int, cudaGraphExec_t> g_resid;
+    // cached graphs (with the number of kernel nodes each replay launches)
+    struct GraphSlot {
+        cudaGraphExec_t exec = nullptr;
+        int kernels = 0;
+    };
+    GraphSlot g_factor;
+    std::map<int, GraphSlot> g_solve;   // correction solve, keyed by nrhs
+    std::map<int, GraphSlot> g_fp64;    // FP64 direct solve, keyed by nrhs
+    unsigned long long launches = 0;    // kernels launched by this handle
 
     // tensor maps (opaque bytes, built on the host)
     alignas(64) unsigned char tm_schur[4][128];

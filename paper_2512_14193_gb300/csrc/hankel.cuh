@@ -25,7 +25,6 @@ constexpr double R_ASYM = 20.0;
 constexpr double EULER_GAMMA = 0.57721566490153286060651209008240243;
 constexpr double TWO_OVER_PI = 0.63661977236758134307553505349005745;
 constexpr double ONE_OVER_PI = 0.31830988618379067153776752674502872;
-constexpr double PI_4 = 0.78539816339744830961566084581987572;
 
 __device__ __forceinline__ double2 clog(double2 z) {
     return make_double2(log(hypot(z.x, z.y)), atan2(z.y, z.x));
@@ -122,12 +121,14 @@ __device__ __forceinline__ void asym(double2 z, double2& h0, double2& h1) {
         s1 = cadd(s1, t1);
         if (cnorm1(t0) <= 1e-17 * cnorm1(s0) && cnorm1(t1) <= 1e-17 * cnorm1(s1)) break;
     }
-    // c = sqrt(2/(pi z)) * exp(i (z - pi/4))
+    // c = sqrt(2/(pi z)) * exp(i (z - pi/4)); the -pi/4 is applied as the exact rotation
+    // (1 - i)/sqrt(2) after sincos(Re z): subtracting pi/4 from a large Re z in FP64 would lose
+    // up to half an ulp of the argument (5e-14 of phase at |z| = 550).
     double2 c = csqrt(cscale(cinv(z), TWO_OVER_PI));
     double sn, cs;
-    sincos(z.x - PI_4, &sn, &cs);
-    double e = exp(-z.y);
-    c = cmul(c, make_double2(e * cs, e * sn));
+    sincos(z.x, &sn, &cs);
+    double e = exp(-z.y) * 0.70710678118654752440;
+    c = cmul(c, make_double2(e * (cs + sn), e * (sn - cs)));
     h0 = cmul(c, s0);
     h1 = cneg(cmuli(cmul(c, s1)));  // -i c s1
 }

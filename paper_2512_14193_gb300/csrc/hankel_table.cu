@@ -115,7 +115,8 @@ void asym_start(double x, double y, cd& h0, cd& h1) {
     double m = std::sqrt(2.0 / (M_PI * r));
     cd c{m * std::cos(-0.5 * th), m * std::sin(-0.5 * th)};
     double e = std::exp(-y);
-    cd ph{e * std::cos(x - M_PI / 4), e * std::sin(x - M_PI / 4)};
+    const double r2 = 0.70710678118654752440;  // e^{-i pi/4} applied exactly
+    cd ph{e * r2 * (std::cos(x) + std::sin(x)), e * r2 * (std::sin(x) - std::cos(x))};
     c = mul(c, ph);
     h0 = mul(c, s0);
     cd cs1 = mul(c, s1);
