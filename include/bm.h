@@ -88,7 +88,10 @@ typedef struct {
  *  prec          : bm_precision (default BM_FP64).
  *  refine_tol    : backward-error target of refinement (default 1e-9).
  *  refine_maxit  : refinement iteration cap (default 30).
- *  nb            : outer LU block size, a multiple of 32 in [32, 512] (0 = library default). */
+ *  nb            : outer LU block size, a multiple of 32 in [32, 256] (0 = library default).
+ *  refine_full_residual: 1 = every refinement residual b - A x in FP64; 0 (default) = the first
+ *                  in FP64, later ones updated as r -= A d with the product in FP32 (d, the last
+ *                  correction, is already small, so the update error stays far below refine_tol). */
 typedef struct {
     double eps0;
     bm_c64 eps1;
@@ -99,6 +102,7 @@ typedef struct {
     double refine_tol;
     int refine_maxit;
     int nb;
+    int refine_full_residual;
 } bm_opts;
 
 /* Per-solve report.  Times are device times (CUDA events) of the solve's phases. */

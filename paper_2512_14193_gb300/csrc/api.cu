@@ -379,6 +379,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     c->beta = beta;
     c->refine_tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : 1e-9;
     c->refine_maxit = (opts && opts->refine_maxit > 0) ? opts->refine_maxit : 30;
+    c->full_residual = opts && opts->refine_full_residual;
     c->ldtop = p.ldtop;
     c->ldbot = p.ldbot;
     c->ldA = p.ldA;
@@ -675,11 +676,19 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
         cudaMemsetAsync(c->d_X, 0, (size_t)ld * nrhs * 16, s);
         cudaMemcpyAsync(c->d_R, c->d_Bw, (size_t)ld * nrhs * 16, cudaMemcpyDeviceToDevice, s);
         for (int it = 0;; ++it) {
-            if (it > 0) {
+            if (it == 1 || (it > 1 && c->full_residual)) {
+                // r = b - A x in FP64 (after the first correction x is the plain FP32 solve)
                 cudaEventRecord(r0, s);
                 st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
                 cudaEventRecord(r1, s);
                 c->launches += k_res;
+                if (st != BM_OK) break;
+            } else if (it > 1) {
+                // r -= A d for the last correction d (FP32 products; d is small by now)
+                cudaEventRecord(r0, s);
+                st = residual_update_c32(c, c->d_R, ld, nrhs);
+                cudaEventRecord(r1, s);
+                c->launches += (c->form == BM_MIXED) ? 3 : 1;
                 if (st != BM_OK) break;
             }
             st = backward_error(c, c->d_R, c->d_X, c->d_Bw, ld, nrhs, d_eta);

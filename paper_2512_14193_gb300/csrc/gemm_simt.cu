@@ -1,11 +1,13 @@
 // Complex GEMM on the CUDA cores: C = beta C + alpha op(A) B for column-major views.
 //
 // FP64 (Z64, interleaved double2): the engine of the FP64 path (Schur complement
-// U33 = -[M31 M32][M13; M23] of Theorem thm:LU, LU trailing updates, FP64 residuals of
+// U33 = -[M31 M32][M13; M23] of Theorem thm:LU, LU trailing updates, the FP64 residual of
 // refinement).  GB300 executes FP64 on the CUDA cores only, so this kernel is bound by the FP64
-// pipe; it keeps a 64 x 64 (or 64 x 16 for few right-hand sides) tile per CTA with 4 x 4
-// (4 x 1) complex accumulators per thread staged through shared memory.
+// pipe; it keeps a 64 x BN tile per CTA (BN = 16, 32 or 64, whichever pads the column count
+// least) with 4 x BN/16 complex accumulators per thread staged through shared memory.
 // FP32 (C32, planar): skinny updates inside the LU panel and the FP32 correction solves.
+// Mixed (A and C FP64 storage, B FP32, FP32 arithmetic): the refinement residual update
+// r -= A d for a small correction d.
 //
 // op(A) = A (m x k view) or, with a_trans, A is given as its transpose stored column-major
 // (k x m view), i.e. row-major A - the layout of the tensor-core operand packs.
@@ -16,11 +18,30 @@ namespace {
 
 constexpr int BK = 16;
 
-template <class V, bool AT, int BM, int BN>
-__global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, V A, V B, V C,
-                                                         typename V::real alpha, typename V::real beta) {
-    using R = typename V::real;
-    using CV = typename V::cv;
+template <class R> BM_HD cplx_t<R> conv(double2 v);
+template <class R> BM_HD cplx_t<R> conv(float2 v);
+template <> BM_HD double2 conv<double>(double2 v) { return v; }
+template <> BM_HD double2 conv<double>(float2 v) { return make_double2(v.x, v.y); }
+template <> BM_HD float2 conv<float>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <> BM_HD float2 conv<float>(float2 v) { return v; }
+
+template <class VC> BM_HD typename VC::cv from_acc(double2 v) {
+    typename VC::cv r;
+    r.x = (typename VC::real)v.x;
+    r.y = (typename VC::real)v.y;
+    return r;
+}
+template <class VC> BM_HD typename VC::cv from_acc(float2 v) {
+    typename VC::cv r;
+    r.x = (typename VC::real)v.x;
+    r.y = (typename VC::real)v.y;
+    return r;
+}
+
+// VA, VB, VC: storage views of A, B, C; R: arithmetic precision
+template <class VA, class VB, class VC, class R, bool AT, int BM, int BN>
+__global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, VA A, VB B, VC C, R alpha, R beta) {
+    using CV = cplx_t<R>;
     constexpr int TM = BM / 16, TN = BN / 16;
     __shared__ CV As[BK][BM + 1];
     __shared__ CV Bs[BK][BN + 1];
@@ -34,7 +55,6 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, V 
         for (int b = 0; b < TN; ++b) acc[a][b] = czero<R>();
 
     for (int k0 = 0; k0 < k; k0 += BK) {
-        // A tile BM x BK
 #pragma unroll
         for (int e = t; e < BM * BK; e += 256) {
             int ii, kk;
@@ -48,17 +68,16 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, V 
             long gi = i0 + ii;
             int gk = k0 + kk;
             CV v = czero<R>();
-            if (gi < m && gk < k) v = AT ? A.get(gk, gi) : A.get(gi, gk);
+            if (gi < m && gk < k) v = conv<R>(AT ? A.get(gk, gi) : A.get(gi, gk));
             As[kk][ii] = v;
         }
-        // B tile BK x BN
 #pragma unroll
         for (int e = t; e < BN * BK; e += 256) {
             int kk = e % BK, jj = e / BK;
             long gj = j0 + jj;
             int gk = k0 + kk;
             CV v = czero<R>();
-            if (gj < n && gk < k) v = B.get(gk, gj);
+            if (gj < n && gk < k) v = conv<R>(B.get(gk, gj));
             Bs[kk][jj] = v;
         }
         __syncthreads();
@@ -87,26 +106,40 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, V 
             CV r;
             r.x = alpha * acc[a][b].x;
             r.y = alpha * acc[a][b].y;
+            typename VC::cv out = from_acc<VC>(r);
             if (beta != (R)0) {
-                CV c = C.get(gi, gj);
-                r.x += beta * c.x;
-                r.y += beta * c.y;
+                typename VC::cv c = C.get(gi, gj);
+                out.x += (typename VC::real)beta * c.x;
+                out.y += (typename VC::real)beta * c.y;
             }
-            C.set(gi, gj, r);
+            C.set(gi, gj, out);
         }
     }
 }
 
-template <class V, bool AT>
-cudaError_t launch_impl(cudaStream_t s, int m, int n, int k, V A, V B, V C, typename V::real alpha,
-                        typename V::real beta) {
+template <class VA, class VB, class VC, class R, bool AT>
+cudaError_t launch_impl(cudaStream_t s, int m, int n, int k, VA A, VB B, VC C, R alpha, R beta) {
     if (m <= 0 || n <= 0) return cudaSuccess;
-    if (n <= 16) {
+    // column tile with the least padding (ties go to the wider tile): n = 65 right-hand sides
+    // run as 5 x 16 columns instead of 2 x 64
+    int bn = 64;
+    long best = (long)ceil_div(n, 64) * 64 - n;
+    for (int cand : {32, 16}) {
+        long waste = (long)ceil_div(n, cand) * cand - n;
+        if (waste < best) {
+            best = waste;
+            bn = cand;
+        }
+    }
+    if (bn == 16) {
         dim3 grid(ceil_div(m, 64), ceil_div(n, 16));
-        cgemm_simt_kernel<V, AT, 64, 16><<<grid, 256, 0, s>>>(m, n, k, A, B, C, alpha, beta);
+        cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 16><<<grid, 256, 0, s>>>(m, n, k, A, B, C, alpha, beta);
+    } else if (bn == 32) {
+        dim3 grid(ceil_div(m, 64), ceil_div(n, 32));
+        cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 32><<<grid, 256, 0, s>>>(m, n, k, A, B, C, alpha, beta);
     } else {
         dim3 grid(ceil_div(m, 64), ceil_div(n, 64));
-        cgemm_simt_kernel<V, AT, 64, 64><<<grid, 256, 0, s>>>(m, n, k, A, B, C, alpha, beta);
+        cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 64><<<grid, 256, 0, s>>>(m, n, k, A, B, C, alpha, beta);
     }
     return cudaGetLastError();
 }
@@ -115,18 +148,20 @@ cudaError_t launch_impl(cudaStream_t s, int m, int n, int k, V A, V B, V C, type
 
 cudaError_t gemm_z64(cudaStream_t s, int m, int n, int k, double alpha, Z64 A, bool a_trans, Z64 B, double beta,
                      Z64 C) {
-    if (k <= 0) {
-        if (beta == 1.0) return cudaSuccess;
-    }
-    return a_trans ? launch_impl<Z64, true>(s, m, n, k, A, B, C, alpha, beta)
-                   : launch_impl<Z64, false>(s, m, n, k, A, B, C, alpha, beta);
+    if (k <= 0 && beta == 1.0) return cudaSuccess;
+    return a_trans ? launch_impl<Z64, Z64, Z64, double, true>(s, m, n, k, A, B, C, alpha, beta)
+                   : launch_impl<Z64, Z64, Z64, double, false>(s, m, n, k, A, B, C, alpha, beta);
 }
 
 cudaError_t gemm_c32(cudaStream_t s, int m, int n, int k, float alpha, C32 A, bool a_trans, C32 B, float beta,
                      C32 C) {
-    if (k <= 0) {
-        if (beta == 1.0f) return cudaSuccess;
-    }
-    return a_trans ? launch_impl<C32, true>(s, m, n, k, A, B, C, alpha, beta)
-                   : launch_impl<C32, false>(s, m, n, k, A, B, C, alpha, beta);
+    if (k <= 0 && beta == 1.0f) return cudaSuccess;
+    return a_trans ? launch_impl<C32, C32, C32, float, true>(s, m, n, k, A, B, C, alpha, beta)
+                   : launch_impl<C32, C32, C32, float, false>(s, m, n, k, A, B, C, alpha, beta);
+}
+
+// C (FP64) += alpha A (FP64 storage) B (FP32 planar), products and sums in FP32
+cudaError_t gemm_update_z64_c32(cudaStream_t s, int m, int n, int k, float alpha, Z64 A, C32 B, Z64 C) {
+    if (k <= 0) return cudaSuccess;
+    return launch_impl<Z64, C32, Z64, float, false>(s, m, n, k, A, B, C, alpha, 1.0f);
 }

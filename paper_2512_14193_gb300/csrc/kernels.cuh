@@ -16,6 +16,7 @@ cudaError_t launch_to_c32(cudaStream_t s, const double2* A, long lda, int m, int
 // gemm_simt.cu
 cudaError_t gemm_z64(cudaStream_t s, int m, int n, int k, double alpha, Z64 A, bool a_trans, Z64 B, double beta, Z64 C);
 cudaError_t gemm_c32(cudaStream_t s, int m, int n, int k, float alpha, C32 A, bool a_trans, C32 B, float beta, C32 C);
+cudaError_t gemm_update_z64_c32(cudaStream_t s, int m, int n, int k, float alpha, Z64 A, C32 B, Z64 C);
 
 // gemm_tc.cu (tensor maps are CUtensorMap, passed as opaque 128-byte blobs)
 bm_status tc_make_map(void* tmap, const float* base, long rows, long kext, long ldk, int box_rows);
@@ -41,4 +42,5 @@ bm_status residual_fp64(bm_ctx* c, const double2* B, const double2* X, double2* 
 bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const double2* B, long ld, int nrhs,
                          double* d_eta);
 bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int nrhs);
+bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs);
 cudaError_t launch_copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd);

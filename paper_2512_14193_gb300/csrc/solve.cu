@@ -106,6 +106,17 @@ __global__ void add_c32_kernel(double2* __restrict__ X, long ldx, int r0, int m,
     x.y += (double)Di[i + (long)j * ldd];
 }
 
+// X[r0 + i, c] -= D[i, c]
+__global__ void sub_c32_kernel(double2* __restrict__ X, long ldx, int r0, int m, int n, const float* __restrict__ Dr,
+                               const float* __restrict__ Di, long ldd) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)m * n) return;
+    int j = (int)(idx / m), i = (int)(idx % m);
+    double2& x = X[r0 + i + (long)j * ldx];
+    x.x -= (double)Dr[i + (long)j * ldd];
+    x.y -= (double)Di[i + (long)j * ldd];
+}
+
 __global__ void copy_z64_kernel(const double2* __restrict__ S, long lds, int m, int n, double2* __restrict__ D,
                                 long ldd) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -232,6 +243,30 @@ bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int n
         long t2 = (long)c->n * nrhs;
         add_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(X, ld, 0, c->n, nrhs, Vr, Vi, ldv);
         SV_CUDA(cudaGetLastError());
+    }
+    return BM_OK;
+}
+
+// R -= A d for the correction d of the last correction_c32 call (still in the FP32 work buffers),
+// with the products in FP32.  d is small next to x after the first correction, so the FP32
+// product error (~1e-6 |A| |d|) stays far below the backward-error target: this replaces the
+// full FP64 residual b - A x from the second refinement step on.
+bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs) {
+    cudaStream_t s = c->stream;
+    const int N = c->N;
+    const long ldw = c->nsys, ldv = c->n;
+    if (c->form == BM_MIXED) {
+        // rows [0, 2N): r -= d12 + [M13; M23] d3 ; rows [2N, 3N): r -= [M31 M32] d12
+        long t2 = (long)2 * N * nrhs;
+        sub_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(R, ld, 0, 2 * N, nrhs, c->d_Wr, c->d_Wi, ldw);
+        SV_CUDA(cudaGetLastError());
+        SV_CUDA(gemm_update_z64_c32(s, 2 * N, nrhs, N, -1.0f, Z64{c->d_Mtop, c->ldtop}, C32{c->d_W2r, c->d_W2i, ldv},
+                                    Z64{R, ld}));
+        SV_CUDA(gemm_update_z64_c32(s, N, nrhs, 2 * N, -1.0f, Z64{c->d_Mbot, c->ldbot}, C32{c->d_Wr, c->d_Wi, ldw},
+                                    Z64{R + 2 * N, ld}));
+    } else {
+        SV_CUDA(gemm_update_z64_c32(s, 2 * N, nrhs, 2 * N, -1.0f, Z64{c->d_A, c->ldA}, C32{c->d_W2r, c->d_W2i, ldv},
+                                    Z64{R, ld}));
     }
     return BM_OK;
 }

@@ -76,11 +76,16 @@ def test_fp64_ordinary_matches_oracle(bmlib, handle, N):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("form", [0, 1])
-def test_mixed_precision_refinement(bmlib, handle, prec, form):
+def test_mixed_precision_refinement(bmlib, handle, prec, form, full):
+    # full=False: only the first residual in FP64, later ones updated r -= A d in FP32
     curve, N, k0, k1 = W.star(1.0, 0.3, 5), 200, 6.0, 9.0
-    g, P = _setup(bmlib, handle, curve, N, k0, k1, form, prec)
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, k0, k1, form,
+                      bmlib.make_opts(prec, full_residual=full))
+    assert bmlib.bm_factor(handle) == 0
+    g, P = O.nodes(curve, N), O.default_params(k0, k1)
     B = _rhs(g, P, N, form, 6, full=(form == 0))
     X = np.zeros_like(B, order="F")
     info = bmlib.bm_solve(handle, B, X)
