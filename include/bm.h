@@ -89,9 +89,13 @@ typedef struct {
  *  refine_tol    : backward-error target of refinement (default 1e-9).
  *  refine_maxit  : refinement iteration cap (default 30).
  *  nb            : outer LU block size, a multiple of 32 in [32, 256] (0 = library default).
- *  refine_full_residual: 1 = every refinement residual b - A x in FP64; 0 (default) = the first
- *                  in FP64, later ones updated as r -= A d with the product in FP32 (d, the last
- *                  correction, is already small, so the update error stays far below refine_tol). */
+ *  refine_residual: how refinement forms r = b - A x (bm_refine_residual):
+ *     BM_RESID_DF_UPDATE (0, default): the first residual in double-float arithmetic on the FP32
+ *        cores (each FP64 operand split into two FP32 parts, exact products, compensated sums:
+ *        ~1e-12 of |A||x|), later ones updated as r -= A d with the product in FP32 (d, the last
+ *        correction, is small by then, so the update error stays far below refine_tol);
+ *     BM_RESID_FP64_UPDATE (1): the first residual in FP64, later ones updated as above;
+ *     BM_RESID_FP64_ALL (2): every residual in FP64. */
 typedef struct {
     double eps0;
     bm_c64 eps1;
@@ -102,8 +106,10 @@ typedef struct {
     double refine_tol;
     int refine_maxit;
     int nb;
-    int refine_full_residual;
+    int refine_residual;
 } bm_opts;
+
+typedef enum { BM_RESID_DF_UPDATE = 0, BM_RESID_FP64_UPDATE = 1, BM_RESID_FP64_ALL = 2 } bm_refine_residual;
 
 /* Per-solve report.  Times are device times (CUDA events) of the solve's phases. */
 typedef struct {
@@ -188,7 +194,8 @@ bm_status bm_hankel_anchor_table(double* out, int cap_anchors, int* nx, int* ny,
  *                             Theorem thm:LU (mixed system; tensor cores for the CF32 precisions,
  *                             FP64 CUDA cores for BM_FP64).  It overwrites U33, so the handle
  *                             returns to the assembled-but-not-factored state.
- *  which = BM_PROBE_RESIDUAL: the FP64 residual r = b - A x of the last bm_solve (same nrhs).
+ *  which = BM_PROBE_RESIDUAL: the first refinement residual r = b - A x of the last bm_solve (same
+ *                             nrhs), in the arithmetic the handle uses for it (FP64 or double-float).
  * Errors: BM_ESTATE (nothing assembled / solved yet), BM_EINVAL. */
 enum { BM_PROBE_SCHUR = 0, BM_PROBE_RESIDUAL = 1 };
 bm_status bm_enqueue_probe(bm_ctx* ctx, int which, int reps);

@@ -24,6 +24,7 @@ BM_MIXED, BM_ORDINARY = 0, 1
 BM_FP64, BM_CF32_TF32_IR, BM_CF32_3XTF32_IR = 0, 1, 2
 BM_CURVE_CIRCLE, BM_CURVE_ELLIPSE, BM_CURVE_STAR, BM_CURVE_KITE, BM_CURVE_USER = range(5)
 BM_PROBE_SCHUR, BM_PROBE_RESIDUAL = 0, 1
+BM_RESID_DF_UPDATE, BM_RESID_FP64_UPDATE, BM_RESID_FP64_ALL = 0, 1, 2
 
 
 class bm_c64(C.Structure):
@@ -37,7 +38,7 @@ class bm_curve(C.Structure):
 class bm_opts(C.Structure):
     _fields_ = [("eps0", C.c_double), ("eps1", bm_c64), ("beta", bm_c64), ("eps_set", C.c_int),
                 ("beta_set", C.c_int), ("prec", C.c_int), ("refine_tol", C.c_double), ("refine_maxit", C.c_int),
-                ("nb", C.c_int), ("refine_full_residual", C.c_int)]
+                ("nb", C.c_int), ("refine_residual", C.c_int)]
 
 
 class bm_solve_info(C.Structure):
@@ -146,14 +147,14 @@ def bm_destroy(h) -> None:
 
 
 def make_opts(prec: int = BM_FP64, eps0: float = 1.0, eps1=None, beta=None, refine_tol: float = 1e-9,
-              refine_maxit: int = 30, nb: int = 0, full_residual: bool = False) -> bm_opts:
+              refine_maxit: int = 30, nb: int = 0, residual: int = 0) -> bm_opts:
     o = bm_opts()
     o.eps0 = float(eps0)
     o.prec = int(prec)
     o.refine_tol = float(refine_tol)
     o.refine_maxit = int(refine_maxit)
     o.nb = int(nb)
-    o.refine_full_residual = 1 if full_residual else 0
+    o.refine_residual = int(residual)
     if eps1 is not None:
         o.eps1 = _c64(eps1)
         o.eps_set = 1

@@ -275,7 +275,10 @@ extern "C" bm_status bm_enqueue_probe(bm_ctx* c, int which, int reps) {
     if (which == BM_PROBE_RESIDUAL) {
         if (c->last_nrhs < 1) return BM_ESTATE;
         for (int r = 0; r < reps; ++r) {
-            BM_TRY(residual_fp64(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
+            if (c->prec != BM_FP64 && c->resid_mode == BM_RESID_DF_UPDATE)
+                BM_TRY(residual_df(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
+            else
+                BM_TRY(residual_fp64(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
             c->launches += (c->form == BM_MIXED) ? 3 : 2;
         }
         return BM_OK;
@@ -335,6 +338,8 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     int prec = opts ? opts->prec : BM_FP64;
     if (prec < BM_FP64 || prec > BM_CF32_3XTF32_IR) return BM_EINVAL;
     int nb = opts ? opts->nb : 0;
+    if (opts && (opts->refine_residual < BM_RESID_DF_UPDATE || opts->refine_residual > BM_RESID_FP64_ALL))
+        return BM_EINVAL;
     if (nb != 0 && (nb % 32 != 0 || nb < 32 || nb > 256)) {
         bm_set_error("nb must be a multiple of 32 in [32, 256]");
         return BM_EINVAL;
@@ -379,7 +384,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     c->beta = beta;
     c->refine_tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : 1e-9;
     c->refine_maxit = (opts && opts->refine_maxit > 0) ? opts->refine_maxit : 30;
-    c->full_residual = opts && opts->refine_full_residual;
+    c->resid_mode = opts ? opts->refine_residual : BM_RESID_DF_UPDATE;
     c->ldtop = p.ldtop;
     c->ldbot = p.ldbot;
     c->ldA = p.ldA;
@@ -676,10 +681,14 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
         cudaMemsetAsync(c->d_X, 0, (size_t)ld * nrhs * 16, s);
         cudaMemcpyAsync(c->d_R, c->d_Bw, (size_t)ld * nrhs * 16, cudaMemcpyDeviceToDevice, s);
         for (int it = 0;; ++it) {
-            if (it == 1 || (it > 1 && c->full_residual)) {
-                // r = b - A x in FP64 (after the first correction x is the plain FP32 solve)
+            if (it == 1 || (it > 1 && c->resid_mode == BM_RESID_FP64_ALL)) {
+                // r = b - A x in FP64 or double-float (after the first correction x is the plain
+                // FP32 solve)
                 cudaEventRecord(r0, s);
-                st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
+                if (c->resid_mode == BM_RESID_DF_UPDATE)
+                    st = residual_df(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
+                else
+                    st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
                 cudaEventRecord(r1, s);
                 c->launches += k_res;
                 if (st != BM_OK) break;

@@ -162,7 +162,7 @@ struct bm_ctx {
     double2 k0{}, k1{}, eps0{}, eps1{}, beta{};
     double refine_tol = 1e-9;
     int refine_maxit = 30;
-    bool full_residual = false;
+    int resid_mode = BM_RESID_DF_UPDATE;
     int nb = 0;
 
     // geometry (device, SoA of N each): x, y, nx, ny, speed, kappa, w

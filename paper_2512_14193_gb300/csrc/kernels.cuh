@@ -43,4 +43,9 @@ bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const do
                          double* d_eta);
 bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int nrhs);
 bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs);
+bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs);
+
+// resid_df.cu: C += alpha A X in double-float arithmetic (A, X, C FP64 column-major)
+cudaError_t gemm_df(cudaStream_t s, int m, int n, int k, double alpha, const double2* A, long lda, const double2* X,
+                    long ldx, double2* C, long ldc);
 cudaError_t launch_copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd);

@@ -188,6 +188,23 @@ bm_status residual_fp64(bm_ctx* c, const double2* B, const double2* X, double2* 
     return BM_OK;
 }
 
+// R = B - A X with the FP64 operator, products and sums in double-float on the FP32 cores.
+bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs) {
+    cudaStream_t s = c->stream;
+    const int N = c->N;
+    long t = (long)c->nsys * nrhs;
+    int nsub = (c->form == BM_MIXED) ? 2 * N : 0;
+    resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
+    SV_CUDA(cudaGetLastError());
+    if (c->form == BM_MIXED) {
+        SV_CUDA(gemm_df(s, 2 * N, nrhs, N, -1.0, c->d_Mtop, c->ldtop, X + 2 * N, ld, R, ld));
+        SV_CUDA(gemm_df(s, N, nrhs, 2 * N, -1.0, c->d_Mbot, c->ldbot, X, ld, R + 2 * N, ld));
+    } else {
+        SV_CUDA(gemm_df(s, 2 * N, nrhs, 2 * N, -1.0, c->d_A, c->ldA, X, ld, R, ld));
+    }
+    return BM_OK;
+}
+
 // d_eta[0] = backward error (max over columns), d_eta[1] = non-finite flag of B
 bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const double2* B, long ld, int nrhs,
                          double* d_eta) {

@@ -76,14 +76,14 @@ def test_fp64_ordinary_matches_oracle(bmlib, handle, N):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("full", [False, True])
+@pytest.mark.parametrize("resid", [0, 1, 2])
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("form", [0, 1])
-def test_mixed_precision_refinement(bmlib, handle, prec, form, full):
-    # full=False: only the first residual in FP64, later ones updated r -= A d in FP32
+def test_mixed_precision_refinement(bmlib, handle, prec, form, resid):
+    # resid 0: first residual double-float, later ones r -= A d in FP32; 1: first in FP64; 2: all FP64
     curve, N, k0, k1 = W.star(1.0, 0.3, 5), 200, 6.0, 9.0
     bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, k0, k1, form,
-                      bmlib.make_opts(prec, full_residual=full))
+                      bmlib.make_opts(prec, residual=resid))
     assert bmlib.bm_factor(handle) == 0
     g, P = O.nodes(curve, N), O.default_params(k0, k1)
     B = _rhs(g, P, N, form, 6, full=(form == 0))
@@ -101,6 +101,25 @@ def test_mixed_precision_refinement(bmlib, handle, prec, form, full):
         Xr = O.dense_solve(A, B)
     assert eta <= 1.5e-9
     assert _relerr(X, Xr) < 1e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", [0, 1])
+def test_double_float_residual_reaches_tight_tolerance(bmlib, handle, form):
+    # Refinement can only certify what its residual resolves: reaching 2e-12 through the
+    # double-float residual (and FP32 updates) pins that residual far below the 1e-9 target.
+    curve, N, k0, k1 = W.kite(), 300, 9.0 - 0.2j, 13.5 - 0.3j
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, k0, k1, form,
+                      bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=2e-12, residual=0))
+    assert bmlib.bm_factor(handle) == 0
+    g, P = O.nodes(curve, N), O.default_params(k0, k1)
+    B = _rhs(g, P, N, form, 4, full=(form == 0), seed=3)
+    X = np.zeros_like(B, order="F")
+    info = bmlib.bm_solve(handle, B, X)
+    assert info.backward_error <= 2e-12
+    eta = (O.backward_error_mixed(O.mixed_blocks(g, P), X, B) if form == 0
+           else O.backward_error_dense(O.ordinary_matrix(g, P), X, B))
+    assert eta <= 5e-12
 
 
 @pytest.mark.gpu
