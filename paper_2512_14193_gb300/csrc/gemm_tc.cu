@@ -114,6 +114,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// the same 16 columns of two accumulators (real and imaginary part), one wait for both
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float* va, float* vb) {
+    uint32_t a[16], b[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+        "[%33];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]),
+          "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(b[0]),
+          "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]),
+          "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        va[i] = __uint_as_float(a[i]);
+        vb[i] = __uint_as_float(b[i]);
+    }
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
@@ -216,21 +237,32 @@ __global__ void __launch_bounds__(128, 1)
     if (!*abort_flag) {
         const long row = (long)tm * BM + warp * 32 + lane;
         const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+        const long col0 = (long)tn * BN;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float vr[16], vi[16];
-            tmem_ld16(Dr + lane_off + c0, vr);
-            tmem_ld16(Di + lane_off + c0, vi);
+            tmem_ld16x2(Dr + lane_off + c0, Di + lane_off + c0, vr, vi);
             if (row < m) {
+                // issue every load of this 16-column chunk before any store, so the chunk costs
+                // one memory round trip instead of sixteen
+                float cr[16], ci[16];
+                if (beta != 0.f) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const long col = col0 + c0 + q;
+                        cr[q] = (col < n) ? __ldg(Cr + row + col * ldc) : 0.f;
+                        ci[q] = (col < n) ? __ldg(Ci + row + col * ldc) : 0.f;
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const long col = (long)tn * BN + c0 + q;
+                    const long col = col0 + c0 + q;
                     if (col < n) {
                         const long o = row + col * ldc;
                         float r = alpha * vr[q], im = alpha * vi[q];
                         if (beta != 0.f) {
-                            r += beta * Cr[o];
-                            im += beta * Ci[o];
+                            r = fmaf(beta, cr[q], r);
+                            im = fmaf(beta, ci[q], im);
                         }
                         Cr[o] = r;
                         Ci[o] = im;

@@ -3,12 +3,15 @@
 //
 // Right-looking blocked LU with two block sizes:
 //   for each big panel of NB columns (C32: 128, Z64: 64):
-//     for each sub-panel of nbp columns (<= 32):
+//     for each sub-panel of nbp columns (nbp = 32/16/8 for C32, 16/8/4 for Z64 - wider when the
+//     rows below the diagonal are fewer):
 //        panel_kernel      : unblocked LU with partial pivoting of rows [j, n) x nbp columns.
-//                            Rows are spread over a cluster of up to 16 CTAs held in shared
-//                            memory; each column's pivot candidates (value, index, whole row) are
-//                            pushed to every CTA through distributed shared memory, so one
-//                            cluster barrier per column decides the pivot everywhere.
+//                            Rows are spread over a cluster of up to 16 CTAs, one to four rows per
+//                            thread, held in registers.  Each column's pivot candidates (value,
+//                            index, whole row) are pushed to every CTA through distributed shared
+//                            memory; the cluster barrier is split into arrive/wait so that the
+//                            rank-1 update of all but the next column runs while it completes.
+//                            The last CTA work also builds the row-interchange maps.
 //        swap_trsm_kernel  : row interchanges + unit-lower solve for the rest of the big panel
 //        gemm (SIMT)       : rank-nbp update of the rest of the big panel
 //     swap_trsm_kernel     : interchanges for all other columns, U12 = L11^{-1} A12 (and its
@@ -32,190 +35,29 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-// ------------------------------------------------------------------------------------------------
-// panel factorisation
-// ------------------------------------------------------------------------------------------------
 constexpr int PANEL_THREADS = 512;
 constexpr int MAX_CLUSTER = 16;
+constexpr int MAP_MAX = 512;  // 2 * max NB (NB <= 256)
 
-template <class CV> struct real_of;
-template <> struct real_of<double2> { using type = double; };
-template <> struct real_of<float2> { using type = float; };
-
-template <class CV>
-__host__ __device__ size_t panel_smem_bytes(int nbp, int R) {
-    using Rl = typename real_of<CV>::type;
-    size_t b = (size_t)nbp * R * sizeof(CV);                // slab
-    b += (size_t)2 * MAX_CLUSTER * nbp * sizeof(CV);         // candidate rows
-    b += (size_t)2 * nbp * sizeof(CV);                       // diagonal rows
-    b += (size_t)2 * MAX_CLUSTER * sizeof(Rl) + 2 * MAX_CLUSTER * sizeof(int);
-    b += 32 * (sizeof(Rl) + sizeof(int)) + 64;
-    return b;
-}
+struct SwapMap {  // new[dst[t]] = old[src[t]], t < count
+    int count;
+    int dst[MAP_MAX];
+    int src[MAP_MAX];
+};
 
 template <class Rl>
 __device__ __forceinline__ bool better(Rl v1, int i1, Rl v2, int i2) {
     return v1 > v2 || (v1 == v2 && i1 < i2);
 }
 
-template <class V, int NBP>
-__global__ void __launch_bounds__(PANEL_THREADS) panel_kernel(V A, int j0, int m, int ib, int R,
-                                                              int* __restrict__ ipiv, int* __restrict__ info) {
-    using CV = typename V::cv;
-    using Rl = typename V::real;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int cta = (int)cluster.block_rank();
-    const int CL = (int)cluster.num_blocks();
-    extern __shared__ __align__(16) unsigned char sm[];
-    CV* slab = reinterpret_cast<CV*>(sm);                     // [NBP][R]
-    CV* cand_row = slab + (size_t)NBP * R;                     // [2][MAX_CLUSTER][NBP]
-    CV* diag_row = cand_row + 2 * MAX_CLUSTER * NBP;           // [2][NBP]
-    Rl* cand_val = reinterpret_cast<Rl*>(diag_row + 2 * NBP);  // [2][MAX_CLUSTER]
-    int* cand_idx = reinterpret_cast<int*>(cand_val + 2 * MAX_CLUSTER);
-    Rl* red_val = reinterpret_cast<Rl*>(cand_idx + 2 * MAX_CLUSTER);  // [32]
-    int* red_idx = reinterpret_cast<int*>(red_val + 32);               // [32]
-
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-    const int rb = cta * R;
-    const int nloc = max(0, min(R, m - rb));
-
-    for (int c = 0; c < ib; ++c)
-        for (int r = tid; r < nloc; r += nth) slab[c * R + r] = A.get((long)j0 + rb + r, (long)j0 + c);
-
-    Rl bv = (Rl)-1;
-    int bi = INT_MAX;
-    for (int r = tid; r < nloc; r += nth) {
-        Rl v = cnorm1(slab[r]);
-        if (v > bv) {
-            bv = v;
-            bi = rb + r;
-        }
-    }
-    __syncthreads();
-    cluster.sync();  // every CTA of the cluster is running before remote shared-memory traffic
-
-    for (int c = 0; c < ib; ++c) {
-        const int par = c & 1;
-        // ---- CTA-wide argmax (max value, then smallest index) ----
-        for (int o = 16; o > 0; o >>= 1) {
-            Rl ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (better(ov, oi, bv, bi)) {
-                bv = ov;
-                bi = oi;
-            }
-        }
-        if (lane == 0) {
-            red_val[warp] = bv;
-            red_idx[warp] = bi;
-        }
-        __syncthreads();
-        Rl cv = red_val[0];
-        int ci = red_idx[0];
-        for (int w = 1; w < nwarp; ++w) {
-            if (better(red_val[w], red_idx[w], cv, ci)) {
-                cv = red_val[w];
-                ci = red_idx[w];
-            }
-        }
-        // ---- publish candidate row (and the diagonal row if owned) to every CTA ----
-        const bool own_diag = (c >= rb && c < rb + nloc);
-        for (int e = tid; e < CL * NBP; e += nth) {
-            int dst = e / NBP, col = e % NBP;
-            CV val = czero<Rl>();
-            if (ci != INT_MAX && col < ib) val = slab[col * R + (ci - rb)];
-            CV* rr = cluster.map_shared_rank(cand_row + (par * MAX_CLUSTER + cta) * NBP, dst);
-            rr[col] = val;
-            if (own_diag) {
-                CV* rd = cluster.map_shared_rank(diag_row + par * NBP, dst);
-                rd[col] = (col < ib) ? slab[col * R + (c - rb)] : czero<Rl>();
-            }
-            if (col == 0) {
-                Rl* rv = cluster.map_shared_rank(cand_val + par * MAX_CLUSTER + cta, dst);
-                int* ri = cluster.map_shared_rank(cand_idx + par * MAX_CLUSTER + cta, dst);
-                *rv = (ci != INT_MAX) ? cv : (Rl)-1;
-                *ri = ci;
-            }
-        }
-        cluster.sync();
-        // ---- pivot decision (identical in every CTA) ----
-        Rl pv = (Rl)-1;
-        int pi = INT_MAX, pq = 0;
-        for (int q = 0; q < CL; ++q) {
-            Rl v = cand_val[par * MAX_CLUSTER + q];
-            int ix = cand_idx[par * MAX_CLUSTER + q];
-            if (better(v, ix, pv, pi)) {
-                pv = v;
-                pi = ix;
-                pq = q;
-            }
-        }
-        const CV* u = cand_row + (par * MAX_CLUSTER + pq) * NBP;
-        const CV* drow = diag_row + par * NBP;
-        const bool sing = !(pv > (Rl)0);
-        if (cta == 0 && tid == 0) {
-            ipiv[j0 + c] = j0 + pi;
-            if (sing && info != nullptr && *info == 0) *info = j0 + c + 1;
-        }
-        if (!sing && pi != c) {
-            if (own_diag)
-                for (int col = tid; col < ib; col += nth) slab[col * R + (c - rb)] = u[col];
-            if (pi >= rb && pi < rb + nloc)
-                for (int col = tid; col < ib; col += nth) slab[col * R + (pi - rb)] = drow[col];
-        }
-        __syncthreads();
-        // ---- scale column c and rank-1 update of the local rows below the pivot ----
-        CV inv = sing ? czero<Rl>() : cinv(u[c]);
-        bv = (Rl)-1;
-        bi = INT_MAX;
-        for (int r = tid; r < nloc; r += nth) {
-            int gr = rb + r;
-            if (gr <= c) continue;
-            CV l = slab[c * R + r];
-            if (!sing) {
-                l = cmul(l, inv);
-                slab[c * R + r] = l;
-            }
-            CV nl;
-            nl.x = -l.x;
-            nl.y = -l.y;
-            for (int k2 = c + 1; k2 < ib; ++k2) {
-                CV a = slab[k2 * R + r];
-                cfma(a, nl, u[k2]);
-                slab[k2 * R + r] = a;
-            }
-            if (c + 1 < ib) {
-                Rl v = cnorm1(slab[(c + 1) * R + r]);
-                if (v > bv) {
-                    bv = v;
-                    bi = gr;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    for (int c = 0; c < ib; ++c)
-        for (int r = tid; r < nloc; r += nth) A.set((long)j0 + rb + r, (long)j0 + c, slab[c * R + r]);
-}
-
 // ------------------------------------------------------------------------------------------------
-// swap maps: the net effect of ib sequential interchanges (j0+k <-> ipiv[j0+k]) on the affected
-// rows, as new[dst[t]] = old[src[t]] for t < count.  One warp.
+// swap maps: the net effect of ib sequential interchanges (j0+k <-> ipiv[j0+k]) on the rows they
+// touch.  Run by one warp; s_* are shared scratch arrays of MAP_MAX/2 (pk, cidx, extra) and
+// MAP_MAX (content) ints.
 // ------------------------------------------------------------------------------------------------
-constexpr int MAP_MAX = 512;  // 2 * max NB (NB <= 256)
-struct SwapMap {
-    int count;
-    int dst[MAP_MAX];
-    int src[MAP_MAX];
-};
-
-__global__ void build_swap_map_kernel(const int* __restrict__ ipiv, int j0, int ib, SwapMap* __restrict__ out) {
-    __shared__ int pk[MAP_MAX / 2];
-    __shared__ int cidx[MAP_MAX / 2];
-    __shared__ int extra[MAP_MAX / 2];
-    __shared__ int content[MAP_MAX];
-    const int lane = threadIdx.x;
+__device__ void build_map_warp(const int* ipiv, int j0, int ib, SwapMap* out, int* pk, int* cidx, int* extra,
+                               int* content) {
+    const int lane = threadIdx.x & 31;
     for (int k = lane; k < ib; k += 32) pk[k] = ipiv[j0 + k];
     for (int t = lane; t < 2 * ib; t += 32) content[t] = t;
     __syncwarp();
@@ -226,8 +68,7 @@ __global__ void build_swap_map_kernel(const int* __restrict__ ipiv, int j0, int 
         if (p < j0 + ib) {
             ci = p - j0;
         } else {
-            // earlier k' with the same pivot row?
-            int found = INT_MAX;
+            int found = INT_MAX;  // earlier interchange with the same row?
             for (int base = 0; base < k; base += 32) {
                 int kk = base + lane;
                 bool hit = (kk < k) && (pk[kk] == p);
@@ -257,11 +98,267 @@ __global__ void build_swap_map_kernel(const int* __restrict__ ipiv, int j0, int 
     for (int t = lane; t < cnt; t += 32) {
         int d = (t < ib) ? j0 + t : extra[t - ib];
         int sidx = content[t];
-        int s = (sidx < ib) ? j0 + sidx : extra[sidx - ib];
+        int sr = (sidx < ib) ? j0 + sidx : extra[sidx - ib];
         out->dst[t] = d;
-        out->src[t] = s;
+        out->src[t] = sr;
     }
     if (lane == 0) out->count = cnt;
+    __syncwarp();
+}
+
+// apply a map to an int vector (the row order of the factorisation), one warp
+__device__ void apply_map_int_warp(const SwapMap* map, int* v) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = map->count;
+    int val[MAP_MAX / 32];
+#pragma unroll
+    for (int q = 0; q < MAP_MAX / 32; ++q) {
+        int t = lane + 32 * q;
+        if (t < cnt) val[q] = v[map->src[t]];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < MAP_MAX / 32; ++q) {
+        int t = lane + 32 * q;
+        if (t < cnt) v[map->dst[t]] = val[q];
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------------------
+// panel factorisation
+// ------------------------------------------------------------------------------------------------
+template <class CV, int NBP>
+__device__ __forceinline__ CV pick(const CV (&r)[NBP], int c) {
+    CV v = r[0];
+#pragma unroll
+    for (int k = 1; k < NBP; ++k)
+        if (k == c) v = r[k];
+    return v;
+}
+
+template <class V, int NBP, int RPT>
+__global__ void __launch_bounds__(PANEL_THREADS, 1)
+    panel_kernel(V A, int j0, int m, int ib, int R, int* __restrict__ ipiv, int* __restrict__ info, int J, int jb,
+                 SwapMap* __restrict__ map_inner, SwapMap* __restrict__ map_big, int* __restrict__ perm) {
+    using CV = typename V::cv;
+    using Rl = typename V::real;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cta = (int)cluster.block_rank();
+    const int CL = (int)cluster.num_blocks();
+    __shared__ CV cand_row[2][MAX_CLUSTER][NBP];
+    __shared__ CV diag_row[2][NBP];
+    __shared__ Rl cand_val[2][MAX_CLUSTER];
+    __shared__ int cand_idx[2][MAX_CLUSTER];
+    __shared__ CV ucur[2][NBP];   // local copies of the last two pivot rows
+    __shared__ CV mycand[NBP];    // this CTA's candidate row, staged for publishing
+    __shared__ CV mydiag[NBP];    // the diagonal row (if this CTA owns it), staged
+    __shared__ Rl red_val[PANEL_THREADS / 32];
+    __shared__ int red_idx[PANEL_THREADS / 32];
+    __shared__ int s_map[MAP_MAX / 2 * 3 + MAP_MAX];
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int rb = cta * R;
+    const int nloc = max(0, min(R, m - rb));
+    const CV zero = czero<Rl>();
+
+    CV row[RPT][NBP];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int lr = tid + q * PANEL_THREADS;
+#pragma unroll
+        for (int k = 0; k < NBP; ++k)
+            row[q][k] = (lr < nloc && k < ib) ? A.get((long)j0 + rb + lr, (long)j0 + k) : zero;
+    }
+    Rl bv = (Rl)-1;
+    int bi = INT_MAX;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int lr = tid + q * PANEL_THREADS;
+        if (lr < nloc) {
+            Rl v = cnorm1(row[q][0]);
+            if (v > bv) {
+                bv = v;
+                bi = rb + lr;
+            }
+        }
+    }
+    cluster.sync();  // every CTA of the cluster runs before remote shared-memory traffic
+
+    for (int c = 0; c < ib; ++c) {
+        const int par = c & 1;
+        const CV* uprev = ucur[par ^ 1];  // pivot row of column c-1 (valid for c > 0)
+        // ---- (1) CTA-wide argmax of column c: max |Re|+|Im|, then the smallest row ----
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Rl ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (better(ov, oi, bv, bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            red_val[warp] = bv;
+            red_idx[warp] = bi;
+        }
+        __syncthreads();
+        Rl cv = (lane < PANEL_THREADS / 32) ? red_val[lane] : (Rl)-1;
+        int ci = (lane < PANEL_THREADS / 32) ? red_idx[lane] : INT_MAX;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {  // whole warp, so every lane ends with the CTA result
+            Rl ov = __shfl_xor_sync(0xffffffffu, cv, o);
+            int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+            if (better(ov, oi, cv, ci)) {
+                cv = ov;
+                ci = oi;
+            }
+        }
+        // ---- (2) stage the candidate row and the diagonal row with pivot c-1's update applied ----
+        const bool own_diag = (c >= rb && c < rb + nloc);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int gr = rb + tid + q * PANEL_THREADS;
+            const bool is_cand = (gr == ci), is_diag = (gr == c);
+            if (is_cand || is_diag) {
+                CV lp = zero;
+                if (c > 0) {
+                    lp = pick<CV, NBP>(row[q], c - 1);
+                    lp.x = -lp.x;
+                    lp.y = -lp.y;
+                }
+#pragma unroll
+                for (int k = 0; k < NBP; ++k) {
+                    CV v = row[q][k];
+                    if (c > 0 && k > c) cfma(v, lp, uprev[k]);
+                    if (is_cand) mycand[k] = v;
+                    if (is_diag) mydiag[k] = v;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- (3) publish to every CTA, arrive ----
+        for (int e = tid; e < CL * NBP; e += PANEL_THREADS) {
+            const int dst = e / NBP, col = e % NBP;
+            CV* rr = cluster.map_shared_rank(&cand_row[par][cta][0], dst);
+            rr[col] = (ci != INT_MAX) ? mycand[col] : zero;
+            if (own_diag) {
+                CV* rd = cluster.map_shared_rank(&diag_row[par][0], dst);
+                rd[col] = mydiag[col];
+            }
+            if (col == 0) {
+                *cluster.map_shared_rank(&cand_val[par][cta], dst) = (ci != INT_MAX) ? cv : (Rl)-1;
+                *cluster.map_shared_rank(&cand_idx[par][cta], dst) = ci;
+            }
+        }
+        cluster.barrier_arrive();
+        // ---- (4) while the barrier completes: pivot c-1's update of columns c+1.. ----
+        if (c > 0) {
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int lr = tid + q * PANEL_THREADS;
+                if (lr < nloc && rb + lr > c - 1) {
+                    CV lp = pick<CV, NBP>(row[q], c - 1);
+                    lp.x = -lp.x;
+                    lp.y = -lp.y;
+#pragma unroll
+                    for (int k = 0; k < NBP; ++k)
+                        if (k > c) cfma(row[q][k], lp, uprev[k]);
+                }
+            }
+        }
+        cluster.barrier_wait();
+        // ---- (5) pivot decision for column c (identical in every CTA) ----
+        Rl pv = (Rl)-1;
+        int pi = INT_MAX, pq = 0;
+        for (int q = 0; q < CL; ++q) {
+            Rl v = cand_val[par][q];
+            int ix = cand_idx[par][q];
+            if (better(v, ix, pv, pi)) {
+                pv = v;
+                pi = ix;
+                pq = q;
+            }
+        }
+        const CV* u = &cand_row[par][pq][0];
+        const CV* drow = &diag_row[par][0];
+        const bool sing = !(pv > (Rl)0);
+        if (tid < NBP) ucur[par][tid] = u[tid];
+        if (cta == 0 && tid == 0) {
+            ipiv[j0 + c] = j0 + pi;
+            if (sing && info != nullptr && *info == 0) *info = j0 + c + 1;
+        }
+        // ---- (6) interchange rows c and pi ----
+        if (!sing && pi != c) {
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int gr = rb + tid + q * PANEL_THREADS;
+                if (gr == c) {
+#pragma unroll
+                    for (int k = 0; k < NBP; ++k) row[q][k] = u[k];
+                } else if (gr == pi) {
+#pragma unroll
+                    for (int k = 0; k < NBP; ++k) row[q][k] = drow[k];
+                }
+            }
+        }
+        // ---- (7) scale column c, update column c+1, argmax of column c+1 ----
+        const CV uc = u[0 + c];
+        const CV inv = sing ? zero : cinv(uc);
+        const CV un = (c + 1 < NBP) ? u[c + 1] : zero;
+        bv = (Rl)-1;
+        bi = INT_MAX;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int lr = tid + q * PANEL_THREADS;
+            const int gr = rb + lr;
+            if (lr < nloc && gr > c) {
+                CV l = pick<CV, NBP>(row[q], c);
+                if (!sing) l = cmul(l, inv);
+                CV nl;
+                nl.x = -l.x;
+                nl.y = -l.y;
+#pragma unroll
+                for (int k = 0; k < NBP; ++k) {
+                    if (k == c) row[q][k] = l;
+                    if (k == c + 1) {
+                        cfma(row[q][k], nl, un);
+                        Rl v = cnorm1(row[q][k]);
+                        if (v > bv) {
+                            bv = v;
+                            bi = gr;
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int lr = tid + q * PANEL_THREADS;
+        if (lr < nloc)
+#pragma unroll
+            for (int k = 0; k < NBP; ++k)
+                if (k < ib) A.set((long)j0 + rb + lr, (long)j0 + k, row[q][k]);
+    }
+    // ---- row-interchange maps (CTA 0, warp 0): this sub-panel's, and the big panel's at its end ----
+    if (cta == 0) {
+        __syncthreads();
+        __threadfence_block();
+        if (warp == 0) {
+            int* pk = s_map;
+            int* cidx = pk + MAP_MAX / 2;
+            int* extra = cidx + MAP_MAX / 2;
+            int* content = extra + MAP_MAX / 2;
+            if (map_inner) build_map_warp(ipiv, j0, ib, map_inner, pk, cidx, extra, content);
+            if (map_big && j0 + ib == J + jb) {
+                build_map_warp(ipiv, J, jb, map_big, pk, cidx, extra, content);
+                __threadfence_block();
+                if (perm) apply_map_int_warp(map_big, perm);
+            }
+        }
+    }
 }
 
 __device__ __forceinline__ float tf32_rna(float x) {
@@ -271,114 +368,114 @@ __device__ __forceinline__ float tf32_rna(float x) {
 }
 
 // Row interchanges (from a swap map) for columns in [a0, a1) u [b0, b1); for columns of the
-// second range also X = L11^{-1} X on rows [t0, t0+tb) with the unit-lower L11 at (t0, t0).
-// Optionally writes the solved rows as a K-major tensor-core pack (column c -> row c - b0).
-// One warp per column; also permutes `perm` (as one extra int column) when given.
+// second range also X = L11^{-1} X on rows [t0, t0+tb) with the unit-lower L11 at (t0, t0),
+// staged in shared memory when it fits.  Optionally writes the solved rows as a K-major
+// tensor-core pack (column c -> row c - b0).  One warp per column, COLS columns per warp.
+constexpr int ST_WARPS = 8, ST_COLS = 4;
 template <class V>
-__global__ void __launch_bounds__(256) swap_trsm_kernel(V A, const SwapMap* __restrict__ map, int a0, int a1,
-                                                         int b0, int b1, int t0, int tb, float* Upr, float* Upi,
-                                                         long ldk, int split, int* perm) {
+__global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const SwapMap* __restrict__ map, int a0, int a1,
+                                                                   int b0, int b1, int t0, int tb, float* Upr,
+                                                                   float* Upi, long ldk, int split, int l_in_smem) {
     using CV = typename V::cv;
     using Rl = typename V::real;
     constexpr int QMAX = 8;  // rows per lane: tb <= 256
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CV* Ls = reinterpret_cast<CV*>(smraw);  // tb x tb, column-major
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int na = a1 - a0, nbc = b1 - b0;
+    const int ncols = na + nbc;
+    const int cta_col0 = blockIdx.x * ST_WARPS * ST_COLS;
+    const bool cta_has_b = (cta_col0 + ST_WARPS * ST_COLS > na) && tb > 0;
+    if (cta_has_b && l_in_smem) {
+        for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) {
+            int i = e % tb, k = e / tb;
+            Ls[e] = (i > k) ? A.get((long)t0 + i, (long)t0 + k) : czero<Rl>();
+        }
+        __syncthreads();
+    }
     const int cnt = map ? map->count : 0;
-    if (gw == na + nbc && perm != nullptr && map != nullptr) {
-        // permute the row-order vector: perm_new[dst] = perm_old[src]
-        int v[MAP_MAX / 32];
+    for (int cc = 0; cc < ST_COLS; ++cc) {
+        const int gw = cta_col0 + warp * ST_COLS + cc;
+        if (gw >= ncols) break;
+        const bool in_b = gw >= na;
+        const long col = in_b ? (long)b0 + (gw - na) : (long)a0 + gw;
+        if (cnt > 0) {
+            CV v[MAP_MAX / 32];
 #pragma unroll
-        for (int q = 0; q < MAP_MAX / 32; ++q) {
-            int t = lane + 32 * q;
-            if (t < cnt) v[q] = perm[map->src[t]];
+            for (int q = 0; q < MAP_MAX / 32; ++q) {
+                int t = lane + 32 * q;
+                if (t < cnt) v[q] = A.get(map->src[t], col);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < MAP_MAX / 32; ++q) {
+                int t = lane + 32 * q;
+                if (t < cnt) A.set(map->dst[t], col, v[q]);
+            }
+            __syncwarp();
         }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < MAP_MAX / 32; ++q) {
-            int t = lane + 32 * q;
-            if (t < cnt) perm[map->dst[t]] = v[q];
-        }
-        return;
-    }
-    if (gw >= na + nbc) return;
-    const bool in_b = gw >= na;
-    const long col = in_b ? (long)b0 + (gw - na) : (long)a0 + gw;
-    // interchanges
-    if (cnt > 0) {
-        CV v[MAP_MAX / 32];
-#pragma unroll
-        for (int q = 0; q < MAP_MAX / 32; ++q) {
-            int t = lane + 32 * q;
-            if (t < cnt) v[q] = A.get(map->src[t], col);
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < MAP_MAX / 32; ++q) {
-            int t = lane + 32 * q;
-            if (t < cnt) A.set(map->dst[t], col, v[q]);
-        }
-        __syncwarp();
-    }
-    if (!in_b || tb <= 0) return;
-    // forward substitution with the unit-lower block (lanes own rows lane + 32 q)
-    CV x[QMAX];
-#pragma unroll
-    for (int q = 0; q < QMAX; ++q) {
-        int i = lane + 32 * q;
-        x[q] = (i < tb) ? A.get((long)t0 + i, col) : czero<Rl>();
-    }
-    for (int k = 0; k < tb; ++k) {
-        const int qk = k >> 5, lk = k & 31;
-        CV xk = czero<Rl>();
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q)
-            if (q == qk) xk = x[q];
-        xk.x = __shfl_sync(0xffffffffu, xk.x, lk);
-        xk.y = __shfl_sync(0xffffffffu, xk.y, lk);
-        CV nx;
-        nx.x = -xk.x;
-        nx.y = -xk.y;
+        if (!in_b || tb <= 0) continue;
+        CV x[QMAX];
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
             int i = lane + 32 * q;
-            if (q >= qk && i > k && i < tb) cfma(x[q], A.get((long)t0 + i, (long)t0 + k), nx);
+            x[q] = (i < tb) ? A.get((long)t0 + i, col) : czero<Rl>();
         }
-    }
+        for (int k = 0; k < tb; ++k) {
+            const int qk = k >> 5, lk = k & 31;
+            CV xk = czero<Rl>();
 #pragma unroll
-    for (int q = 0; q < QMAX; ++q) {
-        int i = lane + 32 * q;
-        if (i < tb) A.set((long)t0 + i, col, x[q]);
-    }
-    if (Upr != nullptr) {
-        // K-major pack of this column (row index = col - b0); segments [hi | lo | hi] when split
-        long row = col - b0;
-        float* pr = Upr + row * ldk;
-        float* pi = Upi + row * ldk;
+            for (int q = 0; q < QMAX; ++q)
+                if (q == qk) xk = x[q];
+            xk.x = __shfl_sync(0xffffffffu, xk.x, lk);
+            xk.y = __shfl_sync(0xffffffffu, xk.y, lk);
+            CV nx;
+            nx.x = -xk.x;
+            nx.y = -xk.y;
 #pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-            int i = lane + 32 * q;
-            if (i < tb) {
-                float vr = (float)x[q].x, vi = (float)x[q].y;
-                if (!split) {
-                    pr[i] = vr;
-                    pi[i] = vi;
-                } else {
-                    float hr = tf32_rna(vr), hi = tf32_rna(vi);
-                    pr[i] = hr;
-                    pi[i] = hi;
-                    pr[tb + i] = vr - hr;
-                    pi[tb + i] = vi - hi;
-                    pr[2 * tb + i] = hr;
-                    pi[2 * tb + i] = hi;
+            for (int q = 0; q < QMAX; ++q) {
+                int i = lane + 32 * q;
+                if (q >= qk && i > k && i < tb) {
+                    CV l = l_in_smem ? Ls[i + k * tb] : A.get((long)t0 + i, (long)t0 + k);
+                    cfma(x[q], l, nx);
                 }
             }
         }
-        long kext = split ? 3L * tb : (long)tb;
-        long kpad = (kext + 31) / 32 * 32;
-        for (long i = kext + lane; i < kpad; i += 32) {
-            pr[i] = 0.f;
-            pi[i] = 0.f;
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q) {
+            int i = lane + 32 * q;
+            if (i < tb) A.set((long)t0 + i, col, x[q]);
+        }
+        if (Upr != nullptr) {
+            // K-major pack of this column (row index = col - b0); segments [hi | lo | hi] when split
+            long rowp = col - b0;
+            float* pr = Upr + rowp * ldk;
+            float* pi = Upi + rowp * ldk;
+#pragma unroll
+            for (int q = 0; q < QMAX; ++q) {
+                int i = lane + 32 * q;
+                if (i < tb) {
+                    float vr = (float)x[q].x, vi = (float)x[q].y;
+                    if (!split) {
+                        pr[i] = vr;
+                        pi[i] = vi;
+                    } else {
+                        float hr = tf32_rna(vr), hi = tf32_rna(vi);
+                        pr[i] = hr;
+                        pi[i] = hi;
+                        pr[tb + i] = vr - hr;
+                        pi[tb + i] = vi - hi;
+                        pr[2 * tb + i] = hr;
+                        pi[2 * tb + i] = hi;
+                    }
+                }
+            }
+            long kext = split ? 3L * tb : (long)tb;
+            long kpad = (kext + 31) / 32 * 32;
+            for (long i = kext + lane; i < kpad; i += 32) {
+                pr[i] = 0.f;
+                pi[i] = 0.f;
+            }
         }
     }
 }
@@ -416,7 +513,6 @@ __global__ void pack_L_kernel(C32 A, long r0, long c0, int m, int kb, int split,
                 pi[2 * kb + k] = v.y - hi;
             }
         }
-        // zero padding (done by the first column block)
         if (blockIdx.x == 0)
             for (long kk = kext + tx; kk < kpad; kk += 32) {
                 pr[kk] = 0.f;
@@ -527,82 +623,84 @@ __global__ void gather_rows_c32_kernel(const int* __restrict__ perm, int n, int 
 // ------------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------------
-struct PanelCfg {
-    int nbp = 32;
-    int cl_max = 8;
+#define LU_CUDA(expr)                                                                                  \
+    do {                                                                                               \
+        cudaError_t _e = (expr);                                                                       \
+        if (_e != cudaSuccess) {                                                                       \
+            bm_set_error(std::string("lu: ") + #expr + ": " + cudaGetErrorString(_e));                 \
+            return BM_ECUDA;                                                                           \
+        }                                                                                              \
+    } while (0)
+
+struct PanelShape {
+    int CL, R, RPT, nbp;
 };
 
-template <class V, int NBP>
-cudaError_t launch_panel_t(cudaStream_t s, V A, int j0, int m, int ib, int cl_max, int* ipiv, int* info) {
-    using CV = typename V::cv;
-    const int rcap = (int)((200 * 1024 - 4096) / ((size_t)NBP * sizeof(CV)));
-    int CL = ceil_div(m, rcap);
-    if (CL < 1) CL = 1;
-    if (CL > cl_max) return cudaErrorInvalidValue;
+// cluster size, rows per CTA, rows per thread and sub-panel width for a panel of m rows
+template <class V>
+bool panel_shape(int m, int cl_max, PanelShape& ps) {
+    constexpr int W = std::is_same<V, C32>::value ? 32 : 16;  // widest sub-panel (1 row per thread)
+    int CL = std::min(cl_max, std::max(1, ceil_div(m, PANEL_THREADS)));
     int R = ceil_div(m, CL);
-    size_t smem = panel_smem_bytes<CV>(NBP, R);
-    auto kern = panel_kernel<V, NBP>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (CL > 8) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int RPT = ceil_div(R, PANEL_THREADS);
+    if (RPT > 4) return false;
+    if (RPT == 3) RPT = 4;
+    ps = PanelShape{CL, R, RPT, W / RPT};
+    return true;
+}
+
+template <class V, int NBP, int RPT>
+cudaError_t launch_panel_t(cudaStream_t s, V A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info,
+                           int J, int jb, SwapMap* mi, SwapMap* mb, int* perm) {
+    auto kern = panel_kernel<V, NBP, RPT>;
+    if (ps.CL > 8) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CL, 1, 1);
+    cfg.gridDim = dim3(ps.CL, 1, 1);
     cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.x = ps.CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, A, j0, m, ib, R, ipiv, info);
+    return cudaLaunchKernelEx(&cfg, kern, A, j0, m, ib, ps.R, ipiv, info, J, jb, mi, mb, perm);
 }
 
 template <class V>
-cudaError_t launch_panel(cudaStream_t s, V A, int nbp, int j0, int m, int ib, int cl_max, int* ipiv, int* info);
+cudaError_t launch_panel(cudaStream_t s, V A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info, int J,
+                         int jb, SwapMap* mi, SwapMap* mb, int* perm);
 template <>
-cudaError_t launch_panel<C32>(cudaStream_t s, C32 A, int nbp, int j0, int m, int ib, int cl_max, int* ipiv,
-                              int* info) {
-    if (nbp == 32) return launch_panel_t<C32, 32>(s, A, j0, m, ib, cl_max, ipiv, info);
-    if (nbp == 16) return launch_panel_t<C32, 16>(s, A, j0, m, ib, cl_max, ipiv, info);
-    return launch_panel_t<C32, 8>(s, A, j0, m, ib, cl_max, ipiv, info);
+cudaError_t launch_panel<C32>(cudaStream_t s, C32 A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info,
+                              int J, int jb, SwapMap* mi, SwapMap* mb, int* perm) {
+    if (ps.RPT == 1) return launch_panel_t<C32, 32, 1>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
+    if (ps.RPT == 2) return launch_panel_t<C32, 16, 2>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
+    return launch_panel_t<C32, 8, 4>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
 }
 template <>
-cudaError_t launch_panel<Z64>(cudaStream_t s, Z64 A, int nbp, int j0, int m, int ib, int cl_max, int* ipiv,
-                              int* info) {
-    if (nbp == 16) return launch_panel_t<Z64, 16>(s, A, j0, m, ib, cl_max, ipiv, info);
-    if (nbp == 8) return launch_panel_t<Z64, 8>(s, A, j0, m, ib, cl_max, ipiv, info);
-    return launch_panel_t<Z64, 4>(s, A, j0, m, ib, cl_max, ipiv, info);
-}
-
-template <class V>
-int pick_nbp(int n, int cl_max, int nbp_max) {
-    using CV = typename V::cv;
-    for (int nbp = nbp_max; nbp >= 4; nbp /= 2) {
-        int rcap = (int)((200 * 1024 - 4096) / ((size_t)nbp * sizeof(CV)));
-        if ((long)rcap * cl_max >= n) return nbp;
-    }
-    return -1;
+cudaError_t launch_panel<Z64>(cudaStream_t s, Z64 A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info,
+                              int J, int jb, SwapMap* mi, SwapMap* mb, int* perm) {
+    if (ps.RPT == 1) return launch_panel_t<Z64, 16, 1>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
+    if (ps.RPT == 2) return launch_panel_t<Z64, 8, 2>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
+    return launch_panel_t<Z64, 4, 4>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
 }
 
 template <class V>
 int query_cluster_max() {
     // largest cluster size (16 or 8) the device will co-schedule for the panel kernel
-    using CV = typename V::cv;
-    int nbp = 16;
-    size_t smem = panel_smem_bytes<CV>(nbp, 512);
-    auto kern = panel_kernel<V, 16>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 8;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 8;
+    auto kern = panel_kernel<V, std::is_same<V, C32>::value ? 32 : 16, 1>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
     cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 16;
@@ -620,12 +718,20 @@ int query_cluster_max() {
 
 template <class V>
 cudaError_t launch_swap_trsm(cudaStream_t s, V A, const SwapMap* map, int a0, int a1, int b0, int b1, int t0, int tb,
-                             float* Upr, float* Upi, long ldk, int split, int* perm) {
-    long ncols = (long)(a1 - a0) + (b1 - b0) + (perm ? 1 : 0);
+                             float* Upr, float* Upi, long ldk, int split) {
+    using CV = typename V::cv;
+    long ncols = (long)(a1 - a0) + (b1 - b0);
     if (ncols <= 0) return cudaSuccess;
-    long threads = ncols * 32;
-    swap_trsm_kernel<V><<<ceil_div(threads, 256), 256, 0, s>>>(A, map, a0, a1, b0, b1, t0, tb, Upr, Upi, ldk, split,
-                                                                perm);
+    size_t lbytes = (size_t)tb * tb * sizeof(CV);
+    int l_in_smem = (tb > 0 && lbytes <= 160 * 1024) ? 1 : 0;
+    size_t smem = l_in_smem ? lbytes : 0;
+    auto kern = swap_trsm_kernel<V>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int grid = ceil_div(ncols, ST_WARPS * ST_COLS);
+    kern<<<grid, ST_WARPS * 32, smem, s>>>(A, map, a0, a1, b0, b1, t0, tb, Upr, Upi, ldk, split, l_in_smem);
     return cudaGetLastError();
 }
 
@@ -636,50 +742,37 @@ cudaError_t gemm_any(cudaStream_t s, int m, int n, int k, C32 A, C32 B, C32 C) {
     return gemm_c32(s, m, n, k, -1.0f, A, false, B, 1.0f, C);
 }
 
-#define LU_CUDA(expr)                                                                                  \
-    do {                                                                                               \
-        cudaError_t _e = (expr);                                                                       \
-        if (_e != cudaSuccess) {                                                                       \
-            bm_set_error(std::string("lu: ") + #expr + ": " + cudaGetErrorString(_e));                 \
-            return BM_ECUDA;                                                                           \
-        }                                                                                              \
-    } while (0)
-
 template <class V>
 bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
     cudaStream_t s = c->stream;
     const int n = c->n;
     const int NB = c->nb;
     const int cl_max = c->panel_cluster;
-    const int nbp = pick_nbp<V>(n, cl_max, std::is_same<V, C32>::value ? 32 : 16);
-    if (nbp < 0) {
-        bm_set_error("lu: system too large for the panel kernel");
-        return BM_EINVAL;
-    }
     SwapMap* d_map = reinterpret_cast<SwapMap*>(c->d_maps);  // big-panel map
     SwapMap* d_map2 = d_map + 1;                              // sub-panel map
     iota_kernel<<<ceil_div(n, 256), 256, 0, s>>>(c->d_perm, n);
     LU_CUDA(cudaGetLastError());
     for (int J = 0; J < n; J += NB) {
         const int jb = std::min(NB, n - J);
-        for (int j = J; j < J + jb; j += nbp) {
-            const int ib = std::min(nbp, J + jb - j);
-            LU_CUDA(launch_panel<V>(s, F, nbp, j, n - j, ib, cl_max, c->d_ipiv, c->d_info));
+        for (int j = J; j < J + jb;) {
+            PanelShape ps;
+            if (!panel_shape<V>(n - j, cl_max, ps)) {
+                bm_set_error("lu: system too large for the panel kernel");
+                return BM_EINVAL;
+            }
+            const int ib = std::min(ps.nbp, J + jb - j);
+            LU_CUDA(launch_panel<V>(s, F, ps, j, n - j, ib, c->d_ipiv, c->d_info, J, jb, d_map2, d_map, c->d_perm));
             if (jb > ib) {
-                build_swap_map_kernel<<<1, 32, 0, s>>>(c->d_ipiv, j, ib, d_map2);
-                LU_CUDA(cudaGetLastError());
-                LU_CUDA(launch_swap_trsm<V>(s, F, d_map2, J, j, j + ib, J + jb, j, ib, nullptr, nullptr, 0, 0,
-                                            nullptr));
+                LU_CUDA(launch_swap_trsm<V>(s, F, d_map2, J, j, j + ib, J + jb, j, ib, nullptr, nullptr, 0, 0));
                 if (j + ib < J + jb)
                     LU_CUDA(gemm_any(s, n - j - ib, J + jb - j - ib, ib, F.sub(j + ib, j), F.sub(j, j + ib),
                                      F.sub(j + ib, j + ib)));
             }
+            j += ib;
         }
-        build_swap_map_kernel<<<1, 32, 0, s>>>(c->d_ipiv, J, jb, d_map);
-        LU_CUDA(cudaGetLastError());
         const bool pack = tc && (J + jb < n);
         LU_CUDA(launch_swap_trsm<V>(s, F, d_map, 0, J, J + jb, n, J, jb, pack ? c->d_Up_r : nullptr,
-                                    pack ? c->d_Up_i : nullptr, c->ldk_lu, split, c->d_perm));
+                                    pack ? c->d_Up_i : nullptr, c->ldk_lu, split));
         if (J + jb < n) {
             const int mm = n - J - jb;
             if (tc) {
@@ -738,6 +831,12 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, int nrhs, const typename V::cv* dinvL, co
 bm_status lu_setup(bm_ctx* c) {
     if (c->panel_cluster == 0) {
         c->panel_cluster = (c->prec == BM_FP64) ? query_cluster_max<Z64>() : query_cluster_max<C32>();
+        // BM_PANEL_CLUSTER_MAX caps the panel cluster (1..16); fewer CTAs put more rows on
+        // each thread, which selects the narrower sub-panel variants
+        if (const char* e = getenv("BM_PANEL_CLUSTER_MAX")) {
+            int v = atoi(e);
+            if (v >= 1 && v <= 16) c->panel_cluster = std::min(c->panel_cluster, v);
+        }
     }
     return BM_OK;
 }

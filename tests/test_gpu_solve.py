@@ -104,6 +104,32 @@ def test_mixed_precision_refinement(bmlib, handle, prec, form, resid):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("clmax,N", [(1, 600), (1, 1100), (2, 1100)])
+def test_panel_variants_match_oracle(bmlib, monkeypatch, prec, clmax, N):
+    # Capping the panel cluster puts 2 (N=600, cap 1; N=1100, cap 2) or 4 (N=1100, cap 1) rows on
+    # each panel thread, which selects the narrower register-resident sub-panel kernels.
+    monkeypatch.setenv("BM_PANEL_CLUSTER_MAX", str(clmax))
+    h = bmlib.bm_create(0)
+    try:
+        curve, k0, k1 = W.ellipse(1.0, 0.6), 6.0 - 0.1j, 9.0 - 0.15j
+        bmlib.bm_assemble(h, curve.kind, curve.params4(), N, k0, k1, bmlib.BM_MIXED, bmlib.make_opts(prec))
+        assert bmlib.bm_factor(h) == 0
+        g, P = O.nodes(curve, N), O.default_params(k0, k1)
+        B = _rhs(g, P, N, W.MIXED, 3, full=True, seed=5)
+        X = np.zeros_like(B, order="F")
+        info = bmlib.bm_solve(h, B, X)
+        blocks = O.mixed_blocks(g, P)
+        if prec == 0:
+            assert _relerr(X, schur_solve(blocks, B)) < 1e-10
+        else:
+            assert info.backward_error <= 1e-9
+            assert O.backward_error_mixed(blocks, X, B) <= 1.5e-9
+    finally:
+        bmlib.bm_destroy(h)
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("form", [0, 1])
 def test_double_float_residual_reaches_tight_tolerance(bmlib, handle, form):
     # Refinement can only certify what its residual resolves: reaching 2e-12 through the
