@@ -23,343 +23,11 @@
 // Solves (getrs): Y = P B, then block forward substitution with the unit L and block back
 // substitution with U; the bs x bs diagonal blocks are inverted once after the factorisation so
 // that every step is a small matrix product.
-#include "common.cuh"
-#include "kernels.cuh"
+#include "lu_internal.cuh"
 
-#include <cooperative_groups.h>
-#include <algorithm>
-#include <climits>
-#include <type_traits>
-
-namespace cg = cooperative_groups;
+using namespace lu_detail;
 
 namespace {
-
-constexpr int PANEL_THREADS = 512;
-constexpr int MAX_CLUSTER = 16;
-constexpr int MAP_MAX = 512;  // 2 * max NB (NB <= 256)
-
-struct SwapMap {  // new[dst[t]] = old[src[t]], t < count
-    int count;
-    int dst[MAP_MAX];
-    int src[MAP_MAX];
-};
-
-template <class Rl>
-__device__ __forceinline__ bool better(Rl v1, int i1, Rl v2, int i2) {
-    return v1 > v2 || (v1 == v2 && i1 < i2);
-}
-
-// ------------------------------------------------------------------------------------------------
-// swap maps: the net effect of ib sequential interchanges (j0+k <-> ipiv[j0+k]) on the rows they
-// touch.  Run by one warp; s_* are shared scratch arrays of MAP_MAX/2 (pk, cidx, extra) and
-// MAP_MAX (content) ints.
-// ------------------------------------------------------------------------------------------------
-__device__ void build_map_warp(const int* ipiv, int j0, int ib, SwapMap* out, int* pk, int* cidx, int* extra,
-                               int* content) {
-    const int lane = threadIdx.x & 31;
-    for (int k = lane; k < ib; k += 32) pk[k] = ipiv[j0 + k];
-    for (int t = lane; t < 2 * ib; t += 32) content[t] = t;
-    __syncwarp();
-    int nextra = 0;
-    for (int k = 0; k < ib; ++k) {
-        int p = pk[k];
-        int ci;
-        if (p < j0 + ib) {
-            ci = p - j0;
-        } else {
-            int found = INT_MAX;  // earlier interchange with the same row?
-            for (int base = 0; base < k; base += 32) {
-                int kk = base + lane;
-                bool hit = (kk < k) && (pk[kk] == p);
-                unsigned b = __ballot_sync(0xffffffffu, hit);
-                if (b) {
-                    found = base + __ffs(b) - 1;
-                    break;
-                }
-            }
-            if (found != INT_MAX) {
-                ci = cidx[found];
-            } else {
-                ci = ib + nextra;
-                if (lane == 0) extra[nextra] = p;
-                ++nextra;
-            }
-        }
-        if (lane == 0) {
-            cidx[k] = ci;
-            int t = content[k];
-            content[k] = content[ci];
-            content[ci] = t;
-        }
-        __syncwarp();
-    }
-    int cnt = ib + nextra;
-    for (int t = lane; t < cnt; t += 32) {
-        int d = (t < ib) ? j0 + t : extra[t - ib];
-        int sidx = content[t];
-        int sr = (sidx < ib) ? j0 + sidx : extra[sidx - ib];
-        out->dst[t] = d;
-        out->src[t] = sr;
-    }
-    if (lane == 0) out->count = cnt;
-    __syncwarp();
-}
-
-// apply a map to an int vector (the row order of the factorisation), one warp
-__device__ void apply_map_int_warp(const SwapMap* map, int* v) {
-    const int lane = threadIdx.x & 31;
-    const int cnt = map->count;
-    int val[MAP_MAX / 32];
-#pragma unroll
-    for (int q = 0; q < MAP_MAX / 32; ++q) {
-        int t = lane + 32 * q;
-        if (t < cnt) val[q] = v[map->src[t]];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < MAP_MAX / 32; ++q) {
-        int t = lane + 32 * q;
-        if (t < cnt) v[map->dst[t]] = val[q];
-    }
-    __syncwarp();
-}
-
-// ------------------------------------------------------------------------------------------------
-// panel factorisation
-// ------------------------------------------------------------------------------------------------
-template <class CV, int NBP>
-__device__ __forceinline__ CV pick(const CV (&r)[NBP], int c) {
-    CV v = r[0];
-#pragma unroll
-    for (int k = 1; k < NBP; ++k)
-        if (k == c) v = r[k];
-    return v;
-}
-
-template <class V, int NBP, int RPT>
-__global__ void __launch_bounds__(PANEL_THREADS, 1)
-    panel_kernel(V A, int j0, int m, int ib, int R, int* __restrict__ ipiv, int* __restrict__ info, int J, int jb,
-                 SwapMap* __restrict__ map_inner, SwapMap* __restrict__ map_big, int* __restrict__ perm) {
-    using CV = typename V::cv;
-    using Rl = typename V::real;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int cta = (int)cluster.block_rank();
-    const int CL = (int)cluster.num_blocks();
-    __shared__ CV cand_row[2][MAX_CLUSTER][NBP];
-    __shared__ CV diag_row[2][NBP];
-    __shared__ Rl cand_val[2][MAX_CLUSTER];
-    __shared__ int cand_idx[2][MAX_CLUSTER];
-    __shared__ CV ucur[2][NBP];   // local copies of the last two pivot rows
-    __shared__ CV mycand[NBP];    // this CTA's candidate row, staged for publishing
-    __shared__ CV mydiag[NBP];    // the diagonal row (if this CTA owns it), staged
-    __shared__ Rl red_val[PANEL_THREADS / 32];
-    __shared__ int red_idx[PANEL_THREADS / 32];
-    __shared__ int s_map[MAP_MAX / 2 * 3 + MAP_MAX];
-
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int rb = cta * R;
-    const int nloc = max(0, min(R, m - rb));
-    const CV zero = czero<Rl>();
-
-    CV row[RPT][NBP];
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        const int lr = tid + q * PANEL_THREADS;
-#pragma unroll
-        for (int k = 0; k < NBP; ++k)
-            row[q][k] = (lr < nloc && k < ib) ? A.get((long)j0 + rb + lr, (long)j0 + k) : zero;
-    }
-    Rl bv = (Rl)-1;
-    int bi = INT_MAX;
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        const int lr = tid + q * PANEL_THREADS;
-        if (lr < nloc) {
-            Rl v = cnorm1(row[q][0]);
-            if (v > bv) {
-                bv = v;
-                bi = rb + lr;
-            }
-        }
-    }
-    cluster.sync();  // every CTA of the cluster runs before remote shared-memory traffic
-
-    for (int c = 0; c < ib; ++c) {
-        const int par = c & 1;
-        const CV* uprev = ucur[par ^ 1];  // pivot row of column c-1 (valid for c > 0)
-        // ---- (1) CTA-wide argmax of column c: max |Re|+|Im|, then the smallest row ----
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            Rl ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (better(ov, oi, bv, bi)) {
-                bv = ov;
-                bi = oi;
-            }
-        }
-        if (lane == 0) {
-            red_val[warp] = bv;
-            red_idx[warp] = bi;
-        }
-        __syncthreads();
-        Rl cv = (lane < PANEL_THREADS / 32) ? red_val[lane] : (Rl)-1;
-        int ci = (lane < PANEL_THREADS / 32) ? red_idx[lane] : INT_MAX;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {  // whole warp, so every lane ends with the CTA result
-            Rl ov = __shfl_xor_sync(0xffffffffu, cv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, ci, o);
-            if (better(ov, oi, cv, ci)) {
-                cv = ov;
-                ci = oi;
-            }
-        }
-        // ---- (2) stage the candidate row and the diagonal row with pivot c-1's update applied ----
-        const bool own_diag = (c >= rb && c < rb + nloc);
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-            const int gr = rb + tid + q * PANEL_THREADS;
-            const bool is_cand = (gr == ci), is_diag = (gr == c);
-            if (is_cand || is_diag) {
-                CV lp = zero;
-                if (c > 0) {
-                    lp = pick<CV, NBP>(row[q], c - 1);
-                    lp.x = -lp.x;
-                    lp.y = -lp.y;
-                }
-#pragma unroll
-                for (int k = 0; k < NBP; ++k) {
-                    CV v = row[q][k];
-                    if (c > 0 && k > c) cfma(v, lp, uprev[k]);
-                    if (is_cand) mycand[k] = v;
-                    if (is_diag) mydiag[k] = v;
-                }
-            }
-        }
-        __syncthreads();
-        // ---- (3) publish to every CTA, arrive ----
-        for (int e = tid; e < CL * NBP; e += PANEL_THREADS) {
-            const int dst = e / NBP, col = e % NBP;
-            CV* rr = cluster.map_shared_rank(&cand_row[par][cta][0], dst);
-            rr[col] = (ci != INT_MAX) ? mycand[col] : zero;
-            if (own_diag) {
-                CV* rd = cluster.map_shared_rank(&diag_row[par][0], dst);
-                rd[col] = mydiag[col];
-            }
-            if (col == 0) {
-                *cluster.map_shared_rank(&cand_val[par][cta], dst) = (ci != INT_MAX) ? cv : (Rl)-1;
-                *cluster.map_shared_rank(&cand_idx[par][cta], dst) = ci;
-            }
-        }
-        cluster.barrier_arrive();
-        // ---- (4) while the barrier completes: pivot c-1's update of columns c+1.. ----
-        if (c > 0) {
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                const int lr = tid + q * PANEL_THREADS;
-                if (lr < nloc && rb + lr > c - 1) {
-                    CV lp = pick<CV, NBP>(row[q], c - 1);
-                    lp.x = -lp.x;
-                    lp.y = -lp.y;
-#pragma unroll
-                    for (int k = 0; k < NBP; ++k)
-                        if (k > c) cfma(row[q][k], lp, uprev[k]);
-                }
-            }
-        }
-        cluster.barrier_wait();
-        // ---- (5) pivot decision for column c (identical in every CTA) ----
-        Rl pv = (Rl)-1;
-        int pi = INT_MAX, pq = 0;
-        for (int q = 0; q < CL; ++q) {
-            Rl v = cand_val[par][q];
-            int ix = cand_idx[par][q];
-            if (better(v, ix, pv, pi)) {
-                pv = v;
-                pi = ix;
-                pq = q;
-            }
-        }
-        const CV* u = &cand_row[par][pq][0];
-        const CV* drow = &diag_row[par][0];
-        const bool sing = !(pv > (Rl)0);
-        if (tid < NBP) ucur[par][tid] = u[tid];
-        if (cta == 0 && tid == 0) {
-            ipiv[j0 + c] = j0 + pi;
-            if (sing && info != nullptr && *info == 0) *info = j0 + c + 1;
-        }
-        // ---- (6) interchange rows c and pi ----
-        if (!sing && pi != c) {
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                const int gr = rb + tid + q * PANEL_THREADS;
-                if (gr == c) {
-#pragma unroll
-                    for (int k = 0; k < NBP; ++k) row[q][k] = u[k];
-                } else if (gr == pi) {
-#pragma unroll
-                    for (int k = 0; k < NBP; ++k) row[q][k] = drow[k];
-                }
-            }
-        }
-        // ---- (7) scale column c, update column c+1, argmax of column c+1 ----
-        const CV uc = u[0 + c];
-        const CV inv = sing ? zero : cinv(uc);
-        const CV un = (c + 1 < NBP) ? u[c + 1] : zero;
-        bv = (Rl)-1;
-        bi = INT_MAX;
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-            const int lr = tid + q * PANEL_THREADS;
-            const int gr = rb + lr;
-            if (lr < nloc && gr > c) {
-                CV l = pick<CV, NBP>(row[q], c);
-                if (!sing) l = cmul(l, inv);
-                CV nl;
-                nl.x = -l.x;
-                nl.y = -l.y;
-#pragma unroll
-                for (int k = 0; k < NBP; ++k) {
-                    if (k == c) row[q][k] = l;
-                    if (k == c + 1) {
-                        cfma(row[q][k], nl, un);
-                        Rl v = cnorm1(row[q][k]);
-                        if (v > bv) {
-                            bv = v;
-                            bi = gr;
-                        }
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        const int lr = tid + q * PANEL_THREADS;
-        if (lr < nloc)
-#pragma unroll
-            for (int k = 0; k < NBP; ++k)
-                if (k < ib) A.set((long)j0 + rb + lr, (long)j0 + k, row[q][k]);
-    }
-    // ---- row-interchange maps (CTA 0, warp 0): this sub-panel's, and the big panel's at its end ----
-    if (cta == 0) {
-        __syncthreads();
-        __threadfence_block();
-        if (warp == 0) {
-            int* pk = s_map;
-            int* cidx = pk + MAP_MAX / 2;
-            int* extra = cidx + MAP_MAX / 2;
-            int* content = extra + MAP_MAX / 2;
-            if (map_inner) build_map_warp(ipiv, j0, ib, map_inner, pk, cidx, extra, content);
-            if (map_big && j0 + ib == J + jb) {
-                build_map_warp(ipiv, J, jb, map_big, pk, cidx, extra, content);
-                __threadfence_block();
-                if (perm) apply_map_int_warp(map_big, perm);
-            }
-        }
-    }
-}
 
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
@@ -371,7 +39,7 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // second range also X = L11^{-1} X on rows [t0, t0+tb) with the unit-lower L11 at (t0, t0),
 // staged in shared memory when it fits.  Optionally writes the solved rows as a K-major
 // tensor-core pack (column c -> row c - b0).  One warp per column, COLS columns per warp.
-constexpr int ST_WARPS = 8, ST_COLS = 4;
+constexpr int ST_WARPS = 16, ST_COLS = 1;
 template <class V>
 __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const SwapMap* __restrict__ map, int a0, int a1,
                                                                    int b0, int b1, int t0, int tb, float* Upr,
@@ -632,90 +300,6 @@ __global__ void gather_rows_c32_kernel(const int* __restrict__ perm, int n, int 
         }                                                                                              \
     } while (0)
 
-struct PanelShape {
-    int CL, R, RPT, nbp;
-};
-
-// cluster size, rows per CTA, rows per thread and sub-panel width for a panel of m rows
-template <class V>
-bool panel_shape(int m, int cl_max, PanelShape& ps) {
-    constexpr int W = std::is_same<V, C32>::value ? 32 : 16;  // widest sub-panel (1 row per thread)
-    int CL = std::min(cl_max, std::max(1, ceil_div(m, PANEL_THREADS)));
-    int R = ceil_div(m, CL);
-    int RPT = ceil_div(R, PANEL_THREADS);
-    if (RPT > 4) return false;
-    if (RPT == 3) RPT = 4;
-    ps = PanelShape{CL, R, RPT, W / RPT};
-    return true;
-}
-
-template <class V, int NBP, int RPT>
-cudaError_t launch_panel_t(cudaStream_t s, V A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info,
-                           int J, int jb, SwapMap* mi, SwapMap* mb, int* perm) {
-    auto kern = panel_kernel<V, NBP, RPT>;
-    if (ps.CL > 8) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ps.CL, 1, 1);
-    cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = ps.CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, A, j0, m, ib, ps.R, ipiv, info, J, jb, mi, mb, perm);
-}
-
-template <class V>
-cudaError_t launch_panel(cudaStream_t s, V A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info, int J,
-                         int jb, SwapMap* mi, SwapMap* mb, int* perm);
-template <>
-cudaError_t launch_panel<C32>(cudaStream_t s, C32 A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info,
-                              int J, int jb, SwapMap* mi, SwapMap* mb, int* perm) {
-    if (ps.RPT == 1) return launch_panel_t<C32, 32, 1>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
-    if (ps.RPT == 2) return launch_panel_t<C32, 16, 2>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
-    return launch_panel_t<C32, 8, 4>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
-}
-template <>
-cudaError_t launch_panel<Z64>(cudaStream_t s, Z64 A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info,
-                              int J, int jb, SwapMap* mi, SwapMap* mb, int* perm) {
-    if (ps.RPT == 1) return launch_panel_t<Z64, 16, 1>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
-    if (ps.RPT == 2) return launch_panel_t<Z64, 8, 2>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
-    return launch_panel_t<Z64, 4, 4>(s, A, ps, j0, m, ib, ipiv, info, J, jb, mi, mb, perm);
-}
-
-template <class V>
-int query_cluster_max() {
-    // largest cluster size (16 or 8) the device will co-schedule for the panel kernel
-    auto kern = panel_kernel<V, std::is_same<V, C32>::value ? 32 : 16, 1>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-        cudaGetLastError();
-        return 8;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(16, 1, 1);
-    cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 16;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return 8;
-    }
-    return ncl >= 1 ? 16 : 8;
-}
-
 template <class V>
 cudaError_t launch_swap_trsm(cudaStream_t s, V A, const SwapMap* map, int a0, int a1, int b0, int b1, int t0, int tb,
                              float* Upr, float* Upi, long ldk, int split) {
@@ -761,7 +345,7 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
                 return BM_EINVAL;
             }
             const int ib = std::min(ps.nbp, J + jb - j);
-            LU_CUDA(launch_panel<V>(s, F, ps, j, n - j, ib, c->d_ipiv, c->d_info, J, jb, d_map2, d_map, c->d_perm));
+            LU_CUDA(launch_panel(s, F, ps, j, n - j, ib, c->d_ipiv, c->d_info, J, jb, d_map2, d_map, c->d_perm));
             if (jb > ib) {
                 LU_CUDA(launch_swap_trsm<V>(s, F, d_map2, J, j, j + ib, J + jb, j, ib, nullptr, nullptr, 0, 0));
                 if (j + ib < J + jb)
@@ -830,7 +414,7 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, int nrhs, const typename V::cv* dinvL, co
 
 bm_status lu_setup(bm_ctx* c) {
     if (c->panel_cluster == 0) {
-        c->panel_cluster = (c->prec == BM_FP64) ? query_cluster_max<Z64>() : query_cluster_max<C32>();
+        c->panel_cluster = (c->prec == BM_FP64) ? query_cluster_max_z64() : query_cluster_max_c32();
         // BM_PANEL_CLUSTER_MAX caps the panel cluster (1..16); fewer CTAs put more rows on
         // each thread, which selects the narrower sub-panel variants
         if (const char* e = getenv("BM_PANEL_CLUSTER_MAX")) {
