@@ -107,6 +107,9 @@ void free_solve_ws(bm_ctx* c) {
     FREE(c->d_W2i);
     FREE(c->d_Y64);
     FREE(c->d_Y64b);
+    FREE(c->d_Zw64);
+    FREE(c->d_Zwr);
+    FREE(c->d_Zwi);
     c->ws_nrhs = 0;
     c->last_nrhs = 0;
     drop_solve_graphs(c);
@@ -119,6 +122,9 @@ void free_problem(bm_ctx* c) {
     FREE(c->d_Mtop);
     FREE(c->d_Mbot);
     FREE(c->d_A);
+    FREE(c->d_Ptop);
+    FREE(c->d_Pbot);
+    FREE(c->d_PA);
     FREE(c->d_F64);
     FREE(c->d_F32r);
     FREE(c->d_F32i);
@@ -170,6 +176,9 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
         b += (size_t)p.ldF * p.n * 16;
     } else {
         b += (size_t)p.ldF * p.n * 8;
+        // split hi/lo planes of the FP64 operator (same size as the FP64 blocks)
+        b += (form == BM_MIXED) ? (size_t)p.ldtop * N * 16 + (size_t)p.ldbot * 2 * N * 16
+                                : (size_t)p.ldA * 2 * N * 16;
         if (form == BM_MIXED) {
             p.kseg = 2 * N;
             long kext = split ? 3L * p.kseg : p.kseg;
@@ -402,6 +411,14 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     }
     if (s == BM_OK && !c32) s = alloc_t(c, &c->d_F64, (size_t)p.ldF * p.n * 16);
     if (s == BM_OK && c32) {
+        if (form == BM_MIXED) {
+            s = alloc_t(c, &c->d_Ptop, (size_t)p.ldtop * N * 16);
+            if (s == BM_OK) s = alloc_t(c, &c->d_Pbot, (size_t)p.ldbot * 2 * N * 16);
+        } else {
+            s = alloc_t(c, &c->d_PA, (size_t)p.ldA * 2 * N * 16);
+        }
+    }
+    if (s == BM_OK && c32) {
         s = alloc_t(c, &c->d_F32r, (size_t)p.ldF * p.n * 4);
         if (s == BM_OK) s = alloc_t(c, &c->d_F32i, (size_t)p.ldF * p.n * 4);
         if (s == BM_OK && form == BM_MIXED) {
@@ -455,7 +472,12 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     if (c32) {
         if (form == BM_MIXED) {
             BM_CUDA_TRY(launch_pack_schur(st, c, prec == BM_CF32_3XTF32_IR));
-            c->launches += 3;
+            BM_CUDA_TRY(launch_split_planes(st, c->d_Mtop, c->ldtop, 2 * N, N, c->d_Ptop, c->ldtop));
+            BM_CUDA_TRY(launch_split_planes(st, c->d_Mbot, c->ldbot, N, 2 * N, c->d_Pbot, c->ldbot));
+            c->launches += 5;
+        } else {
+            BM_CUDA_TRY(launch_split_planes(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_PA, c->ldA));
+            c->launches += 1;
         }
     }
     BM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -601,13 +623,17 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
     size_t yb = (size_t)c->n * w * 16;
     BM_TRY(alloc_t(c, &c->d_Y64, yb));
     BM_TRY(alloc_t(c, &c->d_Y64b, yb));
-    if (c->prec != BM_FP64) {
+    if (c->prec == BM_FP64) {
+        BM_TRY(alloc_t(c, &c->d_Zw64, yb));
+    } else {
         size_t fb = (size_t)c->nsys * w * 4;
         BM_TRY(alloc_t(c, &c->d_Wr, fb));
         BM_TRY(alloc_t(c, &c->d_Wi, fb));
         size_t vb = (size_t)c->n * w * 4;
         BM_TRY(alloc_t(c, &c->d_W2r, vb));
         BM_TRY(alloc_t(c, &c->d_W2i, vb));
+        BM_TRY(alloc_t(c, &c->d_Zwr, vb));
+        BM_TRY(alloc_t(c, &c->d_Zwi, vb));
     }
     c->ws_nrhs = w;
     return BM_OK;

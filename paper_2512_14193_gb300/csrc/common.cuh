@@ -99,6 +99,20 @@ struct C32 {
     BM_HD C32 sub(long i, long j) const { return C32{re + i + j * ld, im + i + j * ld, ld}; }
 };
 
+// F4Hi: read-only view of the hi parts of split FP64 planes (float4 = re_hi, re_lo, im_hi, im_lo)
+struct F4Hi {
+    using real = float;
+    using cv = float2;
+    const float4* p;
+    long ld;
+    BM_HD cv get(long i, long j) const {
+        float4 v = p[i + j * ld];
+        return make_float2(v.x, v.z);
+    }
+    BM_HD void set(long, long, cv) const {}
+    BM_HD F4Hi sub(long i, long j) const { return F4Hi{p + i + j * ld, ld}; }
+};
+
 // ---------------------------------------------------------------------------------------------
 // Error handling
 // ---------------------------------------------------------------------------------------------
@@ -177,6 +191,11 @@ struct bm_ctx {
     double2* d_A = nullptr;
     long ldA = 0;
     double* d_normA = nullptr;  // ||A||_inf (device scalar)
+    // the FP64 operator split into FP32 hi/lo planes (CF32 precisions; same layout and leading
+    // dimensions as d_Mtop / d_Mbot / d_A) for the double-float residual
+    float4* d_Ptop = nullptr;
+    float4* d_Pbot = nullptr;
+    float4* d_PA = nullptr;
 
     // factorisation storage
     double2* d_F64 = nullptr;  // FP64 LU (n x n, ld ldF)
@@ -219,6 +238,9 @@ struct bm_ctx {
     float* d_W2i = nullptr;
     double2* d_Y64 = nullptr; // FP64 work for the FP64 solve
     double2* d_Y64b = nullptr;
+    double2* d_Zw64 = nullptr;  // n x nrhs work buffers of the blocked triangular solves
+    float* d_Zwr = nullptr;
+    float* d_Zwi = nullptr;
     double* d_colred = nullptr;  // per-column reductions (4 x nrhs)
 
     // cached graphs (with the number of kernel nodes each replay launches)

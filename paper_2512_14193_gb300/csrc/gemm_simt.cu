@@ -165,3 +165,9 @@ cudaError_t gemm_update_z64_c32(cudaStream_t s, int m, int n, int k, float alpha
     if (k <= 0) return cudaSuccess;
     return launch_impl<Z64, C32, Z64, float, false>(s, m, n, k, A, B, C, alpha, 1.0f);
 }
+
+// C (FP64) += alpha A_hi (FP32 hi parts of split planes) B (FP32 planar), FP32 arithmetic
+cudaError_t gemm_update_f4hi_c32(cudaStream_t s, int m, int n, int k, float alpha, F4Hi A, C32 B, Z64 C) {
+    if (k <= 0) return cudaSuccess;
+    return launch_impl<F4Hi, C32, Z64, float, false>(s, m, n, k, A, B, C, alpha, 1.0f);
+}

@@ -45,7 +45,10 @@ bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int n
 bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs);
 bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs);
 
-// resid_df.cu: C += alpha A X in double-float arithmetic (A, X, C FP64 column-major)
-cudaError_t gemm_df(cudaStream_t s, int m, int n, int k, double alpha, const double2* A, long lda, const double2* X,
+// resid_df.cu: C += alpha A X in double-float arithmetic (A as split planes, X and C FP64)
+cudaError_t gemm_df(cudaStream_t s, int m, int n, int k, double alpha, const float4* A, long lda, const double2* X,
                     long ldx, double2* C, long ldc);
+cudaError_t launch_split_planes(cudaStream_t s, const double2* A, long lda, int m, int n, float4* P, long ldp);
+// gemm_simt.cu: C (FP64) += alpha A_hi B with A the hi parts of split planes, FP32 arithmetic
+cudaError_t gemm_update_f4hi_c32(cudaStream_t s, int m, int n, int k, float alpha, F4Hi A, C32 B, Z64 C);
 cudaError_t launch_copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd);

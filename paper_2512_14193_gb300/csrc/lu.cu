@@ -249,25 +249,62 @@ __global__ void tri_inv_kernel(V F, int n, int bs, typename V::cv* __restrict__ 
     for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) out[(long)b * bs * bs + e] = X[e];
 }
 
-// Y[r0:r0+rb, :] = Tinv * Y[r0:r0+rb, :] in place (one CTA per 32 right-hand sides)
-template <class V>
-__global__ void apply_inv_kernel(V Y, int r0, int rb, int nrhs, int bs, const typename V::cv* __restrict__ Tinv) {
+// One block step of a blocked triangular solve with inverted diagonal blocks (one launch per
+// block, all right-hand sides):
+//   Zb = Tinv Y[r0:r0+rb, :]                          (written to Z by the CTAs of row tile 0)
+//   Y[rest0:rest0+nrest, :] -= F[rest0.., r0:r0+rb] Zb (each CTA one 64-row tile of the rest)
+// Forward (unit L) and backward (U) passes use the same kernel with the rows below or above the
+// block as the rest; Z is a second buffer, so no CTA reads a block that another one rewrites.
+constexpr int TS_BM = 64;
+template <class V, int BN>
+__global__ void __launch_bounds__(256) trsv_step_kernel(V F, V Y, V Z, int r0, int rb, int rest0, int nrest, int nrhs,
+                                                        int bs, const typename V::cv* __restrict__ Tinv) {
     using CV = typename V::cv;
     using Rl = typename V::real;
     extern __shared__ __align__(16) unsigned char sm[];
-    CV* Ys = reinterpret_cast<CV*>(sm);  // [32][bs]
-    const int c0 = blockIdx.x * 32;
-    const int nc = min(32, nrhs - c0);
-    for (int e = threadIdx.x; e < bs * 32; e += blockDim.x) {
-        int i = e % bs, cc = e / bs;
-        Ys[cc * bs + i] = (i < rb && cc < nc) ? Y.get((long)r0 + i, (long)c0 + cc) : czero<Rl>();
+    CV* Ts = reinterpret_cast<CV*>(sm);  // [bs][bs] column-major
+    CV* Yb = Ts + bs * bs;               // [BN][bs]
+    CV* Zb = Yb + BN * bs;               // [BN][bs]
+    CV* Ft = Zb + BN * bs;               // [bs][TS_BM] column-major tile of F
+    const int t = threadIdx.x;
+    const int j0 = blockIdx.y * BN;
+    const int nc = min(BN, nrhs - j0);
+    for (int e = t; e < bs * bs; e += 256) Ts[e] = Tinv[e];
+    for (int e = t; e < bs * BN; e += 256) {
+        int i = e % bs, jj = e / bs;
+        Yb[jj * bs + i] = (i < rb && jj < nc) ? Y.get((long)r0 + i, (long)j0 + jj) : czero<Rl>();
+    }
+    const long tr0 = (long)rest0 + (long)blockIdx.x * TS_BM;
+    const int tm = (int)min((long)TS_BM, (long)rest0 + nrest - tr0);
+    if (nrest > 0)
+        for (int e = t; e < TS_BM * bs; e += 256) {
+            int i = e % TS_BM, k = e / TS_BM;
+            Ft[k * TS_BM + i] = (i < tm && k < rb) ? F.get(tr0 + i, (long)r0 + k) : czero<Rl>();
+        }
+    __syncthreads();
+    for (int e = t; e < bs * BN; e += 256) {
+        int i = e % bs, jj = e / bs;
+        CV s = czero<Rl>();
+        if (i < rb)
+            for (int k = 0; k < rb; ++k) cfma(s, Ts[i + k * bs], Yb[jj * bs + k]);
+        Zb[jj * bs + i] = s;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < rb * nc; e += blockDim.x) {
-        int i = e % rb, cc = e / rb;
+    if (blockIdx.x == 0)
+        for (int e = t; e < bs * BN; e += 256) {
+            int i = e % bs, jj = e / bs;
+            if (i < rb && jj < nc) Z.set((long)r0 + i, (long)j0 + jj, Zb[jj * bs + i]);
+        }
+    if (nrest <= 0) return;
+    for (int e = t; e < TS_BM * BN; e += 256) {
+        int i = e % TS_BM, jj = e / TS_BM;
+        if (i >= tm || jj >= nc) continue;
         CV s = czero<Rl>();
-        for (int k = 0; k < rb; ++k) cfma(s, Tinv[i + (long)k * bs], Ys[cc * bs + k]);
-        Y.set((long)r0 + i, (long)c0 + cc, s);
+        for (int k = 0; k < rb; ++k) cfma(s, Ft[k * TS_BM + i], Zb[jj * bs + k]);
+        CV y = Y.get(tr0 + i, (long)j0 + jj);
+        y.x -= s.x;
+        y.y -= s.y;
+        Y.set(tr0 + i, (long)j0 + jj, y);
     }
 }
 
@@ -387,25 +424,35 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
     return BM_OK;
 }
 
+template <class V, int BN>
+cudaError_t launch_trsv_step(cudaStream_t s, V F, V Y, V Z, int r0, int rb, int rest0, int nrest, int nrhs, int bs,
+                             const typename V::cv* Tinv) {
+    size_t smem = ((size_t)bs * bs + 2 * (size_t)BN * bs + (size_t)bs * TS_BM) * sizeof(typename V::cv);
+    auto kern = trsv_step_kernel<V, BN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(std::max(1, ceil_div(nrest, TS_BM)), ceil_div(nrhs, BN));
+    kern<<<grid, 256, smem, s>>>(F, Y, Z, r0, rb, rest0, nrest, nrhs, bs, Tinv);
+    return cudaGetLastError();
+}
+
+// Solve L U X = Y in place (Y holds P B); Zw is an n x nrhs work buffer.
 template <class V>
-bm_status getrs_t(bm_ctx* c, V F, V Y, int nrhs, const typename V::cv* dinvL, const typename V::cv* dinvU) {
+bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* dinvL, const typename V::cv* dinvU) {
     cudaStream_t s = c->stream;
     const int n = c->n, bs = c->bs_solve;
     const int nblk = ceil_div(n, bs);
-    size_t smem = (size_t)32 * bs * sizeof(typename V::cv);
-    LU_CUDA(cudaFuncSetAttribute(apply_inv_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int ncta = ceil_div(nrhs, 32);
-    for (int b = 0; b < nblk; ++b) {
+    auto step = [&](V Yv, V Zv, int r0, int rb, int rest0, int nrest, const typename V::cv* T) {
+        return nrhs > 16 ? launch_trsv_step<V, 32>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T)
+                         : launch_trsv_step<V, 16>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T);
+    };
+    for (int b = 0; b < nblk; ++b) {  // Zw = L^{-1} Y
         int r0 = b * bs, rb = std::min(bs, n - r0);
-        apply_inv_kernel<V><<<ncta, 256, smem, s>>>(Y, r0, rb, nrhs, bs, dinvL + (long)b * bs * bs);
-        LU_CUDA(cudaGetLastError());
-        if (r0 + rb < n) LU_CUDA(gemm_any(s, n - r0 - rb, nrhs, rb, F.sub(r0 + rb, r0), Y.sub(r0, 0), Y.sub(r0 + rb, 0)));
+        LU_CUDA(step(Y, Zw, r0, rb, r0 + rb, n - r0 - rb, dinvL + (long)b * bs * bs));
     }
-    for (int b = nblk - 1; b >= 0; --b) {
+    for (int b = nblk - 1; b >= 0; --b) {  // Y = U^{-1} Zw
         int r0 = b * bs, rb = std::min(bs, n - r0);
-        apply_inv_kernel<V><<<ncta, 256, smem, s>>>(Y, r0, rb, nrhs, bs, dinvU + (long)b * bs * bs);
-        LU_CUDA(cudaGetLastError());
-        if (r0 > 0) LU_CUDA(gemm_any(s, r0, nrhs, rb, F.sub(0, r0), Y.sub(r0, 0), Y.sub(0, 0)));
+        LU_CUDA(step(Zw, Y, r0, rb, 0, r0, dinvU + (long)b * bs * bs));
     }
     return BM_OK;
 }
@@ -438,14 +485,16 @@ bm_status lu_factor_enqueue(bm_ctx* c) {
 bm_status getrs_z64(bm_ctx* c, double2* Y, long ldy, int nrhs) {
     Z64 F{c->d_F64, c->ldF};
     Z64 Yv{Y, ldy};
-    return getrs_t<Z64>(c, F, Yv, nrhs, reinterpret_cast<const double2*>(c->d_dinvL),
+    Z64 Zv{c->d_Zw64, (long)c->n};
+    return getrs_t<Z64>(c, F, Yv, Zv, nrhs, reinterpret_cast<const double2*>(c->d_dinvL),
                         reinterpret_cast<const double2*>(c->d_dinvU));
 }
 
 bm_status getrs_c32(bm_ctx* c, float* Yr, float* Yi, long ldy, int nrhs) {
     C32 F{c->d_F32r, c->d_F32i, c->ldF};
     C32 Yv{Yr, Yi, ldy};
-    return getrs_t<C32>(c, F, Yv, nrhs, reinterpret_cast<const float2*>(c->d_dinvL),
+    C32 Zv{c->d_Zwr, c->d_Zwi, (long)c->n};
+    return getrs_t<C32>(c, F, Yv, Zv, nrhs, reinterpret_cast<const float2*>(c->d_dinvL),
                         reinterpret_cast<const float2*>(c->d_dinvU));
 }
 

@@ -1,10 +1,11 @@
-// Refinement residual r = beta r + alpha A x in double-float arithmetic on the FP32 cores.
+// Refinement residual r = r + alpha A x in double-float arithmetic on the FP32 cores.
 //
 // GB300 runs FP64 at ~1.2 TFLOP/s but FP32 at ~73 TFLOP/s, so the residual of iterative
 // refinement (the only step that needs more than FP32 accuracy) is computed with pairs of FP32
 // numbers instead of FP64:
-//   * each FP64 operand is split once, when its tile is staged in shared memory, into
-//     hi = fl32(a) and lo = fl32(a - hi) (a = hi + lo to ~2^-48 relative);
+//   * the FP64 operator is split once after assembly into float4 planes (re_hi, re_lo, im_hi,
+//     im_lo) with hi = fl32(a), lo = fl32(a - hi) (a = hi + lo to ~2^-48 relative); the iterate
+//     x is split the same way when its tile is staged in shared memory;
 //   * the leading product hi_a * hi_x is formed exactly as p + e with one FMA (TwoProd) and
 //     accumulated into an unevaluated pair (s, t) with TwoSum (Knuth), so the long sum of
 //     K = N..2N products keeps ~46 bits;
@@ -19,16 +20,12 @@ namespace {
 
 constexpr int BM = 64, BN = 16, BK = 16;
 
-struct df4 {  // a complex FP64 value split into FP32 hi/lo parts
-    float rh, rl, ih, il;
-};
-
-__device__ __forceinline__ df4 split(double2 v) {
-    df4 s;
-    s.rh = (float)v.x;
-    s.rl = (float)(v.x - (double)s.rh);
-    s.ih = (float)v.y;
-    s.il = (float)(v.y - (double)s.ih);
+__device__ __forceinline__ float4 split(double2 v) {
+    float4 s;
+    s.x = (float)v.x;
+    s.y = (float)(v.x - (double)s.x);
+    s.z = (float)v.y;
+    s.w = (float)(v.y - (double)s.z);
     return s;
 }
 
@@ -48,29 +45,29 @@ struct DfAcc {
     float rs, rt, is, it, rc, ic;  // real (sum, compensation), imag (sum, compensation), cross terms
 };
 
-__device__ __forceinline__ void dfma(DfAcc& c, const df4& a, const df4& x) {
-    // re += ar xr - ai xi ; im += ar xi + ai xr (hi parts exact, cross terms in FP32)
-    acc2(c.rs, c.rt, a.rh, x.rh);
-    acc2(c.rs, c.rt, -a.ih, x.ih);
-    acc2(c.is, c.it, a.rh, x.ih);
-    acc2(c.is, c.it, a.ih, x.rh);
-    c.rc = fmaf(a.rh, x.rl, c.rc);
-    c.rc = fmaf(a.rl, x.rh, c.rc);
-    c.rc = fmaf(-a.ih, x.il, c.rc);
-    c.rc = fmaf(-a.il, x.ih, c.rc);
-    c.ic = fmaf(a.rh, x.il, c.ic);
-    c.ic = fmaf(a.rl, x.ih, c.ic);
-    c.ic = fmaf(a.ih, x.rl, c.ic);
-    c.ic = fmaf(a.il, x.rh, c.ic);
+// a = (re_hi, re_lo, im_hi, im_lo), x likewise
+__device__ __forceinline__ void dfma(DfAcc& c, const float4& a, const float4& x) {
+    acc2(c.rs, c.rt, a.x, x.x);
+    acc2(c.rs, c.rt, -a.z, x.z);
+    acc2(c.is, c.it, a.x, x.z);
+    acc2(c.is, c.it, a.z, x.x);
+    c.rc = fmaf(a.x, x.y, c.rc);
+    c.rc = fmaf(a.y, x.x, c.rc);
+    c.rc = fmaf(-a.z, x.w, c.rc);
+    c.rc = fmaf(-a.w, x.z, c.rc);
+    c.ic = fmaf(a.x, x.w, c.ic);
+    c.ic = fmaf(a.y, x.z, c.ic);
+    c.ic = fmaf(a.z, x.y, c.ic);
+    c.ic = fmaf(a.w, x.x, c.ic);
 }
 
-// C (m x n) = C + alpha A (m x k) X (k x n); all FP64 interleaved column-major
-__global__ void __launch_bounds__(256) resid_df_kernel(int m, int n, int k, const double2* __restrict__ A, long lda,
+// C (m x n, FP64) += alpha A (m x k, split planes) X (k x n, FP64)
+__global__ void __launch_bounds__(256) resid_df_kernel(int m, int n, int k, const float4* __restrict__ A, long lda,
                                                        const double2* __restrict__ X, long ldx, double2* C, long ldc,
                                                        double alpha) {
     constexpr int TM = BM / 16;
-    __shared__ df4 As[BK][BM + 1];
-    __shared__ df4 Xs[BK][BN + 1];
+    __shared__ float4 As[BK][BM + 1];
+    __shared__ float4 Xs[BK][BN + 1];
     const int t = threadIdx.x;
     const int tx = t % 16, ty = t / 16;
     const long i0 = (long)blockIdx.x * BM, j0 = (long)blockIdx.y * BN;
@@ -83,8 +80,7 @@ __global__ void __launch_bounds__(256) resid_df_kernel(int m, int n, int k, cons
             int ii = e % BM, kk = e / BM;
             long gi = i0 + ii;
             int gk = k0 + kk;
-            double2 v = (gi < m && gk < k) ? A[gi + (long)gk * lda] : make_double2(0.0, 0.0);
-            As[kk][ii] = split(v);
+            As[kk][ii] = (gi < m && gk < k) ? __ldg(A + gi + (long)gk * lda) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         {
             int kk = t % BK, jj = t / BK;  // BN * BK == 256
@@ -96,7 +92,7 @@ __global__ void __launch_bounds__(256) resid_df_kernel(int m, int n, int k, cons
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < BK; ++kk) {
-            df4 xv = Xs[kk][ty];
+            float4 xv = Xs[kk][ty];
 #pragma unroll
             for (int a = 0; a < TM; ++a) dfma(acc[a], As[kk][tx + 16 * a], xv);
         }
@@ -116,12 +112,28 @@ __global__ void __launch_bounds__(256) resid_df_kernel(int m, int n, int k, cons
     }
 }
 
+__global__ void split_planes_kernel(const double2* __restrict__ A, long lda, int m, int n, float4* __restrict__ P,
+                                    long ldp) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)m * n) return;
+    int j = (int)(idx / m), i = (int)(idx % m);
+    P[i + (long)j * ldp] = split(A[i + (long)j * lda]);
+}
+
 }  // namespace
 
-cudaError_t gemm_df(cudaStream_t s, int m, int n, int k, double alpha, const double2* A, long lda, const double2* X,
+cudaError_t gemm_df(cudaStream_t s, int m, int n, int k, double alpha, const float4* A, long lda, const double2* X,
                     long ldx, double2* C, long ldc) {
     if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
     dim3 grid(ceil_div(m, BM), ceil_div(n, BN));
     resid_df_kernel<<<grid, 256, 0, s>>>(m, n, k, A, lda, X, ldx, C, ldc, alpha);
+    return cudaGetLastError();
+}
+
+// P = split(A): float4 (re_hi, re_lo, im_hi, im_lo) planes of an FP64 column-major matrix
+cudaError_t launch_split_planes(cudaStream_t s, const double2* A, long lda, int m, int n, float4* P, long ldp) {
+    long t = (long)m * n;
+    if (t == 0) return cudaSuccess;
+    split_planes_kernel<<<ceil_div(t, 256), 256, 0, s>>>(A, lda, m, n, P, ldp);
     return cudaGetLastError();
 }

@@ -197,10 +197,10 @@ bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R,
     resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
     SV_CUDA(cudaGetLastError());
     if (c->form == BM_MIXED) {
-        SV_CUDA(gemm_df(s, 2 * N, nrhs, N, -1.0, c->d_Mtop, c->ldtop, X + 2 * N, ld, R, ld));
-        SV_CUDA(gemm_df(s, N, nrhs, 2 * N, -1.0, c->d_Mbot, c->ldbot, X, ld, R + 2 * N, ld));
+        SV_CUDA(gemm_df(s, 2 * N, nrhs, N, -1.0, c->d_Ptop, c->ldtop, X + 2 * N, ld, R, ld));
+        SV_CUDA(gemm_df(s, N, nrhs, 2 * N, -1.0, c->d_Pbot, c->ldbot, X, ld, R + 2 * N, ld));
     } else {
-        SV_CUDA(gemm_df(s, 2 * N, nrhs, 2 * N, -1.0, c->d_A, c->ldA, X, ld, R, ld));
+        SV_CUDA(gemm_df(s, 2 * N, nrhs, 2 * N, -1.0, c->d_PA, c->ldA, X, ld, R, ld));
     }
     return BM_OK;
 }
@@ -277,12 +277,12 @@ bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs) {
         long t2 = (long)2 * N * nrhs;
         sub_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(R, ld, 0, 2 * N, nrhs, c->d_Wr, c->d_Wi, ldw);
         SV_CUDA(cudaGetLastError());
-        SV_CUDA(gemm_update_z64_c32(s, 2 * N, nrhs, N, -1.0f, Z64{c->d_Mtop, c->ldtop}, C32{c->d_W2r, c->d_W2i, ldv},
+        SV_CUDA(gemm_update_f4hi_c32(s, 2 * N, nrhs, N, -1.0f, F4Hi{c->d_Ptop, c->ldtop}, C32{c->d_W2r, c->d_W2i, ldv},
                                     Z64{R, ld}));
-        SV_CUDA(gemm_update_z64_c32(s, N, nrhs, 2 * N, -1.0f, Z64{c->d_Mbot, c->ldbot}, C32{c->d_Wr, c->d_Wi, ldw},
+        SV_CUDA(gemm_update_f4hi_c32(s, N, nrhs, 2 * N, -1.0f, F4Hi{c->d_Pbot, c->ldbot}, C32{c->d_Wr, c->d_Wi, ldw},
                                     Z64{R + 2 * N, ld}));
     } else {
-        SV_CUDA(gemm_update_z64_c32(s, 2 * N, nrhs, 2 * N, -1.0f, Z64{c->d_A, c->ldA}, C32{c->d_W2r, c->d_W2i, ldv},
+        SV_CUDA(gemm_update_f4hi_c32(s, 2 * N, nrhs, 2 * N, -1.0f, F4Hi{c->d_PA, c->ldA}, C32{c->d_W2r, c->d_W2i, ldv},
                                     Z64{R, ld}));
     }
     return BM_OK;
