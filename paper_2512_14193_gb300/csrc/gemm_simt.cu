@@ -120,8 +120,19 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, VA
 template <class VA, class VB, class VC, class R, bool AT>
 cudaError_t launch_impl(cudaStream_t s, int m, int n, int k, VA A, VB B, VC C, R alpha, R beta) {
     if (m <= 0 || n <= 0) return cudaSuccess;
-    // column tile with the least padding (ties go to the wider tile): n = 65 right-hand sides
-    // run as 5 x 16 columns instead of 2 x 64
+    // Few right-hand sides (n <= 80, e.g. 65): one column tile covers them all, so A is streamed
+    // once; 32-row tiles when 64-row ones would leave SMs idle.
+    if (n > 32 && n <= 80) {
+        if ((long)ceil_div(m, 64) >= 2 * 152) {
+            cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 80><<<dim3(ceil_div(m, 64), 1), 256, 0, s>>>(m, n, k, A, B, C,
+                                                                                                alpha, beta);
+        } else {
+            cgemm_simt_kernel<VA, VB, VC, R, AT, 32, 80><<<dim3(ceil_div(m, 32), 1), 256, 0, s>>>(m, n, k, A, B, C,
+                                                                                                alpha, beta);
+        }
+        return cudaGetLastError();
+    }
+    // otherwise the column tile with the least padding (ties go to the wider tile)
     int bn = 64;
     long best = (long)ceil_div(n, 64) * 64 - n;
     for (int cand : {32, 16}) {

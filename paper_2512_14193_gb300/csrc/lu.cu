@@ -282,12 +282,32 @@ __global__ void __launch_bounds__(256) trsv_step_kernel(V F, V Y, V Z, int r0, i
             Ft[k * TS_BM + i] = (i < tm && k < rb) ? F.get(tr0 + i, (long)r0 + k) : czero<Rl>();
         }
     __syncthreads();
-    for (int e = t; e < bs * BN; e += 256) {
-        int i = e % bs, jj = e / bs;
-        CV s = czero<Rl>();
-        if (i < rb)
-            for (int k = 0; k < rb; ++k) cfma(s, Ts[i + k * bs], Yb[jj * bs + k]);
-        Zb[jj * bs + i] = s;
+    // register micro-tiles: thread (tx, ty) owns rows tx + 16a (a < bs/16) and columns ty + 16b
+    constexpr int TN = BN / 16;
+    const int tx = t % 16, ty = t / 16;
+    const int TMb = bs / 16;  // bs is 64: 4 rows per thread
+    {
+        CV acc[4][TN];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) acc[a][b] = czero<Rl>();
+        for (int k = 0; k < rb; ++k) {
+            CV tv[4], yv[TN];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) tv[a] = (a < TMb) ? Ts[tx + 16 * a + k * bs] : czero<Rl>();
+#pragma unroll
+            for (int b = 0; b < TN; ++b) yv[b] = Yb[(ty + 16 * b) * bs + k];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < TN; ++b) cfma(acc[a][b], tv[a], yv[b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b)
+                if (a < TMb) Zb[(ty + 16 * b) * bs + tx + 16 * a] = acc[a][b];
     }
     __syncthreads();
     if (blockIdx.x == 0)
@@ -296,15 +316,35 @@ __global__ void __launch_bounds__(256) trsv_step_kernel(V F, V Y, V Z, int r0, i
             if (i < rb && jj < nc) Z.set((long)r0 + i, (long)j0 + jj, Zb[jj * bs + i]);
         }
     if (nrest <= 0) return;
-    for (int e = t; e < TS_BM * BN; e += 256) {
-        int i = e % TS_BM, jj = e / TS_BM;
-        if (i >= tm || jj >= nc) continue;
-        CV s = czero<Rl>();
-        for (int k = 0; k < rb; ++k) cfma(s, Ft[k * TS_BM + i], Zb[jj * bs + k]);
-        CV y = Y.get(tr0 + i, (long)j0 + jj);
-        y.x -= s.x;
-        y.y -= s.y;
-        Y.set(tr0 + i, (long)j0 + jj, y);
+    CV acc[4][TN];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = czero<Rl>();
+    for (int k = 0; k < rb; ++k) {
+        CV fv[4], zv[TN];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fv[a] = Ft[k * TS_BM + tx + 16 * a];
+#pragma unroll
+        for (int b = 0; b < TN; ++b) zv[b] = Zb[(ty + 16 * b) * bs + k];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) cfma(acc[a][b], fv[a], zv[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = tx + 16 * a;
+        if (i >= tm) continue;
+#pragma unroll
+        for (int b = 0; b < TN; ++b) {
+            const int jj = ty + 16 * b;
+            if (jj >= nc) continue;
+            CV y = Y.get(tr0 + i, (long)j0 + jj);
+            y.x -= acc[a][b].x;
+            y.y -= acc[a][b].y;
+            Y.set(tr0 + i, (long)j0 + jj, y);
+        }
     }
 }
 

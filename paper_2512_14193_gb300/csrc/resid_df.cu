@@ -18,7 +18,7 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 16, BK = 16;
+constexpr int BM = 128, BN = 16, BK = 16;  // 8 rows x 1 column per thread
 
 __device__ __forceinline__ float4 split(double2 v) {
     float4 s;
@@ -41,16 +41,18 @@ __device__ __forceinline__ void acc2(float& s, float& t, float a, float b) {
     t += err + e;
 }
 
+// Four compensated sums, one per real partial product, so their TwoSum chains run side by side.
 struct DfAcc {
-    float rs, rt, is, it, rc, ic;  // real (sum, compensation), imag (sum, compensation), cross terms
+    float s1, t1, s2, t2, s3, t3, s4, t4;  // ar xr, -ai xi (real); ar xi, ai xr (imag)
+    float rc, ic;                          // cross terms (FP32)
 };
 
 // a = (re_hi, re_lo, im_hi, im_lo), x likewise
 __device__ __forceinline__ void dfma(DfAcc& c, const float4& a, const float4& x) {
-    acc2(c.rs, c.rt, a.x, x.x);
-    acc2(c.rs, c.rt, -a.z, x.z);
-    acc2(c.is, c.it, a.x, x.z);
-    acc2(c.is, c.it, a.z, x.x);
+    acc2(c.s1, c.t1, a.x, x.x);
+    acc2(c.s2, c.t2, -a.z, x.z);
+    acc2(c.s3, c.t3, a.x, x.z);
+    acc2(c.s4, c.t4, a.z, x.x);
     c.rc = fmaf(a.x, x.y, c.rc);
     c.rc = fmaf(a.y, x.x, c.rc);
     c.rc = fmaf(-a.z, x.w, c.rc);
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(256) resid_df_kernel(int m, int n, int k, cons
     const long i0 = (long)blockIdx.x * BM, j0 = (long)blockIdx.y * BN;
     DfAcc acc[TM];
 #pragma unroll
-    for (int a = 0; a < TM; ++a) acc[a] = DfAcc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int a = 0; a < TM; ++a) acc[a] = DfAcc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k0 = 0; k0 < k; k0 += BK) {
 #pragma unroll
         for (int e = t; e < BM * BK; e += 256) {
@@ -104,8 +106,8 @@ __global__ void __launch_bounds__(256) resid_df_kernel(int m, int n, int k, cons
     for (int a = 0; a < TM; ++a) {
         long gi = i0 + tx + 16 * a;
         if (gi >= m) continue;
-        double re = (double)acc[a].rs + (double)acc[a].rt + (double)acc[a].rc;
-        double im = (double)acc[a].is + (double)acc[a].it + (double)acc[a].ic;
+        double re = ((double)acc[a].s1 + (double)acc[a].t1) + ((double)acc[a].s2 + (double)acc[a].t2) + (double)acc[a].rc;
+        double im = ((double)acc[a].s3 + (double)acc[a].t3) + ((double)acc[a].s4 + (double)acc[a].t4) + (double)acc[a].ic;
         double2& c = C[gi + gj * ldc];
         c.x += alpha * re;
         c.y += alpha * im;

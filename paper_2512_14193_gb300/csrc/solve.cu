@@ -42,14 +42,20 @@ __global__ void eta_kernel(const double2* __restrict__ R, const double2* __restr
     int c = blockIdx.x;
     double r = 0, x = 0, b = 0;
     bool bad = false;
+    // magnitudes in FP32 (the ratio needs a few digits; FP64 hypot would cost the FP64 pipe)
+    float rf = 0.f, xf = 0.f, bf = 0.f;
     for (int i = threadIdx.x; i < nsys; i += blockDim.x) {
         long o = i + (long)c * ld;
         double2 bv = B[o];
         if (!isfinite(bv.x) || !isfinite(bv.y)) bad = true;
-        r = fmax(r, hypot(R[o].x, R[o].y));
-        x = fmax(x, hypot(X[o].x, X[o].y));
-        b = fmax(b, hypot(bv.x, bv.y));
+        double2 rv = R[o], xv = X[o];
+        rf = fmaxf(rf, hypotf((float)rv.x, (float)rv.y));
+        xf = fmaxf(xf, hypotf((float)xv.x, (float)xv.y));
+        bf = fmaxf(bf, hypotf((float)bv.x, (float)bv.y));
     }
+    r = rf;
+    x = xf;
+    b = bf;
     __shared__ double sr[32], sx[32], sb[32];
     __shared__ int sbad;
     if (threadIdx.x == 0) sbad = 0;
