@@ -18,7 +18,7 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 16, BK = 16;  // 8 rows x 1 column per thread
+constexpr int BM = 64, BN = 16, BK = 16;  // 4 rows x 1 column per thread
 
 __device__ __forceinline__ float4 split(double2 v) {
     float4 s;
