@@ -110,6 +110,13 @@ void free_solve_ws(bm_ctx* c) {
     FREE(c->d_Zw64);
     FREE(c->d_Zwr);
     FREE(c->d_Zwi);
+    FREE(c->d_Bx1r);
+    FREE(c->d_Bx1i);
+    FREE(c->d_Bx2r);
+    FREE(c->d_Bx2i);
+    FREE(c->d_Pkr);
+    FREE(c->d_Pki);
+    c->pk_elems = 0;
     c->ws_nrhs = 0;
     c->last_nrhs = 0;
     drop_solve_graphs(c);
@@ -140,8 +147,11 @@ void free_problem(bm_ctx* c) {
     FREE(c->d_Lp_i);
     FREE(c->d_Up_r);
     FREE(c->d_Up_i);
+    FREE(c->d_Cp_r);
+    FREE(c->d_Cp_i);
     c->assembled = c->factored = c->singular = false;
     c->tm_ok = false;
+    c->tc_skinny = false;
 }
 
 bool finite_c(bm_c64 z) { return std::isfinite(z.re) && std::isfinite(z.im); }
@@ -150,7 +160,7 @@ double2 d2(bm_c64 z) { return make_double2(z.re, z.im); }
 long round_up(long a, long b) { return (a + b - 1) / b * b; }
 
 struct Plan {
-    long ldtop = 0, ldbot = 0, ldA = 0, ldF = 0, ldk_schur = 0, ldk_lu = 0;
+    long ldtop = 0, ldbot = 0, ldA = 0, ldF = 0, ldk_schur = 0, ldk_lu = 0, ldk_c = 0;
     int n = 0, nsys = 0, nb = 0, kseg = 0, nblk = 0;
     size_t bytes = 0;
 };
@@ -184,6 +194,9 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
             long kext = split ? 3L * p.kseg : p.kseg;
             p.ldk_schur = round_up(kext, 32);
             b += 2 * (size_t)N * p.ldk_schur * 8;
+            // [M13; M23] rows for the skinny products of the solve
+            p.ldk_c = round_up(split ? 3L * N : (long)N, 32);
+            b += 2 * (size_t)N * p.ldk_c * 8;
         }
         long kl = split ? 3L * p.nb : p.nb;
         p.ldk_lu = round_up(kl, 32);
@@ -212,6 +225,9 @@ extern "C" bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size
     BM_CUDA_TRY(cudaSetDevice(device));
     bm_ctx* c = new bm_ctx();
     c->device = device;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        c->num_sms < 1)
+        c->num_sms = 1;
     if (cuda_stream) {
         c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -401,6 +417,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     c->ldk_schur = p.ldk_schur;
     c->kseg_schur = p.kseg;
     c->ldk_lu = p.ldk_lu;
+    c->ldk_c = p.ldk_c;
     const bool c32 = prec != BM_FP64;
     bm_status s = alloc_t(c, &c->d_geom, 7 * (size_t)N * 8);
     if (s == BM_OK && form == BM_MIXED) {
@@ -427,6 +444,9 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
             if (s == BM_OK) s = alloc_t(c, &c->d_Ap_i, pb);
             if (s == BM_OK) s = alloc_t(c, &c->d_Bp_r, pb);
             if (s == BM_OK) s = alloc_t(c, &c->d_Bp_i, pb);
+            size_t cb = (size_t)2 * N * p.ldk_c * 4;
+            if (s == BM_OK) s = alloc_t(c, &c->d_Cp_r, cb);
+            if (s == BM_OK) s = alloc_t(c, &c->d_Cp_i, cb);
         }
         size_t lb = (size_t)p.n * p.ldk_lu * 4;
         if (s == BM_OK) s = alloc_t(c, &c->d_Lp_r, lb);
@@ -474,7 +494,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
             BM_CUDA_TRY(launch_pack_schur(st, c, prec == BM_CF32_3XTF32_IR));
             BM_CUDA_TRY(launch_split_planes(st, c->d_Mtop, c->ldtop, 2 * N, N, c->d_Ptop, c->ldtop));
             BM_CUDA_TRY(launch_split_planes(st, c->d_Mbot, c->ldbot, N, 2 * N, c->d_Pbot, c->ldbot));
-            c->launches += 5;
+            c->launches += 6;
         } else {
             BM_CUDA_TRY(launch_split_planes(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_PA, c->ldA));
             c->launches += 1;
@@ -491,6 +511,10 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
             BM_TRY(tc_make_map(c->tm_schur[1], c->d_Ap_i, N, kext, p.ldk_schur, TC_BM));
             BM_TRY(tc_make_map(c->tm_schur[2], c->d_Bp_r, N, kext, p.ldk_schur, TC_BN));
             BM_TRY(tc_make_map(c->tm_schur[3], c->d_Bp_i, N, kext, p.ldk_schur, TC_BN));
+            long kext_c = split ? 3L * N : (long)N;
+            BM_TRY(tc_make_map(c->tm_skinny[0], c->d_Cp_r, 2L * N, kext_c, p.ldk_c, TC_BM));
+            BM_TRY(tc_make_map(c->tm_skinny[1], c->d_Cp_i, 2L * N, kext_c, p.ldk_c, TC_BM));
+            c->tc_skinny = true;
         }
         long klu = p.ldk_lu;
         BM_TRY(tc_make_map(c->tm_lu[0], c->d_Lp_r, p.n, klu, p.ldk_lu, TC_BM));
@@ -635,14 +659,48 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
         BM_TRY(alloc_t(c, &c->d_Zwr, vb));
         BM_TRY(alloc_t(c, &c->d_Zwi, vb));
     }
+    if (c->tc_skinny) {
+        const int N = c->N;
+        const bool split = c->prec == BM_CF32_3XTF32_IR;
+        const long k1 = split ? 6L * N : 2L * N, k2 = split ? 3L * N : (long)N;
+        BM_TRY(alloc_t(c, &c->d_Bx1r, (size_t)w * c->ldk_schur * 4));
+        BM_TRY(alloc_t(c, &c->d_Bx1i, (size_t)w * c->ldk_schur * 4));
+        BM_TRY(alloc_t(c, &c->d_Bx2r, (size_t)w * c->ldk_c * 4));
+        BM_TRY(alloc_t(c, &c->d_Bx2i, (size_t)w * c->ldk_c * 4));
+        // rows past a call's nrhs only feed output columns that are never stored; zero them anyway
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_Bx1r, 0, (size_t)w * c->ldk_schur * 4, c->stream));
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_Bx1i, 0, (size_t)w * c->ldk_schur * 4, c->stream));
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_Bx2r, 0, (size_t)w * c->ldk_c * 4, c->stream));
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_Bx2i, 0, (size_t)w * c->ldk_c * 4, c->stream));
+        // partial sums of the two product shapes (N x nrhs over 2N, 2N x nrhs over N) for every
+        // nrhs up to w (the split count falls when nrhs crosses a tile boundary)
+        size_t pe = 0;
+        for (int q = 1; q <= w; ++q) {
+            pe = std::max(pe, (size_t)tc_split_k(N, q, (int)k1, c->num_sms) * N * q);
+            pe = std::max(pe, (size_t)tc_split_k(2 * N, q, (int)k2, c->num_sms) * 2 * N * q);
+        }
+        BM_TRY(alloc_t(c, &c->d_Pkr, pe * 4));
+        BM_TRY(alloc_t(c, &c->d_Pki, pe * 4));
+        c->pk_elems = pe;
+        BM_TRY(tc_make_map(c->tm_skinny[2], c->d_Bx1r, w, k1, c->ldk_schur, TC_BN));
+        BM_TRY(tc_make_map(c->tm_skinny[3], c->d_Bx1i, w, k1, c->ldk_schur, TC_BN));
+        BM_TRY(tc_make_map(c->tm_skinny[4], c->d_Bx2r, w, k2, c->ldk_c, TC_BN));
+        BM_TRY(tc_make_map(c->tm_skinny[5], c->d_Bx2i, w, k2, c->ldk_c, TC_BN));
+    }
     c->ws_nrhs = w;
     return BM_OK;
 }
 
 bm_status read_eta(bm_ctx* c, double* eta, bool* nonfinite) {
     double h[2];
+    int herr = 0;
     BM_CUDA_TRY(cudaMemcpyAsync(h, c->d_normA + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    BM_CUDA_TRY(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (herr != 0) {
+        bm_set_error("tensor-core GEMM: a bounded wait timed out");
+        return BM_ETIMEOUT;
+    }
     *eta = h[0];
     if (nonfinite) *nonfinite = h[1] != 0.0;
     return BM_OK;
@@ -723,7 +781,6 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
                 cudaEventRecord(r0, s);
                 st = residual_update_c32(c, c->d_R, ld, nrhs);
                 cudaEventRecord(r1, s);
-                c->launches += (c->form == BM_MIXED) ? 3 : 1;
                 if (st != BM_OK) break;
             }
             st = backward_error(c, c->d_R, c->d_X, c->d_Bw, ld, nrhs, d_eta);

@@ -534,6 +534,10 @@ cudaError_t launch_pack_schur(cudaStream_t s, const bm_ctx* c, int split) {
     long total = (long)N * c->ldk_schur;
     pack_colmajor_kernel<<<ceil_div(total, 256), 256, 0, s>>>(c->d_Mtop, c->ldtop, K, N, split, c->d_Bp_r, c->d_Bp_i,
                                                                c->ldk_schur);
+    // rows of [M13; M23] (2N x N) for the skinny products [M13; M23] z of the solve; only the
+    // tensor maps read this pack, which stop at K, so its padding columns stay unset
+    dim3 gridc(ceil_div(N, 32), ceil_div(2 * N, 32));
+    pack_rowmajor_kernel<<<gridc, blk, 0, s>>>(c->d_Mtop, c->ldtop, 2 * N, N, split, c->d_Cp_r, c->d_Cp_i, c->ldk_c);
     return cudaGetLastError();
 }
 

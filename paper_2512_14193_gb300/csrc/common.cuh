@@ -224,6 +224,9 @@ struct bm_ctx {
     float* d_Up_r = nullptr;
     float* d_Up_i = nullptr;
     long ldk_lu = 0;
+    float* d_Cp_r = nullptr;  // [M13; M23] rows, K = N (2N rows x Kext): A operand of the skinny
+    float* d_Cp_i = nullptr;  //   products [M13; M23] z of the mixed correction and residual update
+    long ldk_c = 0;
     float* d_O32r = nullptr;  // ordinary: FP32 copy of A is the LU buffer (d_F32*)
 
     // solve workspace (sized for the largest nrhs seen)
@@ -242,6 +245,15 @@ struct bm_ctx {
     float* d_Zwr = nullptr;
     float* d_Zwi = nullptr;
     double* d_colred = nullptr;  // per-column reductions (4 x nrhs)
+    // mixed CF32: B operand packs of the skinny tensor-core products (ws_nrhs rows, K-major) and
+    // the split-K partial-sum workspace
+    float* d_Bx1r = nullptr;  // [W1; W2] columns, K = 2N (ld ldk_schur)
+    float* d_Bx1i = nullptr;
+    float* d_Bx2r = nullptr;  // z3 columns, K = N (ld ldk_c)
+    float* d_Bx2i = nullptr;
+    float* d_Pkr = nullptr;
+    float* d_Pki = nullptr;
+    size_t pk_elems = 0;      // capacity of each partial-sum plane (floats)
 
     // cached graphs (with the number of kernel nodes each replay launches)
     struct GraphSlot {
@@ -256,7 +268,11 @@ struct bm_ctx {
     // tensor maps (opaque bytes, built on the host)
     alignas(64) unsigned char tm_schur[4][128];
     alignas(64) unsigned char tm_lu[4][128];
+    // skinny products: [0,1] [M13; M23] pack, [2,3] B pack of [W1; W2], [4,5] B pack of z3
+    alignas(64) unsigned char tm_skinny[6][128];
     bool tm_ok = false;
+    bool tc_skinny = false;  // mixed CF32: skinny products of the solve on the tensor cores
+    int num_sms = 0;
 
     // panel launch configuration
     int panel_cluster = 0;   // max cluster size the device allows for the panel kernel

@@ -147,11 +147,16 @@ __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t neg_a) {
            ((uint32_t)(BM >> 4) << 24);
 }
 
+// Output modes: OUT_C32 C (FP32 planar) = beta C + alpha D; OUT_Z64 C64 (FP64) = beta C64 + alpha D;
+// OUT_PART the raw D of this K split to a workspace slice (split-K partial sums).
+enum { OUT_C32 = 0, OUT_Z64 = 1, OUT_PART = 2 };
+
+template <int OUT>
 __global__ void __launch_bounds__(128, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmAr, const __grid_constant__ CUtensorMap tmAi,
                     const __grid_constant__ CUtensorMap tmBr, const __grid_constant__ CUtensorMap tmBi,
-                    float* __restrict__ Cr, float* __restrict__ Ci, long ldc, int m, int n, int kext, float alpha,
-                    float beta, int* __restrict__ err) {
+                    float* __restrict__ Cr, float* __restrict__ Ci, double2* __restrict__ C64, long ldc, long zstride,
+                    int m, int n, int kext, int S, float alpha, float beta, int* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
@@ -159,7 +164,10 @@ __global__ void __launch_bounds__(128, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tm = blockIdx.x, tn = blockIdx.y;
-    const int nkb = (kext + BKE - 1) / BKE;
+    // this CTA's K split: k-blocks [kb_begin, kb_begin + nkb)
+    const int nkb_all = (kext + BKE - 1) / BKE;
+    const int kb_begin = (int)((long)blockIdx.z * nkb_all / S);
+    const int nkb = (int)((long)(blockIdx.z + 1) * nkb_all / S) - kb_begin;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
 
     if (threadIdx.x == 0) {
@@ -188,7 +196,7 @@ __global__ void __launch_bounds__(128, 1)
             uint8_t* st = smem + s * STAGE_BYTES;
             const uint32_t fb = full0 + 8 * s;
             mbar_expect_tx(fb, STAGE_BYTES);
-            const int kx = kb * BKE;
+            const int kx = (kb_begin + kb) * BKE;
             tma_load_2d(smem_u32(st), &tmAr, fb, kx, tm * BM);
             tma_load_2d(smem_u32(st + TILE_A), &tmAi, fb, kx, tm * BM);
             tma_load_2d(smem_u32(st + 2 * TILE_A), &tmBr, fb, kx, tn * BN);
@@ -242,7 +250,40 @@ __global__ void __launch_bounds__(128, 1)
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float vr[16], vi[16];
             tmem_ld16x2(Dr + lane_off + c0, Di + lane_off + c0, vr, vi);
-            if (row < m) {
+            if (OUT == OUT_PART && row < m) {
+                // slice z of the workspace: m x n column-major, leading dimension ldc (= m)
+                float* Pr = Cr + (long)blockIdx.z * zstride;
+                float* Pi = Ci + (long)blockIdx.z * zstride;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const long col = col0 + c0 + q;
+                    if (col < n) {
+                        Pr[row + col * ldc] = vr[q];
+                        Pi[row + col * ldc] = vi[q];
+                    }
+                }
+            } else if (OUT == OUT_Z64 && row < m) {
+                double2 cz[16];
+                if (beta != 0.f) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const long col = col0 + c0 + q;
+                        cz[q] = (col < n) ? C64[row + col * ldc] : make_double2(0.0, 0.0);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const long col = col0 + c0 + q;
+                    if (col < n) {
+                        double r = (double)alpha * (double)vr[q], im = (double)alpha * (double)vi[q];
+                        if (beta != 0.f) {
+                            r = fma((double)beta, cz[q].x, r);
+                            im = fma((double)beta, cz[q].y, im);
+                        }
+                        C64[row + col * ldc] = make_double2(r, im);
+                    }
+                }
+            } else if (OUT == OUT_C32 && row < m) {
                 // issue every load of this 16-column chunk before any store, so the chunk costs
                 // one memory round trip instead of sixteen
                 float cr[16], ci[16];
@@ -321,20 +362,156 @@ bm_status tc_make_map(void* tmap, const float* base, long rows, long kext, long 
     return BM_OK;
 }
 
-cudaError_t gemm_tc(cudaStream_t s, const void* tAr, const void* tAi, const void* tBr, const void* tBi, float* Cr,
-                    float* Ci, long ldc, int m, int n, int kext, float alpha, float beta, int* d_err) {
-    if (m <= 0 || n <= 0 || kext <= 0) return cudaSuccess;
+namespace {
+
+template <int OUT>
+cudaError_t launch_tc(cudaStream_t s, dim3 grid, const void* tAr, const void* tAi, const void* tBr, const void* tBi,
+                      float* Cr, float* Ci, double2* C64, long ldc, long zstride, int m, int n, int kext, int S,
+                      float alpha, float beta, int* d_err) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        cudaError_t e =
+            cudaFuncSetAttribute(cgemm_tc_kernel<OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    dim3 grid(ceil_div(m, BM), ceil_div(n, BN));
-    cgemm_tc_kernel<<<grid, 128, SMEM_BYTES, s>>>(*reinterpret_cast<const CUtensorMap*>(tAr),
-                                                  *reinterpret_cast<const CUtensorMap*>(tAi),
-                                                  *reinterpret_cast<const CUtensorMap*>(tBr),
-                                                  *reinterpret_cast<const CUtensorMap*>(tBi), Cr, Ci, ldc, m, n, kext,
-                                                  alpha, beta, d_err);
+    cgemm_tc_kernel<OUT><<<grid, 128, SMEM_BYTES, s>>>(
+        *reinterpret_cast<const CUtensorMap*>(tAr), *reinterpret_cast<const CUtensorMap*>(tAi),
+        *reinterpret_cast<const CUtensorMap*>(tBr), *reinterpret_cast<const CUtensorMap*>(tBi), Cr, Ci, C64, ldc,
+        zstride, m, n, kext, S, alpha, beta, d_err);
+    return cudaGetLastError();
+}
+
+// C = beta C + alpha sum_z P[z]  (P: S slices of m x n column-major, leading dimension m)
+__global__ void splitk_reduce_c32_kernel(const float* __restrict__ Pr, const float* __restrict__ Pi, int S, int m,
+                                         int n, float alpha, float beta, float* __restrict__ Cr,
+                                         float* __restrict__ Ci, long ldc) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long zs = (long)m * n;
+    if (idx >= zs) return;
+    const int j = (int)(idx / m), i = (int)(idx % m);
+    float r = 0.f, im = 0.f;
+    for (int z = 0; z < S; ++z) {
+        r += __ldg(Pr + idx + z * zs);
+        im += __ldg(Pi + idx + z * zs);
+    }
+    const long o = i + (long)j * ldc;
+    float cr = alpha * r, ci = alpha * im;
+    if (beta != 0.f) {
+        cr = fmaf(beta, Cr[o], cr);
+        ci = fmaf(beta, Ci[o], ci);
+    }
+    Cr[o] = cr;
+    Ci[o] = ci;
+}
+
+// C64 = beta C64 + alpha sum_z P[z], the slice sum in FP32 (it is an FP32 product)
+__global__ void splitk_reduce_z64_kernel(const float* __restrict__ Pr, const float* __restrict__ Pi, int S, int m,
+                                         int n, float alpha, float beta, double2* __restrict__ C, long ldc) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long zs = (long)m * n;
+    if (idx >= zs) return;
+    const int j = (int)(idx / m), i = (int)(idx % m);
+    float r = 0.f, im = 0.f;
+    for (int z = 0; z < S; ++z) {
+        r += __ldg(Pr + idx + z * zs);
+        im += __ldg(Pi + idx + z * zs);
+    }
+    double2& c = C[i + (long)j * ldc];
+    double cr = (double)alpha * (double)r, ci = (double)alpha * (double)im;
+    if (beta != 0.f) {
+        cr = fma((double)beta, c.x, cr);
+        ci = fma((double)beta, c.y, ci);
+    }
+    c = make_double2(cr, ci);
+}
+
+// B operand of a skinny product: V (K x nrhs FP32 planar, column-major) -> row c of a [nrhs][ldk]
+// K-major pack; 3xTF32 segments [hi | lo | hi] with hi = tf32(v), lo = v - hi.
+__global__ void pack_b_kernel(const float* __restrict__ Vr, const float* __restrict__ Vi, long ldv, int K, int nrhs,
+                              int split, float* __restrict__ Br, float* __restrict__ Bi, long ldk) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)K * nrhs) return;
+    const int c = (int)(idx / K), k = (int)(idx % K);
+    const float vr = __ldg(Vr + k + (long)c * ldv), vi = __ldg(Vi + k + (long)c * ldv);
+    const long o = (long)c * ldk + k;
+    if (!split) {
+        Br[o] = vr;
+        Bi[o] = vi;
+        return;
+    }
+    uint32_t hr, hi;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hr) : "f"(vr));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(vi));
+    const float fr = __uint_as_float(hr), fi = __uint_as_float(hi);
+    Br[o] = fr;
+    Bi[o] = fi;
+    Br[o + K] = vr - fr;
+    Bi[o + K] = vi - fi;
+    Br[o + 2L * K] = fr;
+    Bi[o + 2L * K] = fi;
+}
+
+}  // namespace
+
+// C = beta C + alpha A B^T, C FP32 planar column-major (m x n, ld ldc); one K range per CTA.
+cudaError_t gemm_tc(cudaStream_t s, const void* tAr, const void* tAi, const void* tBr, const void* tBi, float* Cr,
+                    float* Ci, long ldc, int m, int n, int kext, float alpha, float beta, int* d_err) {
+    if (m <= 0 || n <= 0 || kext <= 0) return cudaSuccess;
+    dim3 grid(ceil_div(m, BM), ceil_div(n, BN), 1);
+    return launch_tc<OUT_C32>(s, grid, tAr, tAi, tBr, tBi, Cr, Ci, nullptr, ldc, 0, m, n, kext, 1, alpha, beta,
+                              d_err);
+}
+
+// Number of K splits for a product with few output tiles: about three waves of CTAs over the
+// SMs (one CTA per SM fits), at most 32 splits and at least one 32-wide K step per split.
+int tc_split_k(int m, int n, int kext, int num_sms) {
+    const long tiles = (long)ceil_div(m, BM) * ceil_div(n, BN);
+    const int nkb = ceil_div(kext, BKE);
+    long S = (3L * num_sms) / tiles;
+    if (S > 32) S = 32;
+    if (S > nkb) S = nkb;
+    if (S < 1) S = 1;
+    return (int)S;
+}
+
+// Split-K product into an FP32 planar (dst.re, dst.im) or FP64 (dst.z) destination:
+// dst = beta dst + alpha A B^T.  With S > 1 splits, each writes its partial product to the
+// workspace (Pr, Pi: S m n floats each) and one reduction kernel sums the slices in a fixed order
+// (deterministic).  Returns the number of kernels launched in *launched.
+cudaError_t gemm_tc_split(cudaStream_t s, const void* tAr, const void* tAi, const void* tBr, const void* tBi, int m,
+                          int n, int kext, float alpha, float beta, TcDest dst, int S, float* Pr, float* Pi,
+                          int* d_err, int* launched) {
+    *launched = 0;
+    if (m <= 0 || n <= 0 || kext <= 0) return cudaSuccess;
+    const bool z64 = dst.z != nullptr;
+    if (S <= 1) {
+        dim3 grid(ceil_div(m, BM), ceil_div(n, BN), 1);
+        *launched = 1;
+        if (z64)
+            return launch_tc<OUT_Z64>(s, grid, tAr, tAi, tBr, tBi, nullptr, nullptr, dst.z, dst.ld, 0, m, n, kext, 1,
+                                      alpha, beta, d_err);
+        return launch_tc<OUT_C32>(s, grid, tAr, tAi, tBr, tBi, dst.re, dst.im, nullptr, dst.ld, 0, m, n, kext, 1,
+                                  alpha, beta, d_err);
+    }
+    dim3 grid(ceil_div(m, BM), ceil_div(n, BN), S);
+    const long zs = (long)m * n;
+    cudaError_t e = launch_tc<OUT_PART>(s, grid, tAr, tAi, tBr, tBi, Pr, Pi, nullptr, m, zs, m, n, kext, S, 1.f, 0.f,
+                                        d_err);
+    if (e != cudaSuccess) return e;
+    const int nb = (int)ceil_div(zs, 256L);
+    if (z64)
+        splitk_reduce_z64_kernel<<<nb, 256, 0, s>>>(Pr, Pi, S, m, n, alpha, beta, dst.z, dst.ld);
+    else
+        splitk_reduce_c32_kernel<<<nb, 256, 0, s>>>(Pr, Pi, S, m, n, alpha, beta, dst.re, dst.im, dst.ld);
+    *launched = 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_b(cudaStream_t s, const float* Vr, const float* Vi, long ldv, int K, int nrhs, int split,
+                          float* Br, float* Bi, long ldk) {
+    const long t = (long)K * nrhs;
+    if (t == 0) return cudaSuccess;
+    pack_b_kernel<<<ceil_div(t, 256L), 256, 0, s>>>(Vr, Vi, ldv, K, nrhs, split, Br, Bi, ldk);
     return cudaGetLastError();
 }

@@ -24,6 +24,19 @@ cudaError_t gemm_tc(cudaStream_t s, const void* tAr, const void* tAi, const void
                     float* Ci, long ldc, int m, int n, int kext, float alpha, float beta, int* d_err);
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 128;
+// destination of a split-K product: FP32 planar (re, im) or, when z is set, FP64 interleaved
+struct TcDest {
+    float* re;
+    float* im;
+    double2* z;
+    long ld;
+};
+int tc_split_k(int m, int n, int kext, int num_sms);
+cudaError_t gemm_tc_split(cudaStream_t s, const void* tAr, const void* tAi, const void* tBr, const void* tBi, int m,
+                          int n, int kext, float alpha, float beta, TcDest dst, int S, float* Pr, float* Pi,
+                          int* d_err, int* launched);
+cudaError_t launch_pack_b(cudaStream_t s, const float* Vr, const float* Vi, long ldv, int K, int nrhs, int split,
+                          float* Br, float* Bi, long ldk);
 
 // lu.cu
 bm_status lu_setup(bm_ctx* c);

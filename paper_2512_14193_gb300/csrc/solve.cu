@@ -140,6 +140,13 @@ __global__ void copy_z64_kernel(const double2* __restrict__ S, long lds, int m, 
         }                                                                                              \
     } while (0)
 
+// K splits of a skinny tensor-core product, never more than the partial-sum workspace holds
+int skinny_split(const bm_ctx* c, int m, int n, int kext) {
+    int S = tc_split_k(m, n, kext, c->num_sms);
+    while (S > 1 && (size_t)S * m * n > c->pk_elems) --S;
+    return S;
+}
+
 cudaError_t copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd) {
     long t = (long)m * n;
     if (t == 0) return cudaSuccess;
@@ -234,7 +241,30 @@ bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int n
     to_c32_kernel<<<ceil_div(t, 256), 256, 0, s>>>(R, ld, c->nsys, nrhs, Wr, Wi, ldw);
     SV_CUDA(cudaGetLastError());
     const bool split = (c->prec == BM_CF32_3XTF32_IR);
-    if (c->form == BM_MIXED) {
+    if (c->form == BM_MIXED && c->tc_skinny) {
+        // the two skinny products on the tensor cores, split over K (few output tiles)
+        const int K = 2 * N;
+        int nl = 0;
+        // W3 -= [M31 M32] [W1; W2]
+        const long k1 = split ? 3L * K : (long)K;
+        SV_CUDA(launch_pack_b(s, Wr, Wi, ldw, K, nrhs, split, c->d_Bx1r, c->d_Bx1i, c->ldk_schur));
+        SV_CUDA(gemm_tc_split(s, c->tm_schur[0], c->tm_schur[1], c->tm_skinny[2], c->tm_skinny[3], N, nrhs, (int)k1,
+                              -1.f, 1.f, TcDest{Wr + 2 * N, Wi + 2 * N, nullptr, ldw},
+                              skinny_split(c, N, nrhs, (int)k1), c->d_Pkr, c->d_Pki, c->d_err, &nl));
+        SV_CUDA(launch_gather_rows_c32(s, c->d_perm, N, nrhs, Wr + 2 * N, Wi + 2 * N, ldw, Vr, Vi, ldv));
+        BM_TRY(getrs_c32(c, Vr, Vi, ldv, nrhs));
+        // [W1; W2] -= [M13; M23] z3; the pack of z3 stays for the next residual update
+        const long k2 = split ? 3L * N : (long)N;
+        SV_CUDA(launch_pack_b(s, Vr, Vi, ldv, N, nrhs, split, c->d_Bx2r, c->d_Bx2i, c->ldk_c));
+        SV_CUDA(gemm_tc_split(s, c->tm_skinny[0], c->tm_skinny[1], c->tm_skinny[4], c->tm_skinny[5], 2 * N, nrhs,
+                              (int)k2, -1.f, 1.f, TcDest{Wr, Wi, nullptr, ldw},
+                              skinny_split(c, 2 * N, nrhs, (int)k2), c->d_Pkr, c->d_Pki, c->d_err, &nl));
+        long t2 = (long)K * nrhs;
+        add_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(X, ld, 0, K, nrhs, Wr, Wi, ldw);
+        long t3 = (long)N * nrhs;
+        add_c32_kernel<<<ceil_div(t3, 256), 256, 0, s>>>(X, ld, 2 * N, N, nrhs, Vr, Vi, ldv);
+        SV_CUDA(cudaGetLastError());
+    } else if (c->form == BM_MIXED) {
         const int K = 2 * N;
         // W3 -= [M31 M32] [W1; W2]   (A operand pack is row-major: pass it as its transpose)
         C32 Ahi{c->d_Ap_r, c->d_Ap_i, c->ldk_schur};
@@ -273,12 +303,30 @@ bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int n
 // R -= A d for the correction d of the last correction_c32 call (still in the FP32 work buffers),
 // with the products in FP32.  d is small next to x after the first correction, so the FP32
 // product error (~1e-6 |A| |d|) stays far below the backward-error target: this replaces the
-// full FP64 residual b - A x from the second refinement step on.
+// full FP64 residual b - A x from the second refinement step on.  Runs outside the captured
+// graphs, so it adds its own kernel launches to the handle's count.
 bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs) {
     cudaStream_t s = c->stream;
     const int N = c->N;
     const long ldw = c->nsys, ldv = c->n;
-    if (c->form == BM_MIXED) {
+    if (c->form == BM_MIXED && c->tc_skinny && c->prec == BM_CF32_3XTF32_IR) {
+        // 3xTF32 products on the tensor cores (FP32-level accuracy, as the SIMT FP32 update):
+        // rows [0, 2N): r -= d12 + [M13; M23] d3 with d3 still packed by the correction;
+        // rows [2N, 3N): r -= [M31 M32] d12 with d12 packed here
+        long t2 = (long)2 * N * nrhs;
+        sub_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(R, ld, 0, 2 * N, nrhs, c->d_Wr, c->d_Wi, ldw);
+        SV_CUDA(cudaGetLastError());
+        int n1 = 0, n2 = 0;
+        const long k2 = 3L * N, k1 = 6L * N;
+        SV_CUDA(gemm_tc_split(s, c->tm_skinny[0], c->tm_skinny[1], c->tm_skinny[4], c->tm_skinny[5], 2 * N, nrhs,
+                              (int)k2, -1.f, 1.f, TcDest{nullptr, nullptr, R, ld},
+                              skinny_split(c, 2 * N, nrhs, (int)k2), c->d_Pkr, c->d_Pki, c->d_err, &n1));
+        SV_CUDA(launch_pack_b(s, c->d_Wr, c->d_Wi, ldw, 2 * N, nrhs, 1, c->d_Bx1r, c->d_Bx1i, c->ldk_schur));
+        SV_CUDA(gemm_tc_split(s, c->tm_schur[0], c->tm_schur[1], c->tm_skinny[2], c->tm_skinny[3], N, nrhs, (int)k1,
+                              -1.f, 1.f, TcDest{nullptr, nullptr, R + 2 * N, ld},
+                              skinny_split(c, N, nrhs, (int)k1), c->d_Pkr, c->d_Pki, c->d_err, &n2));
+        c->launches += 2 + n1 + n2;
+    } else if (c->form == BM_MIXED) {
         // rows [0, 2N): r -= d12 + [M13; M23] d3 ; rows [2N, 3N): r -= [M31 M32] d12
         long t2 = (long)2 * N * nrhs;
         sub_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(R, ld, 0, 2 * N, nrhs, c->d_Wr, c->d_Wi, ldw);
@@ -287,9 +335,11 @@ bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs) {
                                     Z64{R, ld}));
         SV_CUDA(gemm_update_f4hi_c32(s, N, nrhs, 2 * N, -1.0f, F4Hi{c->d_Pbot, c->ldbot}, C32{c->d_Wr, c->d_Wi, ldw},
                                     Z64{R + 2 * N, ld}));
+        c->launches += 3;
     } else {
         SV_CUDA(gemm_update_f4hi_c32(s, 2 * N, nrhs, 2 * N, -1.0f, F4Hi{c->d_PA, c->ldA}, C32{c->d_W2r, c->d_W2i, ldv},
                                     Z64{R, ld}));
+        c->launches += 1;
     }
     return BM_OK;
 }
