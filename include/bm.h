@@ -170,6 +170,27 @@ bm_status bm_solve(bm_ctx* ctx, int nrhs, const bm_c64* B, int ldb, bm_c64* X, i
 bm_status bm_far_field(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const double* angles,
                        int M, bm_c64* Uinf, int ldu, int on_device);
 
+/* The far field of bm_far_field (same kernel, same result) for callers that must not allocate
+ * device memory while they run; the paper has no counterpart, it is a library service.
+ * bm_far_field allocates and frees a small device buffer for the angles on each call: cudaFree
+ * waits for all work on the device, which stalls a serving loop that keeps other streams busy,
+ * and the allocation fails once the handle's HBM budget is spent.  This call instead copies the
+ * angles into a fixed device array of BM_FAR_FIELD_STATIC_MAX_ANGLES doubles (64 KB) built into
+ * the library, and allocates nothing.
+ *  X    : device array, nsys x nrhs column-major solutions (ldx >= nsys), as from bm_solve.
+ *  Uinf : device array, M x nrhs column-major output (ldu >= M), fully overwritten.
+ *  angles: host array of M observation angles (radians), 1 <= M <= BM_FAR_FIELD_STATIC_MAX_ANGLES.
+ * Nothing in the fixed array needs to start at zero: each call writes the M angles it reads.
+ * The first call on a device looks up the array's device address once for that device; make it
+ * before any stream capture starts on the device.  The array is shared by all handles and threads
+ * on a device: calls that overlap in time race on it.  The call waits for the handle's stream
+ * before it returns, so calls made one after another are safe.
+ * Errors: BM_EINVAL (M above the limit - bm_last_error says so -, bad sizes or pointers),
+ * BM_ESTATE (nothing assembled), BM_ECUDA. */
+#define BM_FAR_FIELD_STATIC_MAX_ANGLES 8192
+bm_status bm_far_field_static(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const double* angles,
+                              int M, bm_c64* Uinf, int ldu);
+
 /* Copy one assembled FP64 block to dst (column-major, ldd >= rows).
  * Mixed: which = 0..3 selects M13, M23, M31, M32 (N x N).
  * Ordinary: which = 0 selects the whole 2N x 2N matrix. */

@@ -25,6 +25,7 @@ BM_FP64, BM_CF32_TF32_IR, BM_CF32_3XTF32_IR = 0, 1, 2
 BM_CURVE_CIRCLE, BM_CURVE_ELLIPSE, BM_CURVE_STAR, BM_CURVE_KITE, BM_CURVE_USER = range(5)
 BM_PROBE_SCHUR, BM_PROBE_RESIDUAL = 0, 1
 BM_RESID_DF_UPDATE, BM_RESID_FP64_UPDATE, BM_RESID_FP64_ALL = 0, 1, 2
+BM_FAR_FIELD_STATIC_MAX_ANGLES = 8192
 
 
 class bm_c64(C.Structure):
@@ -71,6 +72,7 @@ def lib():
     L.bm_rhs_plane_wave.argtypes = [P, C.POINTER(D), I, P, I, I]
     L.bm_solve.argtypes = [P, I, P, I, P, I, I, C.POINTER(bm_solve_info)]
     L.bm_far_field.argtypes = [P, P, I, I, C.POINTER(D), I, P, I, I]
+    L.bm_far_field_static.argtypes = [P, P, I, I, C.POINTER(D), I, P, I]
     L.bm_copy_block.argtypes = [P, I, P, I, I]
     L.bm_hankel01.argtypes = [P, P, I, P, P, I]
     L.bm_hankel_anchor_table.argtypes = [C.POINTER(D), I, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(D),
@@ -84,6 +86,7 @@ def lib():
     L.bm_last_error.argtypes = []
     L.bm_last_error.restype = C.c_char_p
     for name in ("bm_create", "bm_assemble", "bm_factor", "bm_rhs_plane_wave", "bm_solve", "bm_far_field",
+                 "bm_far_field_static",
                  "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_memory", "bm_destroy",
                  "bm_kernel_launches", "bm_enqueue_probe"):
         getattr(L, name).restype = C.c_int
@@ -210,6 +213,17 @@ def bm_far_field(h, X, angles, U) -> None:
     ang = np.ascontiguousarray(angles, dtype=np.float64)
     _check(lib().bm_far_field(h, px, ldx, nx, ang.ctypes.data_as(C.POINTER(C.c_double)), int(ang.size), pu, ldu,
                               devx), "bm_far_field")
+
+
+def bm_far_field_static(h, X, angles, U) -> None:
+    """bm_far_field without device allocation; X and U must be CUDA tensors."""
+    px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=False)
+    pu, ldu, nu, devu, _ku = _colmajor(U, 0, writable=True)
+    if not (devx and devu):
+        raise ValueError("bm_far_field_static takes device arrays only")
+    ang = np.ascontiguousarray(angles, dtype=np.float64)
+    _check(lib().bm_far_field_static(h, px, ldx, nx, ang.ctypes.data_as(C.POINTER(C.c_double)), int(ang.size), pu,
+                                     ldu), "bm_far_field_static")
 
 
 def bm_copy_block(h, which: int, dst) -> None:

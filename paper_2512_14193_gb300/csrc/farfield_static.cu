@@ -1,0 +1,87 @@
+// bm_far_field_static: the far field of bm_far_field without any device allocation.
+//
+// Who needs it: callers that must not allocate device memory while they run.  bm_far_field
+// allocates a small device buffer for the observation angles on every call and frees it
+// afterwards.  cudaFree waits until all work on the device has finished, so a serving loop that
+// keeps other streams of the same GPU busy stalls at every far-field evaluation; and the
+// allocation fails outright once factorisations have used up the handle's HBM budget.  This
+// entry point launches the same far-field kernel on the same data, but reads the angles from a
+// fixed device array compiled into the library.
+//
+// Scratch: g_ff_angles below, BM_FAR_FIELD_STATIC_MAX_ANGLES doubles (8192 x 8 bytes = 64 KB);
+// the linker gives each device its own copy.  A call copies its M angles into the first M
+// entries before the kernel reads them, and the kernel reads nothing else, so no part of the
+// array has to start at zero and the call clears none of it.
+//
+// Set-up: the first call on a device, with that device current, looks up the device address of
+// the array (cudaGetSymbolAddress) and keeps it for later calls on that device.  The lookup can
+// load the library's device code onto the device, so make this first call before any stream
+// capture starts on the device.
+//
+// Overlapping calls race: the array is shared by every handle and host thread that uses the
+// device, so two calls running at the same time can overwrite each other's angles before the
+// kernel reads them.  Each call waits for its stream to finish before it returns, so calls made
+// one after another, from any handle, are safe.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <mutex>
+
+static __device__ __align__(256) double g_ff_angles[BM_FAR_FIELD_STATIC_MAX_ANGLES];
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_setup_mu;
+double* g_angles_ptr[MAX_DEVICES] = {};
+
+// Device address of g_ff_angles on `dev` (the current device), looked up once per device.
+bm_status angles_scratch(int dev, double** out) {
+    if (dev < 0 || dev >= MAX_DEVICES) {
+        bm_set_error("bm_far_field_static: device index " + std::to_string(dev) + " out of range");
+        return BM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    if (g_angles_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_ff_angles);
+        if (e != cudaSuccess || p == nullptr) {
+            bm_set_error(std::string("bm_far_field_static: cudaGetSymbolAddress failed: ") +
+                         cudaGetErrorString(e));
+            return BM_ECUDA;
+        }
+        g_angles_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_angles_ptr[dev];
+    return BM_OK;
+}
+
+}  // namespace
+
+extern "C" bm_status bm_far_field_static(bm_ctx* c, const bm_c64* X, int ldx, int nrhs, const double* angles, int M,
+                                         bm_c64* Uinf, int ldu) {
+    if (c == nullptr || X == nullptr || angles == nullptr || Uinf == nullptr || nrhs < 1 || M < 1) return BM_EINVAL;
+    if (M > BM_FAR_FIELD_STATIC_MAX_ANGLES) {
+        bm_set_error("bm_far_field_static: M = " + std::to_string(M) + " angles exceeds the fixed device array of " +
+                     std::to_string(BM_FAR_FIELD_STATIC_MAX_ANGLES) + " (use bm_far_field, or split the angles)");
+        return BM_EINVAL;
+    }
+    if (!c->assembled) return BM_ESTATE;
+    if (ldx < c->nsys || ldu < M) return BM_EINVAL;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    double* d_ang = nullptr;
+    BM_TRY(angles_scratch(c->device, &d_ang));
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaMemcpyAsync(d_ang, angles, (size_t)M * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        e = launch_far_field(s, c, reinterpret_cast<const double2*>(X), ldx, nrhs, d_ang, M,
+                             reinterpret_cast<double2*>(Uinf), ldu);
+        c->launches += 1;
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        bm_set_error(std::string("bm_far_field_static: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return BM_ECUDA;
+    }
+    return BM_OK;
+}
