@@ -116,6 +116,9 @@ void free_solve_ws(bm_ctx* c) {
     FREE(c->d_Bx2i);
     FREE(c->d_Pkr);
     FREE(c->d_Pki);
+    FREE(c->d_XP);
+    FREE(c->d_XQ);
+    FREE(c->d_Wdf);
     c->pk_elems = 0;
     c->ws_nrhs = 0;
     c->last_nrhs = 0;
@@ -132,6 +135,9 @@ void free_problem(bm_ctx* c) {
     FREE(c->d_Ptop);
     FREE(c->d_Pbot);
     FREE(c->d_PA);
+    FREE(c->d_Qtop);
+    FREE(c->d_Qbot);
+    FREE(c->d_QA);
     FREE(c->d_F64);
     FREE(c->d_F32r);
     FREE(c->d_F32i);
@@ -186,9 +192,9 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
         b += (size_t)p.ldF * p.n * 16;
     } else {
         b += (size_t)p.ldF * p.n * 8;
-        // split hi/lo planes of the FP64 operator (same size as the FP64 blocks)
-        b += (form == BM_MIXED) ? (size_t)p.ldtop * N * 16 + (size_t)p.ldbot * 2 * N * 16
-                                : (size_t)p.ldA * 2 * N * 16;
+        // split hi/lo planes of the FP64 operator (same size as the FP64 blocks) and of re + im
+        b += (form == BM_MIXED) ? (size_t)p.ldtop * N * 24 + (size_t)p.ldbot * 2 * N * 24
+                                : (size_t)p.ldA * 2 * N * 24;
         if (form == BM_MIXED) {
             p.kseg = 2 * N;
             long kext = split ? 3L * p.kseg : p.kseg;
@@ -304,7 +310,6 @@ extern "C" bm_status bm_enqueue_probe(bm_ctx* c, int which, int reps) {
                 BM_TRY(residual_df(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
             else
                 BM_TRY(residual_fp64(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
-            c->launches += (c->form == BM_MIXED) ? 3 : 2;
         }
         return BM_OK;
     }
@@ -431,8 +436,11 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
         if (form == BM_MIXED) {
             s = alloc_t(c, &c->d_Ptop, (size_t)p.ldtop * N * 16);
             if (s == BM_OK) s = alloc_t(c, &c->d_Pbot, (size_t)p.ldbot * 2 * N * 16);
+            if (s == BM_OK) s = alloc_t(c, &c->d_Qtop, (size_t)p.ldtop * N * 8);
+            if (s == BM_OK) s = alloc_t(c, &c->d_Qbot, (size_t)p.ldbot * 2 * N * 8);
         } else {
             s = alloc_t(c, &c->d_PA, (size_t)p.ldA * 2 * N * 16);
+            if (s == BM_OK) s = alloc_t(c, &c->d_QA, (size_t)p.ldA * 2 * N * 8);
         }
     }
     if (s == BM_OK && c32) {
@@ -492,11 +500,11 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     if (c32) {
         if (form == BM_MIXED) {
             BM_CUDA_TRY(launch_pack_schur(st, c, prec == BM_CF32_3XTF32_IR));
-            BM_CUDA_TRY(launch_split_planes(st, c->d_Mtop, c->ldtop, 2 * N, N, c->d_Ptop, c->ldtop));
-            BM_CUDA_TRY(launch_split_planes(st, c->d_Mbot, c->ldbot, N, 2 * N, c->d_Pbot, c->ldbot));
+            BM_CUDA_TRY(launch_split_planes(st, c->d_Mtop, c->ldtop, 2 * N, N, c->d_Ptop, c->d_Qtop, c->ldtop));
+            BM_CUDA_TRY(launch_split_planes(st, c->d_Mbot, c->ldbot, N, 2 * N, c->d_Pbot, c->d_Qbot, c->ldbot));
             c->launches += 6;
         } else {
-            BM_CUDA_TRY(launch_split_planes(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_PA, c->ldA));
+            BM_CUDA_TRY(launch_split_planes(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_PA, c->d_QA, c->ldA));
             c->launches += 1;
         }
     }
@@ -658,6 +666,9 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
         BM_TRY(alloc_t(c, &c->d_W2i, vb));
         BM_TRY(alloc_t(c, &c->d_Zwr, vb));
         BM_TRY(alloc_t(c, &c->d_Zwi, vb));
+        BM_TRY(alloc_t(c, &c->d_XP, (size_t)c->nsys * w * 16));
+        BM_TRY(alloc_t(c, &c->d_XQ, (size_t)c->nsys * w * 8));
+        BM_TRY(alloc_t(c, &c->d_Wdf, (size_t)4 * c->N * w * 16));
     }
     if (c->tc_skinny) {
         const int N = c->N;
@@ -748,14 +759,13 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
     int iters = 0;
     float t_res = 0.f;
     bm_status st = BM_OK;
-    const unsigned long long k_res = (c->form == BM_MIXED) ? 3 : 2;  // kernels per residual
     if (c->prec == BM_FP64) {
         st = run_captured(c, &c->g_fp64[nrhs], [&]() { return solve_fp64(c, c->d_Bw, c->d_X, ld, nrhs); });
         if (st == BM_OK && info) {
             cudaEventRecord(r0, s);
             st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
             cudaEventRecord(r1, s);
-            c->launches += k_res + 1;
+            c->launches += 1;  // the backward error below (the residual counts its own)
             if (st == BM_OK) st = backward_error(c, c->d_R, c->d_X, c->d_Bw, ld, nrhs, d_eta);
             if (st == BM_OK) st = read_eta(c, &eta, &nonfinite);
             cudaEventElapsedTime(&t_res, r0, r1);
@@ -774,7 +784,6 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
                 else
                     st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
                 cudaEventRecord(r1, s);
-                c->launches += k_res;
                 if (st != BM_OK) break;
             } else if (it > 1) {
                 // r -= A d for the last correction d (FP32 products; d is small by now)

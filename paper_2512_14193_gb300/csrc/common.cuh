@@ -196,6 +196,9 @@ struct bm_ctx {
     float4* d_Ptop = nullptr;
     float4* d_Pbot = nullptr;
     float4* d_PA = nullptr;
+    float2* d_Qtop = nullptr;  // re + im of the same entries, split hi/lo (3-product complex multiply)
+    float2* d_Qbot = nullptr;
+    float2* d_QA = nullptr;
 
     // factorisation storage
     double2* d_F64 = nullptr;  // FP64 LU (n x n, ld ldF)
@@ -253,6 +256,9 @@ struct bm_ctx {
     float* d_Bx2i = nullptr;
     float* d_Pkr = nullptr;
     float* d_Pki = nullptr;
+    float4* d_XP = nullptr;   // CF32: the iterate split for the double-float residual (nsys x nrhs)
+    float2* d_XQ = nullptr;
+    double2* d_Wdf = nullptr; // split-K partial sums of the double-float residual (4N x nrhs)
     size_t pk_elems = 0;      // capacity of each partial-sum plane (floats)
 
     // cached graphs (with the number of kernel nodes each replay launches)

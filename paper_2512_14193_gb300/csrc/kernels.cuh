@@ -59,9 +59,23 @@ bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs);
 bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs);
 
 // resid_df.cu: C += alpha A X in double-float arithmetic (A as split planes, X and C FP64)
-cudaError_t gemm_df(cudaStream_t s, int m, int n, int k, double alpha, const float4* A, long lda, const double2* X,
-                    long ldx, double2* C, long ldc);
-cudaError_t launch_split_planes(cudaStream_t s, const double2* A, long lda, int m, int n, float4* P, long ldp);
+// one product C (m x n) += alpha A (m x k) X (k x n) of a double-float residual; S K splits (S > 1
+// writes S m n raw partial sums to W, reduced in order afterwards)
+struct DfProd {
+    const float4* A;   // split planes of the operator (re_hi, re_lo, im_hi, im_lo)
+    const float2* Q;   // split re + im
+    long lda;
+    const float4* XP;  // the iterate split the same way
+    const float2* XQ;
+    long ldx;
+    double2* C;
+    long ldc;
+    double2* W;
+    int m, k, S;
+};
+cudaError_t gemm_df(cudaStream_t s, const DfProd* prods, int nprod, int n, double alpha, int* launched);
+cudaError_t launch_split_planes(cudaStream_t s, const double2* A, long lda, int m, int n, float4* P, float2* Q,
+                                long ldp);
 // gemm_simt.cu: C (FP64) += alpha A_hi B with A the hi parts of split planes, FP32 arithmetic
 cudaError_t gemm_update_f4hi_c32(cudaStream_t s, int m, int n, int k, float alpha, F4Hi A, C32 B, Z64 C);
 cudaError_t launch_copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd);

@@ -181,7 +181,7 @@ bm_status solve_fp64(bm_ctx* c, const double2* B, double2* X, long ld, int nrhs)
     return BM_OK;
 }
 
-// R = B - A X with the FP64 assembled operator.
+// R = B - A X with the FP64 assembled operator.  Not captured in a graph: counts its own launches.
 bm_status residual_fp64(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs) {
     cudaStream_t s = c->stream;
     const int N = c->N;
@@ -198,10 +198,12 @@ bm_status residual_fp64(bm_ctx* c, const double2* B, const double2* X, double2* 
         SV_CUDA(gemm_z64(s, 2 * N, nrhs, 2 * N, -1.0, Z64{c->d_A, c->ldA}, false, Z64{const_cast<double2*>(X), ld},
                          1.0, Z64{R, ld}));
     }
+    c->launches += (c->form == BM_MIXED) ? 3 : 2;
     return BM_OK;
 }
 
-// R = B - A X with the FP64 operator, products and sums in double-float on the FP32 cores.
+// R = B - A X with the FP64 operator, products and sums in double-float on the FP32 cores.  Not
+// captured in a graph: counts its own launches.
 bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs) {
     cudaStream_t s = c->stream;
     const int N = c->N;
@@ -209,12 +211,20 @@ bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R,
     int nsub = (c->form == BM_MIXED) ? 2 * N : 0;
     resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
     SV_CUDA(cudaGetLastError());
+    const long ldp = c->nsys;
+    SV_CUDA(launch_split_planes(s, X, ld, c->nsys, nrhs, c->d_XP, c->d_XQ, ldp));
+    // K splits chosen so every work unit spans K = N: the K = 2N products are split in two
+    int nl = 0;
     if (c->form == BM_MIXED) {
-        SV_CUDA(gemm_df(s, 2 * N, nrhs, N, -1.0, c->d_Ptop, c->ldtop, X + 2 * N, ld, R, ld));
-        SV_CUDA(gemm_df(s, N, nrhs, 2 * N, -1.0, c->d_Pbot, c->ldbot, X, ld, R + 2 * N, ld));
+        DfProd P[2] = {
+            {c->d_Pbot, c->d_Qbot, c->ldbot, c->d_XP, c->d_XQ, ldp, R + 2 * N, ld, c->d_Wdf, N, 2 * N, 2},
+            {c->d_Ptop, c->d_Qtop, c->ldtop, c->d_XP + 2 * N, c->d_XQ + 2 * N, ldp, R, ld, nullptr, 2 * N, N, 1}};
+        SV_CUDA(gemm_df(s, P, 2, nrhs, -1.0, &nl));
     } else {
-        SV_CUDA(gemm_df(s, 2 * N, nrhs, 2 * N, -1.0, c->d_PA, c->ldA, X, ld, R, ld));
+        DfProd P[1] = {{c->d_PA, c->d_QA, c->ldA, c->d_XP, c->d_XQ, ldp, R, ld, c->d_Wdf, 2 * N, 2 * N, 2}};
+        SV_CUDA(gemm_df(s, P, 1, nrhs, -1.0, &nl));
     }
+    c->launches += 2 + nl;
     return BM_OK;
 }
 
