@@ -627,7 +627,7 @@ extern "C" bm_status bm_factor(bm_ctx* c, int* info) {
     BM_CUDA_TRY(cudaMemcpyAsync(h, c->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (h[1] != 0) {
-        bm_set_error("tensor-core GEMM: a bounded wait timed out");
+        bm_set_error("factorisation: a bounded device-side wait timed out");
         c->factored = false;
         return BM_ETIMEOUT;
     }

@@ -282,6 +282,7 @@ struct bm_ctx {
 
     // panel launch configuration
     int panel_cluster = 0;   // max cluster size the device allows for the panel kernel
+    bool panel_lane_col = true;  // FP32 panels on the lane-per-column kernel where it fits
 };
 
 // allocation helpers (api.cu)

@@ -417,7 +417,7 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
         const int jb = std::min(NB, n - J);
         for (int j = J; j < J + jb;) {
             PanelShape ps;
-            if (!panel_shape<V>(n - j, cl_max, ps)) {
+            if (!panel_shape<V>(n - j, cl_max, c->panel_lane_col, ps)) {
                 bm_set_error("lu: system too large for the panel kernel");
                 return BM_EINVAL;
             }
@@ -508,6 +508,9 @@ bm_status lu_setup(bm_ctx* c) {
             int v = atoi(e);
             if (v >= 1 && v <= 16) c->panel_cluster = std::min(c->panel_cluster, v);
         }
+        // BM_PANEL_KERNEL=rows keeps FP32 panels on the register-row kernel
+        const char* pk = getenv("BM_PANEL_KERNEL");
+        c->panel_lane_col = !(pk != nullptr && std::string(pk) == "rows");
     }
     return BM_OK;
 }

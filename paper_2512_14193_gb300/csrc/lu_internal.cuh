@@ -345,18 +345,31 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
 
 struct PanelShape {
     int CL, R, RPT, nbp;
+    int RPW;  // > 0: lane-per-column kernel with RPW rows per warp (C32), else the register-row kernel
 };
 
-// cluster size, rows per CTA, rows per thread and sub-panel width for a panel of m rows
+// cluster size, rows per CTA, rows per thread and sub-panel width for a panel of m rows.  The
+// lane-per-column kernel (lane_col, C32 only) takes up to 256 rows per CTA (16 per warp); taller
+// panels use the register-row kernel.
 template <class V>
-bool panel_shape(int m, int cl_max, PanelShape& ps) {
+bool panel_shape(int m, int cl_max, bool lane_col, PanelShape& ps) {
+    if (std::is_same<V, C32>::value && lane_col) {
+        const int CL = std::min(cl_max, std::max(1, ceil_div(m, 256)));
+        const int need = ceil_div(ceil_div(m, CL), PANEL_THREADS / 32);  // rows per warp
+        int rpw = 2;
+        while (rpw < need) rpw *= 2;
+        if (rpw <= 16) {
+            ps = PanelShape{CL, (PANEL_THREADS / 32) * rpw, 0, 32, rpw};
+            return true;
+        }
+    }
     constexpr int W = std::is_same<V, C32>::value ? 32 : 16;  // widest sub-panel (1 row per thread)
     int CL = std::min(cl_max, std::max(1, ceil_div(m, PANEL_THREADS)));
     int R = ceil_div(m, CL);
     int RPT = ceil_div(R, PANEL_THREADS);
     if (RPT > 4) return false;
     if (RPT == 3) RPT = 4;
-    ps = PanelShape{CL, R, RPT, W / RPT};
+    ps = PanelShape{CL, R, RPT, W / RPT, 0};
     return true;
 }
 

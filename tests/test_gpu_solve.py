@@ -105,11 +105,16 @@ def test_mixed_precision_refinement(bmlib, handle, prec, form, resid):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", [0, 2])
-@pytest.mark.parametrize("clmax,N", [(1, 600), (1, 1100), (2, 1100)])
-def test_panel_variants_match_oracle(bmlib, monkeypatch, prec, clmax, N):
+@pytest.mark.parametrize("clmax,N,kernel", [(1, 600, ""), (1, 1100, ""), (2, 1100, ""), (2, 500, ""),
+                                            (16, 1100, "rows")])
+def test_panel_variants_match_oracle(bmlib, monkeypatch, prec, clmax, N, kernel):
     # Capping the panel cluster puts 2 (N=600, cap 1; N=1100, cap 2) or 4 (N=1100, cap 1) rows on
-    # each panel thread, which selects the narrower register-resident sub-panel kernels.
+    # each thread of the register-row panel kernel, which selects its narrower sub-panel variants;
+    # FP32 panels of at most 256 rows per CTA run on the lane-per-column kernel (N=500, cap 2: 16
+    # rows per warp).  kernel="rows" keeps every FP32 panel on the register-row kernel.
     monkeypatch.setenv("BM_PANEL_CLUSTER_MAX", str(clmax))
+    if kernel:
+        monkeypatch.setenv("BM_PANEL_KERNEL", kernel)
     h = bmlib.bm_create(0)
     try:
         curve, k0, k1 = W.ellipse(1.0, 0.6), 6.0 - 0.1j, 9.0 - 0.15j
