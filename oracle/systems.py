@@ -26,7 +26,7 @@ import numpy as np
 
 import workloads as W
 from .geometry import Geometry, nodes
-from .operators import layer_operators
+from .operators import layer_entries, layer_operators
 
 
 @dataclass
@@ -85,6 +85,55 @@ def ordinary_matrix(g: Geometry, P: Params, literal_ordinary: bool = False) -> n
     A[N:, :N] = o1["D"] + 0.5 * I
     A[N:, N:] = -(1.0 if literal_ordinary else P.eps1) * o1["S"]
     return A
+
+
+def _row_ops(g: Geometry, k: complex, i: int) -> dict:
+    """Row i of S_k, D_k, D*_k, N_k (all N columns), entry by entry."""
+    J = np.arange(g.N)
+    return layer_entries(g, k, np.full(g.N, i), J)
+
+
+def mixed_rows(g: Geometry, P: Params, rows) -> np.ndarray:
+    """Selected rows (indices in 0..3N-1) of the 3N mixed matrix of Eq. dis_mixedBM, each built
+    from its own operator entries - for checks at sizes where the full matrix is too large."""
+    N = g.N
+    rows = np.asarray(rows, dtype=np.int64)
+    out = np.zeros((rows.size, 3 * N), dtype=np.complex128)
+    for a, i in enumerate(rows):
+        blk, ii = divmod(int(i), N)
+        e = np.zeros(N)
+        e[ii] = 1.0
+        if blk == 0:    # [I 0 M13]
+            out[a, ii] = 1.0
+            out[a, 2 * N:] = -_row_ops(g, P.k1, ii)["S"]
+        elif blk == 1:  # [0 I M23]
+            out[a, N + ii] = 1.0
+            out[a, 2 * N:] = -(_row_ops(g, P.k1, ii)["Ds"] + 0.5 * e) / P.eps1
+        else:           # [M31 M32 0]
+            o0 = _row_ops(g, P.k0, ii)
+            out[a, :N] = o0["D"] - 0.5 * e + P.beta * o0["N"]
+            out[a, N:2 * N] = -P.eps0 * (o0["S"] + P.beta * (o0["Ds"] + 0.5 * e))
+    return out
+
+
+def ordinary_rows(g: Geometry, P: Params, rows) -> np.ndarray:
+    """Selected rows (indices in 0..2N-1) of the 2N ordinary matrix of Eq. dis_BM (eps1 reading)."""
+    N = g.N
+    rows = np.asarray(rows, dtype=np.int64)
+    out = np.zeros((rows.size, 2 * N), dtype=np.complex128)
+    for a, i in enumerate(rows):
+        blk, ii = divmod(int(i), N)
+        e = np.zeros(N)
+        e[ii] = 1.0
+        if blk == 0:
+            o0 = _row_ops(g, P.k0, ii)
+            out[a, :N] = o0["D"] - 0.5 * e + P.beta * o0["N"]
+            out[a, N:] = -P.eps0 * (o0["S"] + P.beta * (o0["Ds"] + 0.5 * e))
+        else:
+            o1 = _row_ops(g, P.k1, ii)
+            out[a, :N] = o1["D"] + 0.5 * e
+            out[a, N:] = -P.eps1 * o1["S"]
+    return out
 
 
 def incident(g: Geometry, k0: complex, angle: float):

@@ -130,3 +130,18 @@ def test_near_singular_at_paper_eigenvalue():
     s1 = smin(ws + 0.05)
     s2 = smin(ws - 0.05j)
     assert s0 < 0.15 * min(s1, s2), (s0, s1, s2)
+
+
+def test_row_builders_match_the_assembled_systems():
+    # The entry-by-entry row builders (used for sampled checks at full size) reproduce rows of the
+    # dense systems, which the Mie-series pins above tie to the physics; ellipse, complex k,
+    # eps1 != 1, rows from every block row including the diagonal entries.
+    curve, N = W.ellipse(1.0, 0.6), 48
+    g = O.nodes(curve, N)
+    P = O.default_params(3.0 - 0.2j, 4.5 - 0.3j)
+    A = O.mixed_matrix(O.mixed_blocks(g, P))
+    rows = [0, 7, N - 1, N, N + 13, 2 * N - 1, 2 * N, 2 * N + 21, 3 * N - 1]
+    assert np.abs(O.mixed_rows(g, P, rows) - A[rows]).max() <= 1e-14 * np.abs(A).max()
+    Ao = O.ordinary_matrix(g, P)
+    rows = [0, 5, N - 1, N, N + 30, 2 * N - 1]
+    assert np.abs(O.ordinary_rows(g, P, rows) - Ao[rows]).max() <= 1e-14 * np.abs(Ao).max()
