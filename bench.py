@@ -223,7 +223,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    w = W.STAR_N4096 if not args.quick else W.scaled(W.STAR_N4096, 1024)
+    w = W.STAR_N4096
+    if args.quick or args.n:
+        w = W.scaled(W.STAR_N4096, args.n or 1024)
     prec = PREC[args.prec]
     phases = {}
 
@@ -428,6 +430,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="N=1024 instead of 4096 (smoke-sized)")
+    ap.add_argument("--n", type=int, default=0, help="another N for the same star workload (profiling sizes)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -177,7 +177,7 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
     const bool split = prec == BM_CF32_3XTF32_IR;
     p.n = (form == BM_MIXED) ? N : 2 * N;
     p.nsys = (form == BM_MIXED) ? 3 * N : 2 * N;
-    p.nb = nb_user > 0 ? nb_user : (c32 ? 128 : 64);
+    p.nb = nb_user > 0 ? nb_user : (c32 ? 256 : 64);
     p.ldF = pad32(p.n);
     size_t b = 7 * (size_t)N * 8;
     if (form == BM_MIXED) {

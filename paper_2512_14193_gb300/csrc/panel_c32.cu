@@ -7,25 +7,28 @@ namespace {
 // ------------------------------------------------------------------------------------------------
 // Lane-per-column panel kernel (FP32 complex).  A sub-panel of m rows x ib <= 32 columns is held
 // in registers with lane k of every warp holding column k: warp w of cluster CTA r owns the RPW
-// consecutive rows starting at r R + w RPW (R = 16 RPW rows per CTA).  Column c of a row is then
-// one warp shuffle away from every lane, so the column loop needs no per-column code copies (the
-// register-row kernel unrolls it 32 times, which overflows the instruction cache) and no select
-// chains over the row's registers.  Per column c:
+// consecutive rows starting at r R + w RPW (R = 16 RPW rows per CTA).  The column loop is a
+// compact runtime loop (the register-row kernel unrolls it 32 times, which overflows the
+// instruction cache).  Per column c:
 //   1. every lane tracks the best row of its own column (max |Re|+|Im|, then smallest row), so
-//      lane c of each warp holds the warp's candidate; the CTA's best comes from 16 shared entries;
-//   2. each CTA pushes its candidate row with its value and index, and the owner of row c pushes
-//      row c, into every CTA of the cluster with st.async; each receiver's mbarrier for this
-//      column completes when all bytes have landed (no cluster barrier, no fence);
-//   3. every CTA picks the pivot from the CL candidates;
+//      lane c of each warp holds the warp's candidate; the CTA's best is two warp reductions
+//      (redux.sync max of the value bits, then min of the row index among the maxima);
+//   2. each CTA stages its candidate row (with value and index) in its own shared memory and
+//      copies it into every CTA of the cluster with one cp.async.bulk per destination, issued by
+//      lanes 0..CL-1 in parallel; the owner of row c does the same with row c.  Each receiver's
+//      mbarrier for this column completes when all bytes have landed (no cluster barrier);
+//   3. every CTA picks the pivot from the CL candidates (the same two reductions);
 //   4. rows c and pivot are interchanged in the registers of their owners;
-//   5. rows below c: new = alpha row + a_c beta, with a_c the row's column-c entry (a shuffle) and
-//      per-lane (alpha, beta) = (1, 0) left of c, (0, 1/u_c) at c (the multiplier), and
+//   5. lane c stages its column (the rows' column-c entries) in shared memory and every lane
+//      reads it back as broadcasts; then on the rows below c, new = alpha row + a_c beta with
+//      per-lane (alpha, beta) = (1, 0) left of c, (0, 1/u_c) at c (the multiplier) and
 //      (1, -u_k / u_c) right of c (the rank-1 update): no divergent branches.
-// Receive buffers and mbarriers are double-buffered by column parity.  A CTA pushes column c + 2
-// only after it received every CTA's column c + 1 push, and each CTA pushes c + 1 only after it
-// has read its column c buffers, so a buffer is never overwritten while still in use.  Waits are
-// bounded (2 s by the global timer): on a timeout the kernel raises *err and carries on without
-// waiting, so every CTA still reaches the final cluster barrier.
+// Stage buffers, receive buffers and mbarriers are double-buffered by column parity.  A CTA sends
+// column c + 2 only after it received every CTA's column c + 1 data, and each CTA sends c + 1 only
+// after it has read its column c buffers (and its own column c copies have landed everywhere), so
+// no buffer is overwritten while still in use.  Waits are bounded (2 s by the global timer): on a
+// timeout the kernel raises *err and carries on without waiting, so every CTA still reaches the
+// final cluster barrier.
 // ------------------------------------------------------------------------------------------------
 template <int RPW>
 __device__ __forceinline__ float2 row_get(const float2 (&row)[RPW], int s) {
@@ -48,18 +51,20 @@ __device__ __forceinline__ uint32_t remote_addr(uint32_t local, int rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
     return r;
 }
-// 8 bytes into another CTA's shared memory, completing on that CTA's mbarrier
-__device__ __forceinline__ void push8(uint32_t raddr, uint32_t x, uint32_t y, uint32_t rbar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
-                 "r"(x), "r"(y), "r"(rbar)
+// bytes (a multiple of 16) from this CTA's shared memory into another CTA's, completing there
+__device__ __forceinline__ void bulk_push(uint32_t rdst, uint32_t lsrc, uint32_t bytes, uint32_t rbar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     rdst),
+                 "r"(lsrc), "r"(bytes), "r"(rbar)
                  : "memory");
 }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ uint64_t gtime() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait for phase `parity` of a local mbarrier, with cluster-scope acquire of the pushed data
+// bounded wait for phase `parity` of a local mbarrier, with cluster-scope acquire of the data
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok = 0;
     uint64_t t0 = 0;
@@ -75,6 +80,22 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
         else if (gtime() - t0 > 2000000000ull) return false;
     }
 }
+// best (value, row) over the warp: the largest value, then the smallest row.  Values are
+// non-negative floats, whose bit patterns order like the values; "no candidate" is (0, INT_MAX).
+__device__ __forceinline__ void warp_best(uint32_t& vbits, uint32_t& idx) {
+    const uint32_t vm = __reduce_max_sync(0xffffffffu, vbits);
+    idx = __reduce_min_sync(0xffffffffu, vbits == vm ? idx : 0xffffffffu);
+    vbits = vm;
+}
+// 1 / a by Smith's scaling, with IEEE reciprocals instead of divisions
+__device__ __forceinline__ float2 cinv_rcp(float2 a) {
+    if (fabsf(a.x) >= fabsf(a.y)) {
+        const float r = a.y * __frcp_rn(a.x), id = __frcp_rn(fmaf(a.y, r, a.x));
+        return make_float2(id, -r * id);
+    }
+    const float r = a.x * __frcp_rn(a.y), id = __frcp_rn(fmaf(a.x, r, a.y));
+    return make_float2(r * id, -id);
+}
 
 template <int RPW>
 __global__ void __launch_bounds__(PANEL_THREADS, 1)
@@ -83,22 +104,24 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
                     SwapMap* __restrict__ map_big, int* __restrict__ perm) {
     constexpr int WARPS = PANEL_THREADS / 32;
     constexpr int R = WARPS * RPW;
+    constexpr int CAND = 34;  // candidate record: 32 entries, then (value bits, row index), 8 pad bytes
     cg::cluster_group cluster = cg::this_cluster();
     const int cta = (int)cluster.block_rank();
     const int CL = (int)cluster.num_blocks();
-    __shared__ float2 cand_row[2][MAX_CLUSTER][32];
-    __shared__ float2 diag_row[2][32];
-    __shared__ uint2 cand_vi[2][MAX_CLUSTER];  // (value bits, row index)
+    __shared__ alignas(16) float2 cand_buf[2][MAX_CLUSTER][CAND];  // received candidates
+    __shared__ alignas(16) float2 diag_buf[2][32];                  // received row c
+    __shared__ alignas(16) float2 cand_stage[2][CAND];              // this CTA's candidate, to send
+    __shared__ alignas(16) float2 diag_stage[2][32];                // row c, to send (its owner)
+    __shared__ alignas(16) float2 colbuf[WARPS][RPW];               // column c of each warp's rows
     __shared__ alignas(8) uint64_t bars[2];
-    __shared__ float red_val[2][WARPS];
-    __shared__ int red_idx[2][WARPS];
+    __shared__ uint2 red[2][WARPS];
     __shared__ int s_map[MAP_MAX / 2 * 3 + MAP_MAX];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rb = cta * R;          // first panel row of this CTA
     const int wb = rb + warp * RPW;  // first panel row of this warp
     const float2 zero = make_float2(0.f, 0.f);
-    const uint32_t bytes = (uint32_t)CL * (32 * 8 + 8) + 32 * 8;  // per column, at every receiver
+    const uint32_t bytes = (uint32_t)CL * (CAND * 8) + 32 * 8;  // per column, at every receiver
     bool timed_out = false;
 
     if (threadIdx.x == 0) {
@@ -122,7 +145,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         bi = (v > bv) ? g : bi;
         bv = fmaxf(v, bv);
     }
-    cluster.sync();  // mbarriers initialised and every CTA running before the first push
+    cluster.sync();  // mbarriers initialised and every CTA running before the first copy
 
 #pragma unroll 1
     for (int c = 0; c < ib; ++c) {
@@ -131,67 +154,53 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         if (threadIdx.x == 0)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
         // ---- (1) CTA candidate of column c ----
-        if (lane == c) {
-            red_val[par][warp] = bv;
-            red_idx[par][warp] = bi;
-        }
+        if (lane == c) red[par][warp] = (bi != INT_MAX) ? make_uint2(__float_as_uint(bv), (uint32_t)bi)
+                                                         : make_uint2(0u, (uint32_t)INT_MAX);
         __syncthreads();
-        float cv = (lane < WARPS) ? red_val[par][lane] : -1.f;
-        int ci = (lane < WARPS) ? red_idx[par][lane] : INT_MAX;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, cv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
-            if (better(ov, oi, cv, ci)) {
-                cv = ov;
-                ci = oi;
-            }
+        uint32_t cvb = 0u, ciu = (uint32_t)INT_MAX;
+        if (lane < WARPS) {
+            const uint2 e = red[par][lane];
+            cvb = e.x;
+            ciu = e.y;
         }
-        // ---- (2) push: candidate row (its owner warp, else warp 0 sends zeros) and row c ----
+        warp_best(cvb, ciu);
+        const int ci = (int)ciu;
+        // ---- (2) send the candidate row (its owner warp, else warp 0 sends zeros) and row c ----
         const bool has = ci != INT_MAX;
-        const int owner = has ? (ci - rb) / RPW : 0;
-        if (warp == owner) {
-            const float2 v = has ? row_get<RPW>(row, ci - wb) : zero;
-            const uint32_t la = smem_addr(&cand_row[par][cta][lane]);
-            for (int d = 0; d < CL; ++d)
-                push8(remote_addr(la, d), __float_as_uint(v.x), __float_as_uint(v.y), remote_addr(bar, d));
+        if (warp == (has ? (ci - rb) / RPW : 0)) {
+            cand_stage[par][lane] = has ? row_get<RPW>(row, ci - wb) : zero;
+            if (lane == 0) reinterpret_cast<uint4*>(&cand_stage[par][32])[0] = make_uint4(cvb, ciu, 0u, 0u);
+            fence_async_smem();
+            __syncwarp();
             if (lane < CL)
-                push8(remote_addr(smem_addr(&cand_vi[par][cta]), lane), __float_as_uint(has ? cv : -1.f), (uint32_t)ci,
-                      remote_addr(bar, lane));
+                bulk_push(remote_addr(smem_addr(&cand_buf[par][cta][0]), lane), smem_addr(&cand_stage[par][0]),
+                          CAND * 8, remote_addr(bar, lane));
         }
         if (c >= wb && c < wb + RPW) {
-            const float2 v = row_get<RPW>(row, c - wb);
-            const uint32_t la = smem_addr(&diag_row[par][lane]);
-            for (int d = 0; d < CL; ++d)
-                push8(remote_addr(la, d), __float_as_uint(v.x), __float_as_uint(v.y), remote_addr(bar, d));
+            diag_stage[par][lane] = row_get<RPW>(row, c - wb);
+            fence_async_smem();
+            __syncwarp();
+            if (lane < CL)
+                bulk_push(remote_addr(smem_addr(&diag_buf[par][0]), lane), smem_addr(&diag_stage[par][0]), 32 * 8,
+                          remote_addr(bar, lane));
         }
-        // ---- (3) wait for every push of this column, pick the pivot ----
+        // ---- (3) wait for this column's data, pick the pivot ----
         if (!timed_out && !bar_wait(bar, (uint32_t)(c >> 1) & 1u)) {
             timed_out = true;
             atomicExch(err, 1);
         }
-        float pv = -1.f;
-        int pi = INT_MAX;
+        uint32_t pvb = 0u, piu = (uint32_t)INT_MAX;
         if (lane < CL) {
-            const uint2 e = cand_vi[par][lane];
-            pv = __uint_as_float(e.x);
-            pi = (int)e.y;
+            const uint2 e = reinterpret_cast<const uint2*>(&cand_buf[par][lane][32])[0];
+            pvb = e.x;
+            piu = e.y;
         }
-        int pq = lane;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, pv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, pi, o);
-            const int oq = __shfl_xor_sync(0xffffffffu, pq, o);
-            if (better(ov, oi, pv, pi)) {
-                pv = ov;
-                pi = oi;
-                pq = oq;
-            }
-        }
-        const float2 u = cand_row[par][pq][lane];
-        const float2 dr = diag_row[par][lane];
-        const bool sing = !(pv > 0.f);
+        warp_best(pvb, piu);
+        const int pi = (int)piu;
+        const int pq = (pi != INT_MAX) ? pi / R : 0;  // the CTA that owns the pivot row
+        const float2 u = cand_buf[par][pq][lane];
+        const float2 dr = diag_buf[par][lane];
+        const bool sing = !(__uint_as_float(pvb) > 0.f);
         if (cta == 0 && threadIdx.x == 0) {
             ipiv[j0 + c] = j0 + pi;
             if (sing && info != nullptr && *info == 0) *info = j0 + c + 1;
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         }
         // ---- (5) new = alpha row + a_c beta on the rows below c; candidates of the next columns ----
         const float2 ucc = make_float2(__shfl_sync(0xffffffffu, u.x, c), __shfl_sync(0xffffffffu, u.y, c));
-        const float2 inv = sing ? make_float2(1.f, 0.f) : cinv(ucc);
+        const float2 inv = sing ? make_float2(1.f, 0.f) : cinv_rcp(ucc);
         float alpha;
         float2 beta;
         if (lane < c) {
@@ -216,24 +225,53 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
             alpha = 1.f;
             beta = cmul(make_float2(-u.x, -u.y), inv);
         }
+        if (lane == c) {
+#pragma unroll
+            for (int r = 0; r < RPW; r += 2)
+                *reinterpret_cast<float4*>(&colbuf[warp][r]) = make_float4(row[r].x, row[r].y, row[r + 1].x,
+                                                                           row[r + 1].y);
+        }
+        __syncwarp();
         bv = -1.f;
         bi = INT_MAX;
         const int r_lo = c + 1 - wb;  // rows r >= r_lo lie below c
         const int r_hi = m - wb;      // rows r < r_hi exist
+        if (r_lo <= 0 && r_hi >= RPW) {
 #pragma unroll
-        for (int r = 0; r < RPW; ++r) {
-            if (r >= r_lo && r < r_hi) {  // uniform across the warp
-                const float ax = __shfl_sync(0xffffffffu, row[r].x, c);
-                const float ay = __shfl_sync(0xffffffffu, row[r].y, c);
-                float2 t;
-                t.x = fmaf(ax, beta.x, fmaf(-ay, beta.y, alpha * row[r].x));
-                t.y = fmaf(ax, beta.y, fmaf(ay, beta.x, alpha * row[r].y));
-                row[r] = t;
-                const float v = cnorm1(t);
-                bi = (v > bv) ? wb + r : bi;
-                bv = fmaxf(v, bv);
+            for (int r = 0; r < RPW; r += 2) {
+                const float4 a2 = *reinterpret_cast<const float4*>(&colbuf[warp][r]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float ax = h ? a2.z : a2.x, ay = h ? a2.w : a2.y;
+                    float2 t;
+                    t.x = fmaf(ax, beta.x, fmaf(-ay, beta.y, alpha * row[r + h].x));
+                    t.y = fmaf(ax, beta.y, fmaf(ay, beta.x, alpha * row[r + h].y));
+                    row[r + h] = t;
+                    const float v = cnorm1(t);
+                    bi = (v > bv) ? wb + r + h : bi;
+                    bv = fmaxf(v, bv);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < RPW; r += 2) {
+                const float4 a2 = *reinterpret_cast<const float4*>(&colbuf[warp][r]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (r + h >= r_lo && r + h < r_hi) {
+                        const float ax = h ? a2.z : a2.x, ay = h ? a2.w : a2.y;
+                        float2 t;
+                        t.x = fmaf(ax, beta.x, fmaf(-ay, beta.y, alpha * row[r + h].x));
+                        t.y = fmaf(ax, beta.y, fmaf(ay, beta.x, alpha * row[r + h].y));
+                        row[r + h] = t;
+                        const float v = cnorm1(t);
+                        bi = (v > bv) ? wb + r + h : bi;
+                        bv = fmaxf(v, bv);
+                    }
+                }
             }
         }
+        __syncwarp();  // colbuf is rewritten by the next column
     }
 #pragma unroll
     for (int r = 0; r < RPW; ++r) {
@@ -257,7 +295,7 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
             }
         }
     }
-    // no CTA leaves while a push into its shared memory could still be on the way (only possible
+    // no CTA leaves while a copy into its shared memory could still be on the way (only possible
     // after a timed-out wait)
     cluster.sync();
 }
