@@ -427,6 +427,7 @@ def run_ours(args, ws, rank, local):
 
     bm.bm_destroy(hm)
     bm.bm_destroy(ho)
+    ssm = None if args.no_ssm else ssm_measure(bm, local)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -441,7 +442,33 @@ def run_ours(args, ws, rank, local):
                     "d2h_bytes_per_step": hbytes, "ms": e2e_s * 1e3,
                     "path": "bm_factor + bm_solve with pinned host B/X (copies inside bm_solve)"},
             "clocks": clk.summary(), "gpu_launches": int(launches)}
+    if ssm is not None:
+        line["ssm"] = ssm
     print(json.dumps(line), flush=True)
+
+
+def ssm_measure(bm, device: int):
+    """Contour batch (block Sakurai-Sugiura, section 5.3): ellipse 1.0/0.6, N = 1024, mixed system,
+    k_in = 1.5 k_out, circle centre 5 radius 0.5, 32 points, 16 Gaussian probes, 4 moments.  The
+    FP32 tensor-core path (FP64 residuals, refined to the FP64 path's accuracy) against the FP64
+    path; a warm-up call each, then one timed call (wall clock of bm_ssm)."""
+    N, L, P = 1024, 16, 32
+    V = np.asfortranarray(W.gaussian_full(3 * N, L, 0))
+    cv = W.ellipse(1.0, 0.6)
+    out = {"workload": "ellipse 1.0/0.6, N=1024 (mixed), k_in=1.5 k_out, circle centre 5 radius 0.5, "
+                       "32 points, 16 probes (seed 0), 4 moments, rank cut 1e-6"}
+    for name, opts in (("3xtf32", bm.make_opts(2, refine_tol=1e-15, residual=bm.BM_RESID_FP64_ALL)),
+                       ("fp64", bm.make_opts(0))):
+        for rep in range(2):
+            t0 = time.perf_counter()
+            om, sig, info = bm.bm_ssm(device, cv.kind, cv.params4(), N, W.MIXED, opts, 5.0, 0.5, P, 4, 1.5, V,
+                                      rank_tol=1e-6)
+            t = time.perf_counter() - t0
+        out[name] = {"ms": t * 1e3, "contour_points_per_s": P / t, "solves_per_s": P * L / t, "rank": info.rank,
+                     "n_inside": info.n_inside, "max_backward_error": info.max_backward_error,
+                     "max_refine_iterations": info.max_iterations}
+    out["speedup_3xtf32_over_fp64"] = out["fp64"]["ms"] / out["3xtf32"]["ms"]
+    return out
 
 
 def main():
@@ -452,6 +479,7 @@ def main():
     ap.add_argument("--prec", choices=list(PREC), default="3xtf32")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ssm", action="store_true", help="skip the contour-batch (Sakurai-Sugiura) timing")
     ap.add_argument("--quick", action="store_true", help="N=1024 instead of 4096 (smoke-sized)")
     ap.add_argument("--n", type=int, default=0, help="another N for the same star workload (profiling sizes)")
     args = ap.parse_args()

@@ -95,7 +95,10 @@ typedef struct {
  *        ~1e-12 of |A||x|), later ones updated as r -= A d with the product in FP32 (d, the last
  *        correction, is small by then, so the update error stays far below refine_tol);
  *     BM_RESID_FP64_UPDATE (1): the first residual in FP64, later ones updated as above;
- *     BM_RESID_FP64_ALL (2): every residual in FP64. */
+ *     BM_RESID_FP64_ALL (2): every residual in FP64.
+ *  The updated residuals of modes 0 and 1 carry the FP32 product error of each update, so the
+ *  backward error they track is reliable down to about 1e-12; refine_tol below 1e-12 needs
+ *  BM_RESID_FP64_ALL (bm_assemble returns BM_EINVAL otherwise). */
 typedef struct {
     double eps0;
     bm_c64 eps1;
@@ -190,6 +193,53 @@ bm_status bm_far_field(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const do
 #define BM_FAR_FIELD_STATIC_MAX_ANGLES 8192
 bm_status bm_far_field_static(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const double* angles,
                               int M, bm_c64* Uinf, int ldu);
+
+/* ---- Contour eigenvalue solver (section 5.3, sec:ssm) ----
+ * The paper finds the complex omega at which the discretised system is singular with the
+ * Sakurai-Sugiura projection method, solving the system at the quadrature points of a closed
+ * contour for random right-hand sides (which Corollary lem:for_ssm_RHS serves for the mixed
+ * system); it cites the method without its steps.  bm_ssm takes the block Hankel variant:
+ *   points   z_p = center + radius zeta_p, zeta_p = exp(i 2 pi (p + 1/2) / npoints), p < npoints,
+ *            in the k_out = omega plane (eps0 = 1), with k_in = k_ratio z_p (eps1 = k_ratio^2 fixed;
+ *            beta = i / k_out unless opts fix it);
+ *   moments  mu_k = sum_p w_p zeta_p^k V^H T(z_p)^{-1} V, w_p = radius zeta_p / npoints, k < 2M
+ *            (L x L each; V holds L probe columns of the system's size);
+ *   Hankel   H = [mu_{i+j}], Hs = [mu_{i+j+1}] (LM x LM block Hankel matrices);
+ *   rank     H = W1 S W2^H, r = #{s_i > rank_tol s_1};
+ *   pencil   the eigenvalues zeta of W1_r^H Hs W2_r S_r^{-1} give omega = center + radius zeta.
+ * Every contour point is assembled, factored and solved on the device (as bm_assemble, bm_factor,
+ * bm_solve, in the precision opts->prec selects), `workers` points at a time on their own streams;
+ * the moments, Hankel matrices and the small pencil are formed on the device, the small SVD and
+ * eigenvalue problem (size L M at most 256) use cuSOLVER. */
+typedef struct {
+    bm_c64 center;    /* contour centre in the k_out plane */
+    double radius;    /* circle radius, > 0 */
+    int npoints;      /* trapezoid points, 4 .. 4096 */
+    int nmoments;     /* M, 1 .. 16 */
+    bm_c64 k_ratio;   /* k_in = k_ratio * k_out on the contour */
+    double rank_tol;  /* relative singular-value cut; 0 selects 1e-8 */
+    int workers;      /* contour points in flight at once, 1 .. 16; 0 selects 4 */
+} bm_ssm_opts;
+
+typedef struct {
+    int rank;            /* r */
+    int n_inside;        /* eigenvalues inside the contour (|zeta| < 1), listed first in omega */
+    int max_iterations;  /* most refinement iterations over the contour points (CF32 precisions) */
+    double max_backward_error;  /* largest backward error of the contour solves */
+    double t_total_ms;   /* wall time of the call */
+    double t_points_ms;  /* wall time of the contour points (assemble + factor + solve + projection) */
+} bm_ssm_info;
+
+/* Eigenvalues of the discretised system `form` (curve, N as in bm_assemble) inside a circle.
+ *  V      : host array, nsys x L column-major (ldv >= nsys; nsys = 3N mixed, 2N ordinary), the
+ *           probe right-hand sides (also used as the left projection), 1 <= L, L * M <= 256.
+ *  omega  : output, the r eigenvalues (cap >= L * M): those inside the contour first, each group
+ *           ordered by real part.  sigma: output, the L * M singular values of H (may be NULL).
+ * Errors: BM_EINVAL (arguments), BM_ESINGULAR (a contour point hits an exactly singular system),
+ * BM_ENOTCONV (refinement), BM_ENOMEM, BM_ECUDA; bm_last_error names the point. */
+bm_status bm_ssm(int device, const bm_curve* curve, int N, bm_formulation form, const bm_opts* opts,
+                 const bm_ssm_opts* ssm, const bm_c64* V, int ldv, int L, bm_c64* omega, int cap,
+                 double* sigma, bm_ssm_info* info);
 
 /* Copy one assembled FP64 block to dst (column-major, ldd >= rows).
  * Mixed: which = 0..3 selects M13, M23, M31, M32 (N x N).

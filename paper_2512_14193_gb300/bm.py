@@ -47,6 +47,16 @@ class bm_solve_info(C.Structure):
                 ("t_residual_ms", C.c_double)]
 
 
+class bm_ssm_opts(C.Structure):
+    _fields_ = [("center", bm_c64), ("radius", C.c_double), ("npoints", C.c_int), ("nmoments", C.c_int),
+                ("k_ratio", bm_c64), ("rank_tol", C.c_double), ("workers", C.c_int)]
+
+
+class bm_ssm_info(C.Structure):
+    _fields_ = [("rank", C.c_int), ("n_inside", C.c_int), ("max_iterations", C.c_int),
+                ("max_backward_error", C.c_double), ("t_total_ms", C.c_double), ("t_points_ms", C.c_double)]
+
+
 class BMError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -74,6 +84,8 @@ def lib():
     L.bm_far_field.argtypes = [P, P, I, I, C.POINTER(D), I, P, I, I]
     L.bm_far_field_static.argtypes = [P, P, I, I, C.POINTER(D), I, P, I]
     L.bm_copy_block.argtypes = [P, I, P, I, I]
+    L.bm_ssm.argtypes = [I, C.POINTER(bm_curve), I, I, C.POINTER(bm_opts), C.POINTER(bm_ssm_opts), P, I, I, P, I,
+                         C.POINTER(D), C.POINTER(bm_ssm_info)]
     L.bm_hankel01.argtypes = [P, P, I, P, P, I]
     L.bm_hankel_anchor_table.argtypes = [C.POINTER(D), I, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(D),
                                          C.POINTER(D)]
@@ -86,7 +98,7 @@ def lib():
     L.bm_last_error.argtypes = []
     L.bm_last_error.restype = C.c_char_p
     for name in ("bm_create", "bm_assemble", "bm_factor", "bm_rhs_plane_wave", "bm_solve", "bm_far_field",
-                 "bm_far_field_static",
+                 "bm_far_field_static", "bm_ssm",
                  "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_memory", "bm_destroy",
                  "bm_kernel_launches", "bm_enqueue_probe"):
         getattr(L, name).restype = C.c_int
@@ -224,6 +236,36 @@ def bm_far_field_static(h, X, angles, U) -> None:
     ang = np.ascontiguousarray(angles, dtype=np.float64)
     _check(lib().bm_far_field_static(h, px, ldx, nx, ang.ctypes.data_as(C.POINTER(C.c_double)), int(ang.size), pu,
                                      ldu), "bm_far_field_static")
+
+
+def bm_ssm(device: int, kind: int, params, N: int, formulation: int, opts: bm_opts | None, center, radius: float,
+           npoints: int, nmoments: int, k_ratio, V, rank_tol: float = 0.0, workers: int = 0):
+    """Eigenvalues inside a circle (block Sakurai-Sugiura).  V: host (nsys x L) probe columns.
+    Returns (omega[r] with the n_inside interior ones first, sigma[L M], bm_ssm_info)."""
+    cv = bm_curve()
+    cv.kind = int(kind)
+    p = list(params) + [0.0] * (4 - len(params))
+    for i in range(4):
+        cv.p[i] = float(p[i])
+    so = bm_ssm_opts()
+    so.center = _c64(center)
+    so.radius = float(radius)
+    so.npoints = int(npoints)
+    so.nmoments = int(nmoments)
+    so.k_ratio = _c64(k_ratio)
+    so.rank_tol = float(rank_tol)
+    so.workers = int(workers)
+    pv, ldv, L, dev, _kv = _colmajor(V, 0, writable=False)
+    if dev:
+        raise ValueError("bm_ssm takes host probe vectors")
+    cap = L * int(nmoments)
+    om = np.zeros(cap, dtype=np.complex128)
+    sig = np.zeros(cap, dtype=np.float64)
+    info = bm_ssm_info()
+    _check(lib().bm_ssm(int(device), C.byref(cv), int(N), int(formulation), C.byref(opts) if opts is not None else None,
+                        C.byref(so), pv, ldv, L, C.c_void_p(om.ctypes.data), cap,
+                        sig.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info)), "bm_ssm")
+    return om[:info.rank].copy(), sig, info
 
 
 def bm_copy_block(h, which: int, dst) -> None:

@@ -65,7 +65,11 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
     with cf.ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(compile_one, sources))
     tmp = LIB + ".tmp"
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
+    # cuSOLVER (the contour solver's small SVD and eigenvalue problem) links dynamically from the
+    # toolkit, found at run time through the rpath
+    cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lcusolver", "-lrt", "-ldl", "-lpthread",
+           "-Xlinker", f"-rpath={cudalib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -370,6 +370,12 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     int nb = opts ? opts->nb : 0;
     if (opts && (opts->refine_residual < BM_RESID_DF_UPDATE || opts->refine_residual > BM_RESID_FP64_ALL))
         return BM_EINVAL;
+    if (opts && opts->refine_tol > 0 && opts->refine_tol < 1e-12 && opts->refine_residual != BM_RESID_FP64_ALL &&
+        prec != BM_FP64) {
+        bm_set_error("refine_tol below 1e-12 needs refine_residual = BM_RESID_FP64_ALL (updated residuals are "
+                     "reliable to about 1e-12)");
+        return BM_EINVAL;
+    }
     if (nb != 0 && (nb % 32 != 0 || nb < 32 || nb > 256)) {
         bm_set_error("nb must be a multiple of 32 in [32, 256]");
         return BM_EINVAL;
@@ -393,10 +399,15 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
 
     BM_CUDA_TRY(cudaSetDevice(c->device));
     cudaStreamSynchronize(c->stream);
-    free_problem(c);
+    Plan p = make_plan(N, form, prec, nb, 64);
+    // Same shape as the assembled system: assemble again into the same buffers (no device
+    // allocation or release - cudaFree would wait for every stream of the device - and the cached
+    // graphs and tensor maps stay valid, as they depend only on these pointers and sizes).
+    const bool reuse = c->assembled && c->N == N && c->form == form && c->prec == prec && c->nb == p.nb &&
+                       curve->kind != BM_CURVE_USER;
+    if (!reuse) free_problem(c);
     c->bs_solve = 64;
-    Plan p = make_plan(N, form, prec, nb, c->bs_solve);
-    if (c->held + p.bytes > c->budget) {
+    if (!reuse && c->held + p.bytes > c->budget) {
         bm_set_error("admission: system needs " + std::to_string(p.bytes) + " bytes, budget leaves " +
                      std::to_string(c->budget - c->held));
         return BM_ENOMEM;
@@ -424,7 +435,10 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     c->ldk_lu = p.ldk_lu;
     c->ldk_c = p.ldk_c;
     const bool c32 = prec != BM_FP64;
-    bm_status s = alloc_t(c, &c->d_geom, 7 * (size_t)N * 8);
+    c->assembled = c->factored = c->singular = false;
+    bm_status s = BM_OK;
+    if (!reuse) {
+    s = alloc_t(c, &c->d_geom, 7 * (size_t)N * 8);
     if (s == BM_OK && form == BM_MIXED) {
         s = alloc_t(c, &c->d_Mtop, (size_t)p.ldtop * N * 16);
         if (s == BM_OK) s = alloc_t(c, &c->d_Mbot, (size_t)p.ldbot * 2 * N * 16);
@@ -471,8 +485,9 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
         free_problem(c);
         return s;
     }
+    }  // !reuse
     cudaStream_t st = c->stream;
-    if (c32) {
+    if (c32 && !reuse) {
         size_t lb = (size_t)p.n * p.ldk_lu * 4;
         BM_CUDA_TRY(cudaMemsetAsync(c->d_Lp_r, 0, lb, st));
         BM_CUDA_TRY(cudaMemsetAsync(c->d_Lp_i, 0, lb, st));

@@ -61,3 +61,15 @@ def test_budget_admission(bmlib):
         assert bmlib.bm_memory(h)[0] <= budget
     finally:
         bmlib.bm_destroy(h)
+
+
+@pytest.mark.gpu
+def test_tight_tolerance_needs_fp64_residuals(bmlib, handle):
+    # updated residuals are only trusted to ~1e-12: a tighter target with them is refused
+    curve = W.circle(1.0)
+    with pytest.raises(bmlib.BMError) as e:
+        bmlib.bm_assemble(handle, curve.kind, curve.params4(), 64, 2.0, 3.0, bmlib.BM_MIXED,
+                          bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=1e-14, residual=0))
+    assert e.value.status == bmlib.BM_EINVAL
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), 64, 2.0, 3.0, bmlib.BM_MIXED,
+                      bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=1e-14, residual=2))
