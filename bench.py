@@ -428,6 +428,7 @@ def run_ours(args, ws, rank, local):
     bm.bm_destroy(hm)
     bm.bm_destroy(ho)
     ssm = None if args.no_ssm else ssm_measure(bm, local)
+    serve = None if args.no_serve else serve_measure(bm, local)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -444,6 +445,8 @@ def run_ours(args, ws, rank, local):
             "clocks": clk.summary(), "gpu_launches": int(launches)}
     if ssm is not None:
         line["ssm"] = ssm
+    if serve is not None:
+        line["serving"] = serve
     print(json.dumps(line), flush=True)
 
 
@@ -471,6 +474,54 @@ def ssm_measure(bm, device: int):
     return out
 
 
+def serve_measure(bm, device: int, n_req: int = 120, slots: int = 8):
+    """Serving stream (first n_req requests of workloads.serving_stream, seed 0: star curves, N in
+    {256 .. 8192}, complex k_out, k_in = 1.5 k_out, 1..64 Gaussian right-hand sides each, mixed
+    system, 3xTF32 + refinement to 1e-9).  Capacity: all requests submitted at once, wall time to
+    drain.  Latency: the same requests arriving as a Poisson process at 0.8 x that capacity;
+    p50 / p99 of submit-to-done."""
+    reqs = W.serving_stream(n_req, seed=0)
+    Bs = [np.asfortranarray(W.place_rhs(W.gaussian_g(r["N"], r["nrhs"], 1000 + i), r["N"], W.MIXED))
+          for i, r in enumerate(reqs)]
+    opts = bm.make_opts(2)
+
+    def run(arrivals):
+        s = bm.bm_server_create(device, slots=slots, opts=opts)
+        Xs = [np.zeros_like(B, order="F") for B in Bs]
+        t0 = time.perf_counter()
+        tickets = []
+        for r, B, X, ta in zip(reqs, Bs, Xs, arrivals):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(bm.bm_server_submit(s, r["curve"].kind, r["curve"].params4(), r["N"], r["k_out"],
+                                               r["k_in"], W.MIXED, B, X))
+        res = [bm.bm_server_wait(s, t) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = bm.bm_server_stats_get(s)
+        bm.bm_server_destroy(s)
+        return res, wall, st
+
+    run([0.0] * 8)  # warm-up (the first 8 requests): memory pool, libraries
+    res, wall, st = run([0.0] * n_req)
+    cap = n_req / wall
+    nrhs_tot = sum(r["nrhs"] for r in reqs)
+    lam = 0.8 * cap
+    arrivals = [r["t"] / lam for r in reqs]
+    res2, wall2, st2 = run(arrivals)
+    lat = np.array([r.t_queue_ms + r.t_service_ms for r in res2])
+    return {"workload": f"first {n_req} requests of the serving stream (seed 0): star curves, N in "
+                        "{256..8192}, Re k_out in [2, 40], Im in [-0.5, 0], k_in = 1.5 k_out, nrhs 1..64; "
+                        "mixed system, 3xTF32 + refinement to 1e-9",
+            "slots": slots, "capacity_requests_per_s": cap, "capacity_solves_per_s": nrhs_tot / wall,
+            "poisson_rate_requests_per_s": lam, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "solves_per_s_at_rate": nrhs_tot / wall2,
+            "max_backward_error": max(r.backward_error for r in res + res2),
+            "max_in_flight": max(st.max_in_flight, st2.max_in_flight),
+            "max_in_flight_gb": max(st.max_in_flight_bytes, st2.max_in_flight_bytes) / 1e9,
+            "budget_gb": st.budget_bytes / 1e9}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,6 +531,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ssm", action="store_true", help="skip the contour-batch (Sakurai-Sugiura) timing")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream timing")
     ap.add_argument("--quick", action="store_true", help="N=1024 instead of 4096 (smoke-sized)")
     ap.add_argument("--n", type=int, default=0, help="another N for the same star workload (profiling sizes)")
     args = ap.parse_args()

@@ -175,9 +175,10 @@ bm_status bm_far_field(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const do
 
 /* The far field of bm_far_field (same kernel, same result) for callers that must not allocate
  * device memory while they run; the paper has no counterpart, it is a library service.
- * bm_far_field allocates and frees a small device buffer for the angles on each call: cudaFree
- * waits for all work on the device, which stalls a serving loop that keeps other streams busy,
- * and the allocation fails once the handle's HBM budget is spent.  This call instead copies the
+ * bm_far_field allocates and frees a small device buffer for the angles on each call, charged to
+ * the handle's HBM budget: once resident systems have used the budget up it fails with BM_ENOMEM,
+ * and each allocation may have to grow the device's memory pool, which a caller holding a
+ * fixed device-memory footprint (a serving loop sized to the GPU) cannot allow.  This call copies the
  * angles into a fixed device array of BM_FAR_FIELD_STATIC_MAX_ANGLES doubles (64 KB) built into
  * the library, and allocates nothing.
  *  X    : device array, nsys x nrhs column-major solutions (ldx >= nsys), as from bm_solve.
@@ -240,6 +241,63 @@ typedef struct {
 bm_status bm_ssm(int device, const bm_curve* curve, int N, bm_formulation form, const bm_opts* opts,
                  const bm_ssm_opts* ssm, const bm_c64* V, int ldv, int L, bm_c64* omega, int cap,
                  double* sigma, bm_ssm_info* info);
+
+/* ---- Serving: continuous batching of independent solves ----
+ * A library service around the solver (the paper has no counterpart; its solves arrive as a
+ * stream, for instance the contour points of section 5.3).  A server owns `slots` worker handles,
+ * each with its own stream and host thread.  Requests (any curve, N, wavenumbers, formulation and
+ * nrhs) queue in arrival order; the head of the queue is admitted as soon as a slot is free and
+ * its device bytes fit what the HBM budget leaves beside the requests in flight, so requests that
+ * arrive while others run join them and their work overlaps on the device.  A worker assembles,
+ * factors (the factors stay on the device for the solve) and solves its request, then releases the
+ * request's device memory before taking the next one.  Every kernel is deterministic and each
+ * request has its own buffers, so a result is the same whether it ran alone or in the mix. */
+typedef struct bm_server bm_server;
+
+typedef struct {
+    int slots;                /* requests on the device at once, 1 .. 32 */
+    size_t hbm_budget_bytes;  /* admission budget over the requests in flight (0: 80 % of free memory) */
+    bm_opts opts;             /* options of every request (precision, refinement, block size) */
+} bm_server_opts;
+
+typedef struct {
+    bm_curve curve;
+    int N;
+    bm_c64 k_out, k_in;
+    int formulation;          /* bm_formulation */
+    int nrhs;
+    const bm_c64* B;          /* host, nsys x nrhs (ldb >= nsys) */
+    int ldb;
+    bm_c64* X;                /* host output, nsys x nrhs (ldx >= nsys) */
+    int ldx;
+} bm_request;                 /* B, X (and a user curve) must stay valid until bm_server_wait returns */
+
+typedef struct {
+    int status;               /* bm_status of the request */
+    int slot;                 /* worker that ran it */
+    int iterations;           /* refinement corrections */
+    double backward_error;
+    double t_queue_ms;        /* submit -> admitted */
+    double t_service_ms;      /* admitted -> done */
+    size_t bytes;             /* device bytes admitted for it */
+} bm_result;
+
+typedef struct {
+    unsigned long long submitted, completed;
+    size_t max_in_flight_bytes;  /* high-water mark of admitted bytes (never above the budget) */
+    int max_in_flight;           /* high-water mark of requests on the device at once */
+    size_t budget_bytes;
+} bm_server_stats;
+
+bm_status bm_server_create(bm_server** out, int device, const bm_server_opts* opts);
+/* Queue a request; returns at once with its ticket.  BM_ENOMEM if it alone exceeds the budget,
+ * BM_EINVAL for bad sizes or pointers. */
+bm_status bm_server_submit(bm_server* s, const bm_request* req, unsigned long long* ticket);
+/* Wait for a request and collect its result (each ticket once). */
+bm_status bm_server_wait(bm_server* s, unsigned long long ticket, bm_result* res);
+bm_status bm_server_stats_get(bm_server* s, bm_server_stats* st);
+/* Finish every queued request, stop the workers, release the handles. */
+bm_status bm_server_destroy(bm_server* s);
 
 /* Copy one assembled FP64 block to dst (column-major, ldd >= rows).
  * Mixed: which = 0..3 selects M13, M23, M31, M32 (N x N).

@@ -57,6 +57,25 @@ class bm_ssm_info(C.Structure):
                 ("max_backward_error", C.c_double), ("t_total_ms", C.c_double), ("t_points_ms", C.c_double)]
 
 
+class bm_server_opts(C.Structure):
+    _fields_ = [("slots", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("opts", bm_opts)]
+
+
+class bm_request(C.Structure):
+    _fields_ = [("curve", bm_curve), ("N", C.c_int), ("k_out", bm_c64), ("k_in", bm_c64), ("formulation", C.c_int),
+                ("nrhs", C.c_int), ("B", C.c_void_p), ("ldb", C.c_int), ("X", C.c_void_p), ("ldx", C.c_int)]
+
+
+class bm_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("slot", C.c_int), ("iterations", C.c_int), ("backward_error", C.c_double),
+                ("t_queue_ms", C.c_double), ("t_service_ms", C.c_double), ("bytes", C.c_size_t)]
+
+
+class bm_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_ulonglong), ("completed", C.c_ulonglong), ("max_in_flight_bytes", C.c_size_t),
+                ("max_in_flight", C.c_int), ("budget_bytes", C.c_size_t)]
+
+
 class BMError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -84,6 +103,11 @@ def lib():
     L.bm_far_field.argtypes = [P, P, I, I, C.POINTER(D), I, P, I, I]
     L.bm_far_field_static.argtypes = [P, P, I, I, C.POINTER(D), I, P, I]
     L.bm_copy_block.argtypes = [P, I, P, I, I]
+    L.bm_server_create.argtypes = [C.POINTER(P), I, C.POINTER(bm_server_opts)]
+    L.bm_server_submit.argtypes = [P, C.POINTER(bm_request), C.POINTER(C.c_ulonglong)]
+    L.bm_server_wait.argtypes = [P, C.c_ulonglong, C.POINTER(bm_result)]
+    L.bm_server_stats_get.argtypes = [P, C.POINTER(bm_server_stats)]
+    L.bm_server_destroy.argtypes = [P]
     L.bm_ssm.argtypes = [I, C.POINTER(bm_curve), I, I, C.POINTER(bm_opts), C.POINTER(bm_ssm_opts), P, I, I, P, I,
                          C.POINTER(D), C.POINTER(bm_ssm_info)]
     L.bm_hankel01.argtypes = [P, P, I, P, P, I]
@@ -98,7 +122,8 @@ def lib():
     L.bm_last_error.argtypes = []
     L.bm_last_error.restype = C.c_char_p
     for name in ("bm_create", "bm_assemble", "bm_factor", "bm_rhs_plane_wave", "bm_solve", "bm_far_field",
-                 "bm_far_field_static", "bm_ssm",
+                 "bm_far_field_static", "bm_ssm", "bm_server_create", "bm_server_submit", "bm_server_wait",
+                 "bm_server_stats_get", "bm_server_destroy",
                  "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_memory", "bm_destroy",
                  "bm_kernel_launches", "bm_enqueue_probe"):
         getattr(L, name).restype = C.c_int
@@ -266,6 +291,58 @@ def bm_ssm(device: int, kind: int, params, N: int, formulation: int, opts: bm_op
                         C.byref(so), pv, ldv, L, C.c_void_p(om.ctypes.data), cap,
                         sig.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info)), "bm_ssm")
     return om[:info.rank].copy(), sig, info
+
+
+def bm_server_create(device: int = 0, slots: int = 4, budget_bytes: int = 0, opts: bm_opts | None = None):
+    o = bm_server_opts()
+    o.slots = int(slots)
+    o.hbm_budget_bytes = int(budget_bytes)
+    o.opts = opts if opts is not None else make_opts()
+    s = C.c_void_p()
+    _check(lib().bm_server_create(C.byref(s), int(device), C.byref(o)), "bm_server_create")
+    return s
+
+
+def bm_server_submit(s, kind: int, params, N: int, k_out, k_in, formulation: int, B: np.ndarray, X: np.ndarray) -> int:
+    """Queue a solve; B and X are Fortran-ordered host complex128 arrays kept alive by the caller
+    until bm_server_wait returns for the ticket."""
+    pb, ldb, nb, devb, _kb = _colmajor(B, 0, writable=False)
+    px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=True)
+    if devb or devx or nb != nx:
+        raise ValueError("host B and X with the same number of columns")
+    if _kb is not B:
+        raise ValueError("B must be a Fortran-ordered complex128 array (no temporary copy)")
+    r = bm_request()
+    r.curve.kind = int(kind)
+    p = list(params) + [0.0] * (4 - len(params))
+    for i in range(4):
+        r.curve.p[i] = float(p[i])
+    r.N = int(N)
+    r.k_out = _c64(k_out)
+    r.k_in = _c64(k_in)
+    r.formulation = int(formulation)
+    r.nrhs = nb
+    r.B, r.ldb, r.X, r.ldx = pb, ldb, px, ldx
+    t = C.c_ulonglong(0)
+    _check(lib().bm_server_submit(s, C.byref(r), C.byref(t)), "bm_server_submit")
+    return int(t.value)
+
+
+def bm_server_wait(s, ticket: int) -> bm_result:
+    res = bm_result()
+    st = lib().bm_server_wait(s, C.c_ulonglong(ticket), C.byref(res))
+    _check(st, "bm_server_wait")
+    return res
+
+
+def bm_server_stats_get(s) -> bm_server_stats:
+    st = bm_server_stats()
+    _check(lib().bm_server_stats_get(s, C.byref(st)), "bm_server_stats_get")
+    return st
+
+
+def bm_server_destroy(s) -> None:
+    _check(lib().bm_server_destroy(s), "bm_server_destroy")
 
 
 def bm_copy_block(h, which: int, dst) -> None:

@@ -41,11 +41,14 @@ bm_status ctx_alloc(bm_ctx* c, void** p, size_t bytes) {
         bm_set_error("allocation of " + std::to_string(bytes) + " bytes exceeds the HBM budget");
         return BM_ENOMEM;
     }
-    cudaError_t e = cudaMalloc(p, bytes);
+    // stream-ordered allocation on the handle's stream: unlike cudaMalloc / cudaFree it never
+    // waits for the rest of the device, so handles that come and go (a serving loop, contour
+    // workers) do not stall each other's streams
+    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
-        bm_set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        bm_set_error(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
         return BM_ENOMEM;
     }
     c->allocs[*p] = bytes;
@@ -60,7 +63,7 @@ void ctx_free(bm_ctx* c, void* p) {
         c->held -= it->second;
         c->allocs.erase(it);
     }
-    cudaFree(p);
+    cudaFreeAsync(p, c->stream);
 }
 
 namespace {
@@ -217,6 +220,29 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
 
 }  // namespace
 
+// Device bytes one request needs: the assembled system and its factorisation, plus the solve
+// workspace for nrhs right-hand sides (an estimate from the same sizes ensure_ws uses, with a
+// margin for the split-K partial sums).
+size_t request_bytes(int N, int form, int prec, int nb, int nrhs) {
+    Plan p = make_plan(N, form, prec, nb, 64);
+    const size_t w = (size_t)std::max(nrhs, 8);
+    size_t b = p.bytes + 7 * (size_t)N * 8 + (size_t)p.nsys * w * 16 * 3 + (size_t)p.n * w * 16 * 2;
+    if (prec == BM_FP64) {
+        b += (size_t)p.n * w * 16;
+    } else {
+        b += (size_t)p.nsys * w * 8 + (size_t)p.n * w * 16 + (size_t)p.nsys * w * 24 + 4 * (size_t)N * w * 16;
+        if (form == BM_MIXED) b += 2 * w * (size_t)(p.ldk_schur + p.ldk_c) * 4 + ((size_t)64 << 20);
+    }
+    return b;
+}
+
+// Release the handle's system, factorisation and solve workspace (stream-ordered frees).
+void ctx_release(bm_ctx* c) {
+    cudaSetDevice(c->device);
+    free_problem(c);
+}
+
+
 // ------------------------------------------------------------------------------------------------
 extern "C" bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size_t hbm_budget_bytes) {
     if (out == nullptr) return BM_EINVAL;
@@ -275,7 +301,8 @@ extern "C" bm_status bm_destroy(bm_ctx* c) {
     FREE(c->d_normA);
     FREE(c->d_info);
     FREE(c->d_maps);
-    for (auto& kv : c->allocs) cudaFree(kv.first);
+    for (auto& kv : c->allocs) cudaFreeAsync(kv.first, c->stream);
+    if (c->stream) cudaStreamSynchronize(c->stream);  // the stream-ordered frees above complete
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return BM_OK;

@@ -288,3 +288,5 @@ struct bm_ctx {
 // allocation helpers (api.cu)
 bm_status ctx_alloc(bm_ctx* c, void** p, size_t bytes);
 void ctx_free(bm_ctx* c, void* p);
+size_t request_bytes(int N, int form, int prec, int nb, int nrhs);  // api.cu
+void ctx_release(bm_ctx* c);                                        // api.cu

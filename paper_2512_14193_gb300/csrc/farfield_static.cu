@@ -1,12 +1,12 @@
 // bm_far_field_static: the far field of bm_far_field without any device allocation.
 //
 // Who needs it: callers that must not allocate device memory while they run.  bm_far_field
-// allocates a small device buffer for the observation angles on every call and frees it
-// afterwards.  cudaFree waits until all work on the device has finished, so a serving loop that
-// keeps other streams of the same GPU busy stalls at every far-field evaluation; and the
-// allocation fails outright once factorisations have used up the handle's HBM budget.  This
-// entry point launches the same far-field kernel on the same data, but reads the angles from a
-// fixed device array compiled into the library.
+// allocates a small device buffer for the observation angles on every call (charged to the
+// handle's HBM budget) and frees it afterwards: it fails outright once resident factorisations
+// have used the budget up, and each allocation may have to grow the device's memory pool, which a
+// caller that holds a fixed device-memory footprint (a serving loop sized to the GPU) cannot
+// allow.  This entry point launches the same far-field kernel on the same data, but reads the
+// angles from a fixed device array compiled into the library.
 //
 // Scratch: g_ff_angles below, BM_FAR_FIELD_STATIC_MAX_ANGLES doubles (8192 x 8 bytes = 64 KB);
 // the linker gives each device its own copy.  A call copies its M angles into the first M
