@@ -482,9 +482,14 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* din
     cudaStream_t s = c->stream;
     const int n = c->n, bs = c->bs_solve;
     const int nblk = ceil_div(n, bs);
+    // Column tiles of 16 right-hand sides halve each CTA's work (the steps are latency-bound) as
+    // long as the widest step still fits about one wave of resident CTAs (two per SM); beyond
+    // that, 32-wide tiles (fewer, fatter CTAs) are faster.
+    const long widest16 = (long)ceil_div(std::max(n - bs, 1), TS_BM) * ceil_div(nrhs, 16);
+    const bool narrow = nrhs <= 16 || widest16 <= (long)(1.1 * 2 * std::max(c->num_sms, 1));
     auto step = [&](V Yv, V Zv, int r0, int rb, int rest0, int nrest, const typename V::cv* T) {
-        return nrhs > 16 ? launch_trsv_step<V, 32>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T)
-                         : launch_trsv_step<V, 16>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T);
+        return narrow ? launch_trsv_step<V, 16>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T)
+                      : launch_trsv_step<V, 32>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T);
     };
     for (int b = 0; b < nblk; ++b) {  // Zw = L^{-1} Y
         int r0 = b * bs, rb = std::min(bs, n - r0);

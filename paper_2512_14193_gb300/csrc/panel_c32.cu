@@ -13,20 +13,19 @@ namespace {
 //   1. every lane tracks the best row of its own column (max |Re|+|Im|, then smallest row), so
 //      lane c of each warp holds the warp's candidate; the CTA's best is two warp reductions
 //      (redux.sync max of the value bits, then min of the row index among the maxima);
-//   2. each CTA stages its candidate row (with value and index) in its own shared memory and
-//      copies it into every CTA of the cluster with one cp.async.bulk per destination, issued by
-//      lanes 0..CL-1 in parallel; the owner of row c does the same with row c.  Each receiver's
-//      mbarrier for this column completes when all bytes have landed (no cluster barrier);
+//   2. the warp owning each CTA's candidate row writes it (lane k its column k entry), with its
+//      value and index, straight from registers into every CTA of the cluster with st.async; the
+//      owner of row c does the same with row c.  Each receiver's mbarrier for this column
+//      completes when all bytes have landed (no cluster barrier, no proxy fence);
 //   3. every CTA picks the pivot from the CL candidates (the same two reductions);
 //   4. rows c and pivot are interchanged in the registers of their owners;
 //   5. lane c stages its column (the rows' column-c entries) in shared memory and every lane
 //      reads it back as broadcasts; then on the rows below c, new = alpha row + a_c beta with
 //      per-lane (alpha, beta) = (1, 0) left of c, (0, 1/u_c) at c (the multiplier) and
 //      (1, -u_k / u_c) right of c (the rank-1 update): no divergent branches.
-// Stage buffers, receive buffers and mbarriers are double-buffered by column parity.  A CTA sends
-// column c + 2 only after it received every CTA's column c + 1 data, and each CTA sends c + 1 only
-// after it has read its column c buffers (and its own column c copies have landed everywhere), so
-// no buffer is overwritten while still in use.  Waits are bounded (2 s by the global timer): on a
+// Receive buffers and mbarriers are double-buffered by column parity.  A CTA sends column c + 2
+// only after it received every CTA's column c + 1 data, and each CTA sends c + 1 only after it has
+// read its column c buffers, so no buffer is overwritten while still in use.  Waits are bounded (2 s by the global timer): on a
 // timeout the kernel raises *err and carries on without waiting, so every CTA still reaches the
 // final cluster barrier.
 // ------------------------------------------------------------------------------------------------
@@ -51,14 +50,12 @@ __device__ __forceinline__ uint32_t remote_addr(uint32_t local, int rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
     return r;
 }
-// bytes (a multiple of 16) from this CTA's shared memory into another CTA's, completing there
-__device__ __forceinline__ void bulk_push(uint32_t rdst, uint32_t lsrc, uint32_t bytes, uint32_t rbar) {
-    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     rdst),
-                 "r"(lsrc), "r"(bytes), "r"(rbar)
+// 8 bytes from registers into another CTA's shared memory, completing on that CTA's mbarrier
+__device__ __forceinline__ void push8(uint32_t raddr, uint32_t x, uint32_t y, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "r"(x), "r"(y), "r"(rbar)
                  : "memory");
 }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ uint64_t gtime() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -104,14 +101,12 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
                     SwapMap* __restrict__ map_big, int* __restrict__ perm) {
     constexpr int WARPS = PANEL_THREADS / 32;
     constexpr int R = WARPS * RPW;
-    constexpr int CAND = 34;  // candidate record: 32 entries, then (value bits, row index), 8 pad bytes
+    constexpr int CAND = 33;  // candidate record: 32 entries, then (value bits, row index)
     cg::cluster_group cluster = cg::this_cluster();
     const int cta = (int)cluster.block_rank();
     const int CL = (int)cluster.num_blocks();
     __shared__ alignas(16) float2 cand_buf[2][MAX_CLUSTER][CAND];  // received candidates
     __shared__ alignas(16) float2 diag_buf[2][32];                  // received row c
-    __shared__ alignas(16) float2 cand_stage[2][CAND];              // this CTA's candidate, to send
-    __shared__ alignas(16) float2 diag_stage[2][32];                // row c, to send (its owner)
     __shared__ alignas(16) float2 colbuf[WARPS][RPW];               // column c of each warp's rows
     __shared__ alignas(8) uint64_t bars[2];
     __shared__ uint2 red[2][WARPS];
@@ -168,21 +163,18 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         // ---- (2) send the candidate row (its owner warp, else warp 0 sends zeros) and row c ----
         const bool has = ci != INT_MAX;
         if (warp == (has ? (ci - rb) / RPW : 0)) {
-            cand_stage[par][lane] = has ? row_get<RPW>(row, ci - wb) : zero;
-            if (lane == 0) reinterpret_cast<uint4*>(&cand_stage[par][32])[0] = make_uint4(cvb, ciu, 0u, 0u);
-            fence_async_smem();
-            __syncwarp();
+            const float2 v = has ? row_get<RPW>(row, ci - wb) : zero;
+            const uint32_t la = smem_addr(&cand_buf[par][cta][lane]);
+            for (int d = 0; d < CL; ++d)
+                push8(remote_addr(la, d), __float_as_uint(v.x), __float_as_uint(v.y), remote_addr(bar, d));
             if (lane < CL)
-                bulk_push(remote_addr(smem_addr(&cand_buf[par][cta][0]), lane), smem_addr(&cand_stage[par][0]),
-                          CAND * 8, remote_addr(bar, lane));
+                push8(remote_addr(smem_addr(&cand_buf[par][cta][32]), lane), cvb, ciu, remote_addr(bar, lane));
         }
         if (c >= wb && c < wb + RPW) {
-            diag_stage[par][lane] = row_get<RPW>(row, c - wb);
-            fence_async_smem();
-            __syncwarp();
-            if (lane < CL)
-                bulk_push(remote_addr(smem_addr(&diag_buf[par][0]), lane), smem_addr(&diag_stage[par][0]), 32 * 8,
-                          remote_addr(bar, lane));
+            const float2 v = row_get<RPW>(row, c - wb);
+            const uint32_t la = smem_addr(&diag_buf[par][lane]);
+            for (int d = 0; d < CL; ++d)
+                push8(remote_addr(la, d), __float_as_uint(v.x), __float_as_uint(v.y), remote_addr(bar, d));
         }
         // ---- (3) wait for this column's data, pick the pivot ----
         if (!timed_out && !bar_wait(bar, (uint32_t)(c >> 1) & 1u)) {
