@@ -49,3 +49,42 @@ def test_create_without_gpu_reports_cuda_error(bmlib):
     h = ctypes.c_void_p()
     st = bmlib.lib().bm_create(ctypes.byref(h), 0, None, 0)
     assert st == bmlib.BM_ECUDA
+
+
+def test_contour_and_server_argument_checks_need_no_gpu(bmlib):
+    # bm_ssm and bm_server_create check their arguments before touching the device
+    import ctypes
+    import numpy as np
+    cv = bmlib.bm_curve()
+    cv.kind = bmlib.BM_CURVE_CIRCLE
+    cv.p[0] = 1.0
+    so = bmlib.bm_ssm_opts()
+    so.center = bmlib.bm_c64(5.0, 0.0)
+    so.radius = 0.5
+    so.npoints = 32
+    so.nmoments = 4
+    so.k_ratio = bmlib.bm_c64(1.5, 0.0)
+    N, L = 64, 4
+    V = np.zeros((3 * N, L), dtype=np.complex128, order="F")
+    om = np.zeros(L * 4, dtype=np.complex128)
+    info = bmlib.bm_ssm_info()
+
+    def call(so_, L_=L, cap=L * 4, ldv=3 * N):
+        return bmlib.lib().bm_ssm(0, ctypes.byref(cv), N, bmlib.BM_MIXED, None, ctypes.byref(so_),
+                                  ctypes.c_void_p(V.ctypes.data), ldv, L_, ctypes.c_void_p(om.ctypes.data), cap,
+                                  None, ctypes.byref(info))
+
+    for field, bad in (("radius", 0.0), ("npoints", 2), ("nmoments", 0), ("nmoments", 17), ("workers", 17),
+                       ("rank_tol", 1.5)):
+        s2 = bmlib.bm_ssm_opts.from_buffer_copy(so)
+        setattr(s2, field, bad)
+        assert call(s2) == bmlib.BM_EINVAL, field
+    assert call(so, cap=L * 4 - 1) == bmlib.BM_EINVAL          # output too small for L M eigenvalues
+    assert call(so, ldv=3 * N - 1) == bmlib.BM_EINVAL          # leading dimension below the system size
+    assert call(so, L_=65) == bmlib.BM_EINVAL                  # L M above 256
+    o = bmlib.bm_server_opts()
+    o.slots = 0
+    srv = ctypes.c_void_p()
+    assert bmlib.lib().bm_server_create(ctypes.byref(srv), 0, ctypes.byref(o)) == bmlib.BM_EINVAL
+    o.slots = 33
+    assert bmlib.lib().bm_server_create(ctypes.byref(srv), 0, ctypes.byref(o)) == bmlib.BM_EINVAL
