@@ -12,9 +12,11 @@
 //
 // CTA tile 128 x 128, K step 32 (128-byte rows), 3-stage TMA -> shared-memory pipeline with
 // mbarriers.  Warp 0 lane 0 issues TMA loads, warp 1 lane 0 issues tcgen05.mma; all four warps
-// then read the accumulators (tcgen05.ld 32x32b, warp w owns TMEM lanes 32w..32w+31 = rows)
-// and update C with coalesced column-major stores.  Every mbarrier wait is bounded (2 s by the
-// global timer); a timeout sets *err, skips the epilogue, waits for issued copies and frees TMEM.
+// then read the accumulators (tcgen05.ld 32x32b, warp w owns TMEM lanes 32(w mod 4) .. +31 = rows)
+// and update C with coalesced column-major stores.  For C = C + alpha A B^T (the LU trailing
+// updates) a six-warp form loads the C tile into the upper half of TMEM during the main loop, so
+// the epilogue only stores.  Every mbarrier wait is bounded (2 s by the global timer); a timeout
+// sets *err, skips the epilogue, waits for issued copies and frees TMEM.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -30,7 +32,7 @@ constexpr int TILE_A = BM * BKE * 4;
 constexpr int TILE_B = BN * BKE * 4;
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t TMEM_COLS = 2 * BN;
+constexpr uint32_t TMEM_COLS = 2 * BN;  // Dr, Di
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -148,11 +150,32 @@ __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t neg_a) {
 }
 
 // Output modes: OUT_C32 C (FP32 planar) = beta C + alpha D; OUT_Z64 C64 (FP64) = beta C64 + alpha D;
-// OUT_PART the raw D of this K split to a workspace slice (split-K partial sums).
-enum { OUT_C32 = 0, OUT_Z64 = 1, OUT_PART = 2 };
+// OUT_PART the raw D of this K split to a workspace slice (split-K partial sums); OUT_C32_PRE as
+// OUT_C32 for beta != 0, with six warps: warps 2-5 copy the C tile into TMEM columns 2BN..4BN while
+// the MMAs run, so the epilogue reads D and C from TMEM and only stores (the C loads no longer
+// follow the main loop; one CTA per SM leaves nothing else to overlap them with).
+enum { OUT_C32 = 0, OUT_Z64 = 1, OUT_PART = 2, OUT_C32_PRE = 3 };
 
 template <int OUT>
-__global__ void __launch_bounds__(128, 1)
+__host__ __device__ constexpr int tc_threads() { return OUT == OUT_C32_PRE ? 192 : 128; }
+template <int OUT>
+__host__ __device__ constexpr uint32_t tc_tmem_cols() { return OUT == OUT_C32_PRE ? 2 * TMEM_COLS : TMEM_COLS; }
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+            taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+template <int OUT>
+__global__ void __launch_bounds__(192, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmAr, const __grid_constant__ CUtensorMap tmAi,
                     const __grid_constant__ CUtensorMap tmBr, const __grid_constant__ CUtensorMap tmBi,
                     float* __restrict__ Cr, float* __restrict__ Ci, double2* __restrict__ C64, long ldc, long zstride,
@@ -179,7 +202,7 @@ __global__ void __launch_bounds__(128, 1)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), tc_tmem_cols<OUT>());
     fence_before();
     __syncthreads();
     fence_after();
@@ -237,20 +260,56 @@ __global__ void __launch_bounds__(128, 1)
         mma_commit(done);
     }
     __syncwarp();
-    // ---------------- epilogue: all four warps ----------------
+    if (OUT == OUT_C32_PRE && warp >= 2) {
+        // ---------------- C tile -> TMEM while the MMAs run (warps 2-5) ----------------
+        const int qw = warp & 3;  // TMEM lane quarter this warp may access
+        const long row = (long)tm * BM + qw * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(qw * 32) << 16;
+        const long col0 = (long)tn * BN;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float cr[16], ci[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const long col = col0 + c0 + q;
+                const bool in = row < m && col < n;
+                cr[q] = in ? __ldg(Cr + row + col * ldc) : 0.f;
+                ci[q] = in ? __ldg(Ci + row + col * ldc) : 0.f;
+            }
+            tmem_st16(Dr + 2 * BN + lane_off + c0, cr);
+            tmem_st16(Di + 2 * BN + lane_off + c0, ci);
+        }
+        tmem_wait_st();
+    }
+    // ---------------- epilogue: all four warps (warps 2-5 in OUT_C32_PRE) ----------------
     mbar_wait(done, 0, abort_flag);
     fence_before();
     __syncthreads();  // the abort decision below must be uniform: tcgen05.ld is warp-synchronous
     fence_after();
-    if (!*abort_flag) {
-        const long row = (long)tm * BM + warp * 32 + lane;
-        const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    if (!*abort_flag && (OUT != OUT_C32_PRE || warp >= 2)) {
+        const int qw = (OUT == OUT_C32_PRE) ? (warp & 3) : warp;
+        const long row = (long)tm * BM + qw * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(qw * 32) << 16;
         const long col0 = (long)tn * BN;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float vr[16], vi[16];
             tmem_ld16x2(Dr + lane_off + c0, Di + lane_off + c0, vr, vi);
-            if (OUT == OUT_PART && row < m) {
+            if (OUT == OUT_C32_PRE) {
+                float cr[16], ci[16];
+                tmem_ld16x2(Dr + 2 * BN + lane_off + c0, Di + 2 * BN + lane_off + c0, cr, ci);
+                if (row < m) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const long col = col0 + c0 + q;
+                        if (col < n) {
+                            const long o = row + col * ldc;
+                            Cr[o] = fmaf(beta, cr[q], alpha * vr[q]);
+                            Ci[o] = fmaf(beta, ci[q], alpha * vi[q]);
+                        }
+                    }
+                }
+            } else if (OUT == OUT_PART && row < m) {
                 // slice z of the workspace: m x n column-major, leading dimension ldc (= m)
                 float* Pr = Cr + (long)blockIdx.z * zstride;
                 float* Pi = Ci + (long)blockIdx.z * zstride;
@@ -316,7 +375,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (warp == 0) {
         fence_after();
-        tmem_dealloc(tmem, TMEM_COLS);
+        tmem_dealloc(tmem, tc_tmem_cols<OUT>());
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
 }
@@ -375,7 +434,7 @@ cudaError_t launch_tc(cudaStream_t s, dim3 grid, const void* tAr, const void* tA
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    cgemm_tc_kernel<OUT><<<grid, 128, SMEM_BYTES, s>>>(
+    cgemm_tc_kernel<OUT><<<grid, tc_threads<OUT>(), SMEM_BYTES, s>>>(
         *reinterpret_cast<const CUtensorMap*>(tAr), *reinterpret_cast<const CUtensorMap*>(tAi),
         *reinterpret_cast<const CUtensorMap*>(tBr), *reinterpret_cast<const CUtensorMap*>(tBi), Cr, Ci, C64, ldc,
         zstride, m, n, kext, S, alpha, beta, d_err);
@@ -459,6 +518,9 @@ cudaError_t gemm_tc(cudaStream_t s, const void* tAr, const void* tAi, const void
                     float* Ci, long ldc, int m, int n, int kext, float alpha, float beta, int* d_err) {
     if (m <= 0 || n <= 0 || kext <= 0) return cudaSuccess;
     dim3 grid(ceil_div(m, BM), ceil_div(n, BN), 1);
+    if (beta != 0.f)
+        return launch_tc<OUT_C32_PRE>(s, grid, tAr, tAi, tBr, tBi, Cr, Ci, nullptr, ldc, 0, m, n, kext, 1, alpha,
+                                      beta, d_err);
     return launch_tc<OUT_C32>(s, grid, tAr, tAi, tBr, tBi, Cr, Ci, nullptr, ldc, 0, m, n, kext, 1, alpha, beta,
                               d_err);
 }
