@@ -37,9 +37,11 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 // Row interchanges (from a swap map) for columns in [a0, a1) u [b0, b1); for columns of the
 // second range also X = L11^{-1} X on rows [t0, t0+tb) with the unit-lower L11 at (t0, t0),
-// staged in shared memory when it fits.  Optionally writes the solved rows as a K-major
-// tensor-core pack (column c -> row c - b0).  One warp per column, COLS columns per warp.
+// staged in shared memory: whole when it fits, else in chunks of ST_KC columns that the CTA's
+// warps step through together.  Optionally writes the solved rows as a K-major tensor-core pack
+// (column c -> row c - b0).  One warp per column.
 constexpr int ST_WARPS = 16, ST_COLS = 1;
+constexpr int ST_KC = 32;  // L11 columns per shared-memory chunk when L11 does not fit whole
 template <class V>
 __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const SwapMap* __restrict__ map, int a0, int a1,
                                                                    int b0, int b1, int t0, int tb, float* Upr,
@@ -54,61 +56,83 @@ __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const Swa
     const int ncols = na + nbc;
     const int cta_col0 = blockIdx.x * ST_WARPS * ST_COLS;
     const bool cta_has_b = (cta_col0 + ST_WARPS * ST_COLS > na) && tb > 0;
-    if (cta_has_b && l_in_smem) {
+    if (cta_has_b && l_in_smem == 1) {
         for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) {
             int i = e % tb, k = e / tb;
             Ls[e] = (i > k) ? A.get((long)t0 + i, (long)t0 + k) : czero<Rl>();
         }
         __syncthreads();
     }
+    static_assert(ST_COLS == 1, "one column per warp");
     const int cnt = map ? map->count : 0;
-    for (int cc = 0; cc < ST_COLS; ++cc) {
-        const int gw = cta_col0 + warp * ST_COLS + cc;
-        if (gw >= ncols) break;
-        const bool in_b = gw >= na;
-        const long col = in_b ? (long)b0 + (gw - na) : (long)a0 + gw;
-        if (cnt > 0) {
-            CV v[MAP_MAX / 32];
+    const int gw = cta_col0 + warp;
+    const bool valid = gw < ncols;
+    const bool in_b = valid && gw >= na;
+    const long col = in_b ? (long)b0 + (gw - na) : (long)a0 + gw;
+    if (valid && cnt > 0) {
+        CV v[MAP_MAX / 32];
 #pragma unroll
-            for (int q = 0; q < MAP_MAX / 32; ++q) {
-                int t = lane + 32 * q;
-                if (t < cnt) v[q] = A.get(map->src[t], col);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int q = 0; q < MAP_MAX / 32; ++q) {
-                int t = lane + 32 * q;
-                if (t < cnt) A.set(map->dst[t], col, v[q]);
-            }
-            __syncwarp();
+        for (int q = 0; q < MAP_MAX / 32; ++q) {
+            int t = lane + 32 * q;
+            if (t < cnt) v[q] = A.get(map->src[t], col);
         }
-        if (!in_b || tb <= 0) continue;
-        CV x[QMAX];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < MAP_MAX / 32; ++q) {
+            int t = lane + 32 * q;
+            if (t < cnt) A.set(map->dst[t], col, v[q]);
+        }
+        __syncwarp();
+    }
+    const bool do_trsm = in_b && tb > 0;
+    CV x[QMAX];
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+        int i = lane + 32 * q;
+        x[q] = (do_trsm && i < tb) ? A.get((long)t0 + i, col) : czero<Rl>();
+    }
+    // x -= L11 columns k < tb, one k at a time; lk(i, k) reads L(t0 + i, t0 + k) from wherever it
+    // is staged
+    auto step = [&](int k, auto lk) {
+        const int qk = k >> 5, lkn = k & 31;
+        CV xk = czero<Rl>();
+#pragma unroll
+        for (int q = 0; q < QMAX; ++q)
+            if (q == qk) xk = x[q];
+        xk.x = __shfl_sync(0xffffffffu, xk.x, lkn);
+        xk.y = __shfl_sync(0xffffffffu, xk.y, lkn);
+        CV nx;
+        nx.x = -xk.x;
+        nx.y = -xk.y;
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
             int i = lane + 32 * q;
-            x[q] = (i < tb) ? A.get((long)t0 + i, col) : czero<Rl>();
+            if (q >= qk && i > k && i < tb) cfma(x[q], lk(i, k), nx);
         }
-        for (int k = 0; k < tb; ++k) {
-            const int qk = k >> 5, lk = k & 31;
-            CV xk = czero<Rl>();
-#pragma unroll
-            for (int q = 0; q < QMAX; ++q)
-                if (q == qk) xk = x[q];
-            xk.x = __shfl_sync(0xffffffffu, xk.x, lk);
-            xk.y = __shfl_sync(0xffffffffu, xk.y, lk);
-            CV nx;
-            nx.x = -xk.x;
-            nx.y = -xk.y;
-#pragma unroll
-            for (int q = 0; q < QMAX; ++q) {
-                int i = lane + 32 * q;
-                if (q >= qk && i > k && i < tb) {
-                    CV l = l_in_smem ? Ls[i + k * tb] : A.get((long)t0 + i, (long)t0 + k);
-                    cfma(x[q], l, nx);
+    };
+    if (l_in_smem == 2) {
+        // L11 larger than the shared-memory budget: stage it ST_KC columns at a time, the whole
+        // CTA stepping through the chunks together (warps without a column to solve only help)
+        if (cta_has_b) {
+            for (int k0 = 0; k0 < tb; k0 += ST_KC) {
+                const int kc = min(ST_KC, tb - k0);
+                __syncthreads();
+                for (int e = threadIdx.x; e < tb * kc; e += blockDim.x) {
+                    const int i = e % tb, kk = e / tb;
+                    Ls[e] = (i > k0 + kk) ? A.get((long)t0 + i, (long)t0 + k0 + kk) : czero<Rl>();
                 }
+                __syncthreads();
+                if (do_trsm)
+                    for (int k = k0; k < k0 + kc; ++k) step(k, [&](int i, int kk) { return Ls[i + (kk - k0) * tb]; });
             }
         }
+    } else if (do_trsm) {
+        for (int k = 0; k < tb; ++k)
+            step(k, [&](int i, int kk) {
+                return l_in_smem ? Ls[i + kk * tb] : A.get((long)t0 + i, (long)t0 + kk);
+            });
+    }
+    if (do_trsm) {
 #pragma unroll
         for (int q = 0; q < QMAX; ++q) {
             int i = lane + 32 * q;
@@ -383,9 +407,10 @@ cudaError_t launch_swap_trsm(cudaStream_t s, V A, const SwapMap* map, int a0, in
     using CV = typename V::cv;
     long ncols = (long)(a1 - a0) + (b1 - b0);
     if (ncols <= 0) return cudaSuccess;
+    // L11 staging: whole (1) when it fits 160 KB, else in ST_KC-column chunks (2)
     size_t lbytes = (size_t)tb * tb * sizeof(CV);
-    int l_in_smem = (tb > 0 && lbytes <= 160 * 1024) ? 1 : 0;
-    size_t smem = l_in_smem ? lbytes : 0;
+    int l_in_smem = tb <= 0 ? 0 : (lbytes <= 160 * 1024 ? 1 : 2);
+    size_t smem = l_in_smem == 1 ? lbytes : (l_in_smem == 2 ? (size_t)tb * ST_KC * sizeof(CV) : 0);
     auto kern = swap_trsm_kernel<V>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
