@@ -2,7 +2,7 @@
 // Theorem thm:LU, or the 2N x 2N ordinary matrix of Eq. dis_BM), and the triangular solves.
 //
 // Right-looking blocked LU with two block sizes:
-//   for each big panel of NB columns (C32: 128, Z64: 64):
+//   for each big panel of NB columns (C32: 256, Z64: 64):
 //     for each sub-panel of nbp columns (nbp = 32/16/8 for C32, 16/8/4 for Z64 - wider when the
 //     rows below the diagonal are fewer):
 //        panel_kernel      : unblocked LU with partial pivoting of rows [j, n) x nbp columns.
@@ -22,7 +22,12 @@
 //
 // Solves (getrs): Y = P B, then block forward substitution with the unit L and block back
 // substitution with U; the bs x bs diagonal blocks are inverted once after the factorisation so
-// that every step is a small matrix product.
+// that every step is a small matrix product.  For C32 the off-diagonal bs x bs tiles of each
+// block column are then multiplied by that column's inverted diagonal block (the "G form"), so
+// that a step is one product with no dependence on the inverse:
+//   forward:  Y[below b] -= (L[below b, b] L_bb^{-1}) Y_b,  then Z_b = L_bb^{-1} Y_b for all b at once
+//   backward: Z[above b] -= (U[above b, b] U_bb^{-1}) Z_b,  then X_b = U_bb^{-1} Z_b for all b at once
+// (the same sums as L_bb^{-1} Y_b formed inside every step, without recomputing it in each CTA).
 #include "lu_internal.cuh"
 
 using namespace lu_detail;
@@ -218,9 +223,12 @@ __global__ void iota_kernel(int* p, int n) {
     if (i < n) p[i] = i;
 }
 
-// Inverse of each bs x bs diagonal block (unit lower L or upper U) of the LU factor.
+// Inverse of each bs x bs diagonal block (unit lower L or upper U) of the LU factor, by a
+// column sweep over X = I: for k in order (L: 0..rb-1; U: rb-1..0, row k first divided by U_kk),
+// every later row i takes X_i -= T_ik X_k, with all (i, column) pairs of a step in parallel.
+// Entries outside the rb x rb leading block are zero.
 template <class V, bool UPPER>
-__global__ void tri_inv_kernel(V F, int n, int bs, typename V::cv* __restrict__ out) {
+__global__ void __launch_bounds__(256) tri_inv_kernel(V F, int n, int bs, typename V::cv* __restrict__ out) {
     using CV = typename V::cv;
     using Rl = typename V::real;
     extern __shared__ __align__(16) unsigned char sm[];
@@ -229,48 +237,34 @@ __global__ void tri_inv_kernel(V F, int n, int bs, typename V::cv* __restrict__ 
     const int b = blockIdx.x;
     const int r0 = b * bs;
     const int rb = min(bs, n - r0);
-    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
-        int i = e % bs, j = e / bs;
+    const int nt = blockDim.x;
+    for (int e = threadIdx.x; e < bs * bs; e += nt) {
+        const int i = e % bs, j = e / bs;
         T[e] = (i < rb && j < rb) ? F.get((long)r0 + i, (long)r0 + j) : czero<Rl>();
+        CV one = czero<Rl>();
+        if (i == j && i < rb) one.x = (Rl)1;
+        X[e] = one;
     }
     __syncthreads();
-    const int c = threadIdx.x;  // one column of the inverse per thread
-    if (c >= rb)
-        for (int i = 0; i < bs; ++i) X[i + c * bs] = czero<Rl>();
-    if (c < rb) {
-        if (!UPPER) {
-            for (int i = 0; i < rb; ++i) {
-                CV s = czero<Rl>();
-                if (i == c) s.x = (Rl)1;
-                if (i > c) {
-                    for (int k = c; k < i; ++k) {
-                        CV nl = T[i + k * bs];
-                        nl.x = -nl.x;
-                        nl.y = -nl.y;
-                        cfma(s, nl, X[k + c * bs]);
-                    }
-                }
-                X[i + c * bs] = (i < c) ? czero<Rl>() : s;
-            }
-        } else {
-            for (int i = rb - 1; i >= 0; --i) {
-                CV s = czero<Rl>();
-                if (i <= c) {
-                    if (i == c) s.x = (Rl)1;
-                    for (int k = i + 1; k <= c; ++k) {
-                        CV nu = T[i + k * bs];
-                        nu.x = -nu.x;
-                        nu.y = -nu.y;
-                        cfma(s, nu, X[k + c * bs]);
-                    }
-                    s = cmul(s, cinv(T[i + i * bs]));
-                }
-                X[i + c * bs] = s;
+    for (int s = 0; s < rb; ++s) {
+        const int k = UPPER ? rb - 1 - s : s;
+        if (UPPER) {
+            const CV d = cinv(T[k + k * bs]);
+            for (int c = threadIdx.x; c < rb; c += nt) X[k + c * bs] = cmul(X[k + c * bs], d);
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < bs * bs; e += nt) {
+            const int i = e % bs, c = e / bs;
+            if (c < rb && (UPPER ? i < k : (i > k && i < rb))) {
+                CV t = T[i + k * bs];
+                t.x = -t.x;
+                t.y = -t.y;
+                cfma(X[e], t, X[k + c * bs]);
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) out[(long)b * bs * bs + e] = X[e];
+    for (int e = threadIdx.x; e < bs * bs; e += nt) out[(long)b * bs * bs + e] = X[e];
 }
 
 // One block step of a blocked triangular solve with inverted diagonal blocks (one launch per
@@ -368,6 +362,173 @@ __global__ void __launch_bounds__(256) trsv_step_kernel(V F, V Y, V Z, int r0, i
             y.x -= acc[a][b].x;
             y.y -= acc[a][b].y;
             Y.set(tr0 + i, (long)j0 + jj, y);
+        }
+    }
+}
+
+// G form of the factors (C32): every off-diagonal bs x bs tile F[it, b] (it != b) becomes
+// F[it, b] T_b with T_b = L_bb^{-1} below the diagonal and U_bb^{-1} above it.  One CTA per tile,
+// in place (each CTA reads its whole tile before writing it).  bs == TS_BM == 64.
+template <class V>
+__global__ void __launch_bounds__(256) g_form_kernel(V F, int n, const typename V::cv* __restrict__ dinvL,
+                                                     const typename V::cv* __restrict__ dinvU) {
+    using CV = typename V::cv;
+    using Rl = typename V::real;
+    constexpr int B = TS_BM;
+    const int it = blockIdx.x, b = blockIdx.y;
+    if (it == b) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    CV* Ft = reinterpret_cast<CV*>(sm);  // [B][B] column-major tile of F
+    CV* Ts = Ft + B * B;                 // [B][B] column-major T_b
+    const int t = threadIdx.x;
+    const long r0 = (long)it * B, c0 = (long)b * B;
+    const int tm = (int)min((long)B, n - r0), rb = (int)min((long)B, n - c0);
+    const CV* T = (it > b ? dinvL : dinvU) + (long)b * B * B;
+    for (int e = t; e < B * B; e += 256) {
+        const int i = e % B, k = e / B;
+        Ft[e] = (i < tm && k < rb) ? F.get(r0 + i, c0 + k) : czero<Rl>();
+        Ts[e] = (i < rb && k < rb) ? T[e] : czero<Rl>();
+    }
+    __syncthreads();
+    const int tx = t % 16, ty = t / 16;  // rows tx + 16 a, columns ty + 16 c
+    CV acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = czero<Rl>();
+    for (int k = 0; k < rb; ++k) {
+        CV fv[4], tv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fv[a] = Ft[k * B + tx + 16 * a];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tv[c] = Ts[k + (ty + 16 * c) * B];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cfma(acc[a][c], fv[a], tv[c]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = tx + 16 * a;
+        if (i >= tm) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = ty + 16 * c;
+            if (j < rb) F.set(r0 + i, c0 + j, acc[a][c]);
+        }
+    }
+}
+
+// One step of a blocked triangular solve in G form (all right-hand sides):
+//   Y[rest0:rest0+nrest, :] -= G[rest0.., r0:r0+rb] Y[r0:r0+rb, :]
+// (each CTA one 64-row tile of the rest and BN columns; the rows it reads and writes are disjoint).
+template <class V, int BN>
+__global__ void __launch_bounds__(256) trsv_g_step_kernel(V F, V Y, int r0, int rb, int rest0, int nrest, int nrhs) {
+    using CV = typename V::cv;
+    using Rl = typename V::real;
+    constexpr int B = TS_BM;
+    extern __shared__ __align__(16) unsigned char sm[];
+    CV* Yb = reinterpret_cast<CV*>(sm);  // [BN][B]
+    CV* Ft = Yb + BN * B;                // [B][B] column-major tile of G
+    const int t = threadIdx.x;
+    const int j0 = blockIdx.y * BN;
+    const int nc = min(BN, nrhs - j0);
+    const long tr0 = (long)rest0 + (long)blockIdx.x * B;
+    const int tm = (int)min((long)B, (long)rest0 + nrest - tr0);
+    for (int e = t; e < B * BN; e += 256) {
+        const int i = e % B, jj = e / B;
+        Yb[e] = (i < rb && jj < nc) ? Y.get((long)r0 + i, (long)j0 + jj) : czero<Rl>();
+    }
+    for (int e = t; e < B * B; e += 256) {
+        const int i = e % B, k = e / B;
+        Ft[e] = (i < tm && k < rb) ? F.get(tr0 + i, (long)r0 + k) : czero<Rl>();
+    }
+    __syncthreads();
+    constexpr int TN = BN / 16;
+    const int tx = t % 16, ty = t / 16;
+    CV acc[4][TN];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[a][c] = czero<Rl>();
+    for (int k = 0; k < rb; ++k) {
+        CV fv[4], yv[TN];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) fv[a] = Ft[k * B + tx + 16 * a];
+#pragma unroll
+        for (int c = 0; c < TN; ++c) yv[c] = Yb[(ty + 16 * c) * B + k];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) cfma(acc[a][c], fv[a], yv[c]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = tx + 16 * a;
+        if (i >= tm) continue;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int jj = ty + 16 * c;
+            if (jj >= nc) continue;
+            CV y = Y.get(tr0 + i, (long)j0 + jj);
+            y.x -= acc[a][c].x;
+            y.y -= acc[a][c].y;
+            Y.set(tr0 + i, (long)j0 + jj, y);
+        }
+    }
+}
+
+// Z_b = T_b Y_b for every diagonal block b at once (grid: blocks x column tiles of BN).
+template <class V, int BN>
+__global__ void __launch_bounds__(256) trsv_diag_kernel(V Y, V Z, int n, int nrhs,
+                                                        const typename V::cv* __restrict__ Tinv) {
+    using CV = typename V::cv;
+    using Rl = typename V::real;
+    constexpr int B = TS_BM;
+    extern __shared__ __align__(16) unsigned char sm[];
+    CV* Ts = reinterpret_cast<CV*>(sm);  // [B][B] column-major
+    CV* Yb = Ts + B * B;                 // [BN][B]
+    const int t = threadIdx.x;
+    const long r0 = (long)blockIdx.x * B;
+    const int rb = (int)min((long)B, n - r0);
+    const int j0 = blockIdx.y * BN;
+    const int nc = min(BN, nrhs - j0);
+    const CV* T = Tinv + (long)blockIdx.x * B * B;
+    for (int e = t; e < B * B; e += 256) {
+        const int i = e % B, k = e / B;
+        Ts[e] = (i < rb && k < rb) ? T[e] : czero<Rl>();
+    }
+    for (int e = t; e < B * BN; e += 256) {
+        const int i = e % B, jj = e / B;
+        Yb[e] = (i < rb && jj < nc) ? Y.get(r0 + i, (long)j0 + jj) : czero<Rl>();
+    }
+    __syncthreads();
+    constexpr int TN = BN / 16;
+    const int tx = t % 16, ty = t / 16;
+    CV acc[4][TN];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[a][c] = czero<Rl>();
+    for (int k = 0; k < rb; ++k) {
+        CV tv[4], yv[TN];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) tv[a] = Ts[tx + 16 * a + k * B];
+#pragma unroll
+        for (int c = 0; c < TN; ++c) yv[c] = Yb[(ty + 16 * c) * B + k];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) cfma(acc[a][c], tv[a], yv[c]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = tx + 16 * a;
+        if (i >= rb) continue;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int jj = ty + 16 * c;
+            if (jj < nc) Z.set(r0 + i, (long)j0 + jj, acc[a][c]);
         }
     }
 }
@@ -483,9 +644,22 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
     using CV = typename V::cv;
     LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tri_inv_kernel<V, false><<<nblk, bs, smem, s>>>(F, n, bs, reinterpret_cast<CV*>(c->d_dinvL));
-    tri_inv_kernel<V, true><<<nblk, bs, smem, s>>>(F, n, bs, reinterpret_cast<CV*>(c->d_dinvU));
+    tri_inv_kernel<V, false><<<nblk, 256, smem, s>>>(F, n, bs, reinterpret_cast<CV*>(c->d_dinvL));
+    tri_inv_kernel<V, true><<<nblk, 256, smem, s>>>(F, n, bs, reinterpret_cast<CV*>(c->d_dinvU));
     LU_CUDA(cudaGetLastError());
+    if constexpr (std::is_same<V, C32>::value) {
+        if (bs != TS_BM) {
+            bm_set_error("lu: the solve block size must be 64");
+            return BM_EINVAL;
+        }
+        if (nblk > 1) {
+            const size_t gsm = 2 * (size_t)TS_BM * TS_BM * sizeof(CV);
+            LU_CUDA(cudaFuncSetAttribute(g_form_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+            g_form_kernel<V><<<dim3(nblk, nblk), 256, gsm, s>>>(F, n, reinterpret_cast<const CV*>(c->d_dinvL),
+                                                                reinterpret_cast<const CV*>(c->d_dinvU));
+            LU_CUDA(cudaGetLastError());
+        }
+    }
     return BM_OK;
 }
 
@@ -501,6 +675,28 @@ cudaError_t launch_trsv_step(cudaStream_t s, V F, V Y, V Z, int r0, int rb, int 
     return cudaGetLastError();
 }
 
+template <class V, int BN>
+cudaError_t launch_trsv_g_step(cudaStream_t s, V F, V Y, int r0, int rb, int rest0, int nrest, int nrhs) {
+    size_t smem = ((size_t)BN * TS_BM + (size_t)TS_BM * TS_BM) * sizeof(typename V::cv);
+    auto kern = trsv_g_step_kernel<V, BN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(nrest, TS_BM), ceil_div(nrhs, BN));
+    kern<<<grid, 256, smem, s>>>(F, Y, r0, rb, rest0, nrest, nrhs);
+    return cudaGetLastError();
+}
+
+template <class V, int BN>
+cudaError_t launch_trsv_diag(cudaStream_t s, V Y, V Z, int n, int nrhs, const typename V::cv* Tinv) {
+    size_t smem = ((size_t)TS_BM * TS_BM + (size_t)BN * TS_BM) * sizeof(typename V::cv);
+    auto kern = trsv_diag_kernel<V, BN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(n, TS_BM), ceil_div(nrhs, BN));
+    kern<<<grid, 256, smem, s>>>(Y, Z, n, nrhs, Tinv);
+    return cudaGetLastError();
+}
+
 // Solve L U X = Y in place (Y holds P B); Zw is an n x nrhs work buffer.
 template <class V>
 bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* dinvL, const typename V::cv* dinvU) {
@@ -512,17 +708,38 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* din
     // that, 32-wide tiles (fewer, fatter CTAs) are faster.
     const long widest16 = (long)ceil_div(std::max(n - bs, 1), TS_BM) * ceil_div(nrhs, 16);
     const bool narrow = nrhs <= 16 || widest16 <= (long)(1.1 * 2 * std::max(c->num_sms, 1));
-    auto step = [&](V Yv, V Zv, int r0, int rb, int rest0, int nrest, const typename V::cv* T) {
-        return narrow ? launch_trsv_step<V, 16>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T)
-                      : launch_trsv_step<V, 32>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T);
-    };
-    for (int b = 0; b < nblk; ++b) {  // Zw = L^{-1} Y
-        int r0 = b * bs, rb = std::min(bs, n - r0);
-        LU_CUDA(step(Y, Zw, r0, rb, r0 + rb, n - r0 - rb, dinvL + (long)b * bs * bs));
-    }
-    for (int b = nblk - 1; b >= 0; --b) {  // Y = U^{-1} Zw
-        int r0 = b * bs, rb = std::min(bs, n - r0);
-        LU_CUDA(step(Zw, Y, r0, rb, 0, r0, dinvU + (long)b * bs * bs));
+    if constexpr (std::is_same<V, C32>::value) {  // factors in G form
+        auto gstep = [&](V Yv, int r0, int rb, int rest0, int nrest) {
+            return narrow ? launch_trsv_g_step<V, 16>(s, F, Yv, r0, rb, rest0, nrest, nrhs)
+                          : launch_trsv_g_step<V, 32>(s, F, Yv, r0, rb, rest0, nrest, nrhs);
+        };
+        auto diag = [&](V Yv, V Zv, const typename V::cv* T) {
+            return narrow ? launch_trsv_diag<V, 16>(s, Yv, Zv, n, nrhs, T)
+                          : launch_trsv_diag<V, 32>(s, Yv, Zv, n, nrhs, T);
+        };
+        for (int b = 0; b + 1 < nblk; ++b) {  // Y[below b] -= G_L Y_b
+            int r0 = b * bs, rb = std::min(bs, n - r0);
+            LU_CUDA(gstep(Y, r0, rb, r0 + rb, n - r0 - rb));
+        }
+        LU_CUDA(diag(Y, Zw, dinvL));  // Zw = L^{-1} P B
+        for (int b = nblk - 1; b > 0; --b) {  // Zw[above b] -= G_U Zw_b
+            int r0 = b * bs, rb = std::min(bs, n - r0);
+            LU_CUDA(gstep(Zw, r0, rb, 0, r0));
+        }
+        LU_CUDA(diag(Zw, Y, dinvU));  // Y = U^{-1} Zw
+    } else {
+        auto step = [&](V Yv, V Zv, int r0, int rb, int rest0, int nrest, const typename V::cv* T) {
+            return narrow ? launch_trsv_step<V, 16>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T)
+                          : launch_trsv_step<V, 32>(s, F, Yv, Zv, r0, rb, rest0, nrest, nrhs, bs, T);
+        };
+        for (int b = 0; b < nblk; ++b) {  // Zw = L^{-1} Y
+            int r0 = b * bs, rb = std::min(bs, n - r0);
+            LU_CUDA(step(Y, Zw, r0, rb, r0 + rb, n - r0 - rb, dinvL + (long)b * bs * bs));
+        }
+        for (int b = nblk - 1; b >= 0; --b) {  // Y = U^{-1} Zw
+            int r0 = b * bs, rb = std::min(bs, n - r0);
+            LU_CUDA(step(Zw, Y, r0, rb, 0, r0, dinvU + (long)b * bs * bs));
+        }
     }
     return BM_OK;
 }
