@@ -45,6 +45,31 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // staged in shared memory: whole when it fits, else in chunks of ST_KC columns that the CTA's
 // warps step through together.  Optionally writes the solved rows as a K-major tensor-core pack
 // (column c -> row c - b0).  One warp per column.
+// Asynchronous 4-byte global -> shared copies (cp.async, zero-filled when !full).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool full) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(full ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Strictly lower part of columns [k0, k0 + kc) of the tb x tb block at (t0, t0) of a planar FP32
+// matrix into dst (interleaved complex, leading dimension tb), by cp.async (nthreads threads).
+__device__ __forceinline__ void stage_lower_async(float2* dst, const C32& A, long t0, int tb, int k0, int kc,
+                                                  int nthreads) {
+    const int tot = tb * kc;
+    for (int e = threadIdx.x; e < tot; e += nthreads) {
+        const int i = e % tb, kk = e / tb;
+        const bool in = i > k0 + kk;
+        const long off = in ? (t0 + i) + (t0 + k0 + kk) * A.ld : 0;
+        cp_async4(&dst[e].x, A.re + off, in);
+        cp_async4(&dst[e].y, A.im + off, in);
+    }
+}
+
 constexpr int ST_WARPS = 16, ST_COLS = 1;
 constexpr int ST_KC = 32;  // L11 columns per shared-memory chunk when L11 does not fit whole
 template <class V>
@@ -61,10 +86,33 @@ __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const Swa
     const int ncols = na + nbc;
     const int cta_col0 = blockIdx.x * ST_WARPS * ST_COLS;
     const bool cta_has_b = (cta_col0 + ST_WARPS * ST_COLS > na) && tb > 0;
+    // strictly lower part of L11 columns [k0, k0 + kc) into Ls (leading dimension tb), SB loads in
+    // flight per thread at a time
+    auto stage = [&](int k0, int kc) {
+        constexpr int SB = 8;
+        const int tot = tb * kc;
+        for (int e0 = 0; e0 < tot; e0 += SB * ST_WARPS * 32) {
+            CV v[SB];
+#pragma unroll
+            for (int m = 0; m < SB; ++m) {
+                const int e = e0 + threadIdx.x + m * ST_WARPS * 32;
+                const int i = e % tb, kk = e / tb;
+                v[m] = (e < tot && i > k0 + kk) ? A.get((long)t0 + i, (long)t0 + k0 + kk) : czero<Rl>();
+            }
+#pragma unroll
+            for (int m = 0; m < SB; ++m) {
+                const int e = e0 + threadIdx.x + m * ST_WARPS * 32;
+                if (e < tot) Ls[e] = v[m];
+            }
+        }
+    };
     if (cta_has_b && l_in_smem == 1) {
-        for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) {
-            int i = e % tb, k = e / tb;
-            Ls[e] = (i > k) ? A.get((long)t0 + i, (long)t0 + k) : czero<Rl>();
+        if constexpr (std::is_same<V, C32>::value) {
+            stage_lower_async(Ls, A, t0, tb, 0, tb, ST_WARPS * 32);
+            cp_async_commit();
+            cp_async_wait<0>();
+        } else {
+            stage(0, tb);
         }
         __syncthreads();
     }
@@ -118,17 +166,38 @@ __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const Swa
     if (l_in_smem == 2) {
         // L11 larger than the shared-memory budget: stage it ST_KC columns at a time, the whole
         // CTA stepping through the chunks together (warps without a column to solve only help)
-        if (cta_has_b) {
-            for (int k0 = 0; k0 < tb; k0 += ST_KC) {
-                const int kc = min(ST_KC, tb - k0);
-                __syncthreads();
-                for (int e = threadIdx.x; e < tb * kc; e += blockDim.x) {
-                    const int i = e % tb, kk = e / tb;
-                    Ls[e] = (i > k0 + kk) ? A.get((long)t0 + i, (long)t0 + k0 + kk) : czero<Rl>();
+        if constexpr (!std::is_same<V, C32>::value) {  // FP64: L11 (NB <= 64) always fits whole
+            if (cta_has_b)
+                for (int k0 = 0; k0 < tb; k0 += ST_KC) {
+                    const int kc = min(ST_KC, tb - k0);
+                    __syncthreads();
+                    stage(k0, kc);
+                    __syncthreads();
+                    if (do_trsm)
+                        for (int k = k0; k < k0 + kc; ++k)
+                            step(k, [&](int i, int kk) { return Ls[i + (kk - k0) * tb]; });
                 }
-                __syncthreads();
+        } else if (cta_has_b) {
+            // two buffers of ST_KC / 2 columns: the next chunk's cp.async copies run while the
+            // warps step through the current one
+            constexpr int KC = ST_KC / 2;
+            CV* const buf1 = Ls + tb * KC;
+            stage_lower_async(Ls, A, t0, tb, 0, min(KC, tb), ST_WARPS * 32);
+            cp_async_commit();
+            for (int k0 = 0, c = 0; k0 < tb; k0 += KC, ++c) {
+                const int kc = min(KC, tb - k0);
+                if (k0 + KC < tb) {
+                    stage_lower_async((c & 1) ? Ls : buf1, A, t0, tb, k0 + KC, min(KC, tb - k0 - KC), ST_WARPS * 32);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncthreads();  // chunk c is in shared memory for every warp
+                const CV* cur = (c & 1) ? buf1 : Ls;
                 if (do_trsm)
-                    for (int k = k0; k < k0 + kc; ++k) step(k, [&](int i, int kk) { return Ls[i + (kk - k0) * tb]; });
+                    for (int k = k0; k < k0 + kc; ++k) step(k, [&](int i, int kk) { return cur[i + (kk - k0) * tb]; });
+                __syncthreads();  // every warp is done with chunk c before its buffer is refilled
             }
         }
     } else if (do_trsm) {
@@ -223,48 +292,94 @@ __global__ void iota_kernel(int* p, int n) {
     if (i < n) p[i] = i;
 }
 
-// Inverse of each bs x bs diagonal block (unit lower L or upper U) of the LU factor, by a
-// column sweep over X = I: for k in order (L: 0..rb-1; U: rb-1..0, row k first divided by U_kk),
-// every later row i takes X_i -= T_ik X_k, with all (i, column) pairs of a step in parallel.
-// Entries outside the rb x rb leading block are zero.
-template <class V, bool UPPER>
-__global__ void __launch_bounds__(256) tri_inv_kernel(V F, int n, int bs, typename V::cv* __restrict__ out) {
+// A ROWS x COLS tile of view A at (r0, c0) into shared memory (column-major, leading dimension
+// ROWS), zero outside nr x nc.  Each thread issues all its global loads before its first shared
+// store, so one memory latency covers the whole tile (256 threads).
+template <int ROWS, int COLS, class V>
+__device__ __forceinline__ void load_tile(typename V::cv* dst, const V& A, long r0, long c0, int nr, int nc) {
     using CV = typename V::cv;
     using Rl = typename V::real;
+    static_assert(ROWS * COLS % 256 == 0, "tile must split evenly over 256 threads");
+    constexpr int PER = ROWS * COLS / 256;
+    CV v[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int e = threadIdx.x + 256 * m;
+        const int i = e % ROWS, j = e / ROWS;
+        v[m] = (i < nr && j < nc) ? A.get(r0 + i, c0 + j) : czero<Rl>();
+    }
+#pragma unroll
+    for (int m = 0; m < PER; ++m) dst[threadIdx.x + 256 * m] = v[m];
+}
+
+// The same for a dense column-major B x B block (leading dimension B), zero outside n x n.
+template <int B, class CV>
+__device__ __forceinline__ void load_block(CV* dst, const CV* __restrict__ src, int nb) {
+    static_assert(B * B % 256 == 0, "block must split evenly over 256 threads");
+    constexpr int PER = B * B / 256;
+    CV v[PER];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int e = threadIdx.x + 256 * m;
+        const int i = e % B, j = e / B;
+        v[m] = (i < nb && j < nb) ? src[e] : CV{};
+    }
+#pragma unroll
+    for (int m = 0; m < PER; ++m) dst[threadIdx.x + 256 * m] = v[m];
+}
+
+// Inverse of each 64 x 64 diagonal block (unit lower L or upper U) of the LU factor, by a
+// column sweep over X = I: for k in order (L: 0..rb-1; U: rb-1..0, row k first divided by U_kk),
+// every later row i takes X_i -= T_ik X_k.  Thread t holds X[t % 64, t / 64 + 4 m] (m < 16) in
+// registers; row k goes through a double-buffered shared row, so each step needs one barrier
+// (the reciprocals 1 / U_kk are formed before the sweep).
+// Entries outside the rb x rb leading block are zero.
+constexpr int TI_B = 64;
+template <class V, bool UPPER>
+__global__ void __launch_bounds__(256) tri_inv_kernel(V F, int n, typename V::cv* __restrict__ out) {
+    using CV = typename V::cv;
+    using Rl = typename V::real;
+    constexpr int B = TI_B, M = B * B / 256;
     extern __shared__ __align__(16) unsigned char sm[];
-    CV* T = reinterpret_cast<CV*>(sm);  // [bs][bs] column-major
-    CV* X = T + bs * bs;
-    const int b = blockIdx.x;
-    const int r0 = b * bs;
-    const int rb = min(bs, n - r0);
-    const int nt = blockDim.x;
-    for (int e = threadIdx.x; e < bs * bs; e += nt) {
-        const int i = e % bs, j = e / bs;
-        T[e] = (i < rb && j < rb) ? F.get((long)r0 + i, (long)r0 + j) : czero<Rl>();
-        CV one = czero<Rl>();
-        if (i == j && i < rb) one.x = (Rl)1;
-        X[e] = one;
+    CV* T = reinterpret_cast<CV*>(sm);  // [B][B] column-major
+    CV* buf = T + B * B;                // [2][B]
+    CV* dg = buf + 2 * B;               // [B] 1 / U_kk
+    const int t = threadIdx.x, i = t % B, c0 = t / B;
+    const long r0 = (long)blockIdx.x * B;
+    const int rb = (int)min((long)B, n - r0);
+    load_tile<B, B>(T, F, r0, r0, rb, rb);
+    if (UPPER && t < rb) dg[t] = cinv(F.get(r0 + t, r0 + t));
+    CV x[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        x[m] = czero<Rl>();
+        if (i == c0 + 4 * m && i < rb) x[m].x = (Rl)1;
     }
     __syncthreads();
     for (int s = 0; s < rb; ++s) {
         const int k = UPPER ? rb - 1 - s : s;
-        if (UPPER) {
-            const CV d = cinv(T[k + k * bs]);
-            for (int c = threadIdx.x; c < rb; c += nt) X[k + c * bs] = cmul(X[k + c * bs], d);
-            __syncthreads();
-        }
-        for (int e = threadIdx.x; e < bs * bs; e += nt) {
-            const int i = e % bs, c = e / bs;
-            if (c < rb && (UPPER ? i < k : (i > k && i < rb))) {
-                CV t = T[i + k * bs];
-                t.x = -t.x;
-                t.y = -t.y;
-                cfma(X[e], t, X[k + c * bs]);
+        CV* bk = buf + (s & 1) * B;
+        if (i == k) {
+            if (UPPER) {
+                const CV d = dg[k];
+#pragma unroll
+                for (int m = 0; m < M; ++m) x[m] = cmul(x[m], d);
             }
+#pragma unroll
+            for (int m = 0; m < M; ++m) bk[c0 + 4 * m] = x[m];
         }
         __syncthreads();
+        if (UPPER ? i < k : (i > k && i < rb)) {
+            CV tik = T[i + k * B];
+            tik.x = -tik.x;
+            tik.y = -tik.y;
+#pragma unroll
+            for (int m = 0; m < M; ++m) cfma(x[m], tik, bk[c0 + 4 * m]);
+        }
     }
-    for (int e = threadIdx.x; e < bs * bs; e += nt) out[(long)b * bs * bs + e] = X[e];
+    CV* o = out + (long)blockIdx.x * B * B;
+#pragma unroll
+    for (int m = 0; m < M; ++m) o[i + (c0 + 4 * m) * B] = x[m];
 }
 
 // One block step of a blocked triangular solve with inverted diagonal blocks (one launch per
@@ -384,11 +499,8 @@ __global__ void __launch_bounds__(256) g_form_kernel(V F, int n, const typename 
     const long r0 = (long)it * B, c0 = (long)b * B;
     const int tm = (int)min((long)B, n - r0), rb = (int)min((long)B, n - c0);
     const CV* T = (it > b ? dinvL : dinvU) + (long)b * B * B;
-    for (int e = t; e < B * B; e += 256) {
-        const int i = e % B, k = e / B;
-        Ft[e] = (i < tm && k < rb) ? F.get(r0 + i, c0 + k) : czero<Rl>();
-        Ts[e] = (i < rb && k < rb) ? T[e] : czero<Rl>();
-    }
+    load_tile<B, B>(Ft, F, r0, c0, tm, rb);
+    load_block<B>(Ts, T, rb);
     __syncthreads();
     const int tx = t % 16, ty = t / 16;  // rows tx + 16 a, columns ty + 16 c
     CV acc[4][4];
@@ -435,14 +547,8 @@ __global__ void __launch_bounds__(256) trsv_g_step_kernel(V F, V Y, int r0, int 
     const int nc = min(BN, nrhs - j0);
     const long tr0 = (long)rest0 + (long)blockIdx.x * B;
     const int tm = (int)min((long)B, (long)rest0 + nrest - tr0);
-    for (int e = t; e < B * BN; e += 256) {
-        const int i = e % B, jj = e / B;
-        Yb[e] = (i < rb && jj < nc) ? Y.get((long)r0 + i, (long)j0 + jj) : czero<Rl>();
-    }
-    for (int e = t; e < B * B; e += 256) {
-        const int i = e % B, k = e / B;
-        Ft[e] = (i < tm && k < rb) ? F.get(tr0 + i, (long)r0 + k) : czero<Rl>();
-    }
+    load_tile<B, BN>(Yb, Y, r0, j0, rb, nc);
+    load_tile<B, B>(Ft, F, tr0, r0, tm, rb);
     __syncthreads();
     constexpr int TN = BN / 16;
     const int tx = t % 16, ty = t / 16;
@@ -462,20 +568,27 @@ __global__ void __launch_bounds__(256) trsv_g_step_kernel(V F, V Y, int r0, int 
 #pragma unroll
             for (int c = 0; c < TN; ++c) cfma(acc[a][c], fv[a], yv[c]);
     }
+    // read all of this thread's outputs before writing any (the reads do not wait on the writes)
+    CV yo[4][TN];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int i = tx + 16 * a;
-        if (i >= tm) continue;
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < TN; ++c) {
-            const int jj = ty + 16 * c;
-            if (jj >= nc) continue;
-            CV y = Y.get(tr0 + i, (long)j0 + jj);
-            y.x -= acc[a][c].x;
-            y.y -= acc[a][c].y;
-            Y.set(tr0 + i, (long)j0 + jj, y);
+            const int i = tx + 16 * a, jj = ty + 16 * c;
+            yo[a][c] = (i < tm && jj < nc) ? Y.get(tr0 + i, (long)j0 + jj) : czero<Rl>();
         }
-    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int i = tx + 16 * a, jj = ty + 16 * c;
+            if (i < tm && jj < nc) {
+                CV y = yo[a][c];
+                y.x -= acc[a][c].x;
+                y.y -= acc[a][c].y;
+                Y.set(tr0 + i, (long)j0 + jj, y);
+            }
+        }
 }
 
 // Z_b = T_b Y_b for every diagonal block b at once (grid: blocks x column tiles of BN).
@@ -493,15 +606,8 @@ __global__ void __launch_bounds__(256) trsv_diag_kernel(V Y, V Z, int n, int nrh
     const int rb = (int)min((long)B, n - r0);
     const int j0 = blockIdx.y * BN;
     const int nc = min(BN, nrhs - j0);
-    const CV* T = Tinv + (long)blockIdx.x * B * B;
-    for (int e = t; e < B * B; e += 256) {
-        const int i = e % B, k = e / B;
-        Ts[e] = (i < rb && k < rb) ? T[e] : czero<Rl>();
-    }
-    for (int e = t; e < B * BN; e += 256) {
-        const int i = e % B, jj = e / B;
-        Yb[e] = (i < rb && jj < nc) ? Y.get(r0 + i, (long)j0 + jj) : czero<Rl>();
-    }
+    load_block<B>(Ts, Tinv + (long)blockIdx.x * B * B, rb);
+    load_tile<B, BN>(Yb, Y, r0, j0, rb, nc);
     __syncthreads();
     constexpr int TN = BN / 16;
     const int tx = t % 16, ty = t / 16;
@@ -639,19 +745,19 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
     }
     // inverted diagonal blocks for getrs
     const int bs = c->bs_solve;
+    if (bs != TI_B || bs != TS_BM) {
+        bm_set_error("lu: the solve block size must be 64");
+        return BM_EINVAL;
+    }
     const int nblk = ceil_div(n, bs);
-    size_t smem = 2 * (size_t)bs * bs * sizeof(typename V::cv);
+    size_t smem = ((size_t)bs * bs + 3 * (size_t)bs) * sizeof(typename V::cv);
     using CV = typename V::cv;
     LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tri_inv_kernel<V, false><<<nblk, 256, smem, s>>>(F, n, bs, reinterpret_cast<CV*>(c->d_dinvL));
-    tri_inv_kernel<V, true><<<nblk, 256, smem, s>>>(F, n, bs, reinterpret_cast<CV*>(c->d_dinvU));
+    tri_inv_kernel<V, false><<<nblk, 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvL));
+    tri_inv_kernel<V, true><<<nblk, 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvU));
     LU_CUDA(cudaGetLastError());
     if constexpr (std::is_same<V, C32>::value) {
-        if (bs != TS_BM) {
-            bm_set_error("lu: the solve block size must be 64");
-            return BM_EINVAL;
-        }
         if (nblk > 1) {
             const size_t gsm = 2 * (size_t)TS_BM * TS_BM * sizeof(CV);
             LU_CUDA(cudaFuncSetAttribute(g_form_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
