@@ -95,6 +95,19 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, VA
         }
         __syncthreads();
     }
+    // all of this thread's C reads are issued before its first write (the compiler cannot move a
+    // read of C past a write to C, so interleaving them would cost one memory latency each)
+    using OCV = typename VC::cv;
+    OCV cin[TM][TN];
+    if (beta != (R)0) {
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) {
+                const long gi = i0 + tx + 16 * a, gj = j0 + ty + 16 * b;
+                if (gi < m && gj < n) cin[a][b] = C.get(gi, gj);
+            }
+    }
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
         long gi = i0 + tx + 16 * a;
@@ -106,11 +119,10 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, VA
             CV r;
             r.x = alpha * acc[a][b].x;
             r.y = alpha * acc[a][b].y;
-            typename VC::cv out = from_acc<VC>(r);
+            OCV out = from_acc<VC>(r);
             if (beta != (R)0) {
-                typename VC::cv c = C.get(gi, gj);
-                out.x += (typename VC::real)beta * c.x;
-                out.y += (typename VC::real)beta * c.y;
+                out.x += (typename VC::real)beta * cin[a][b].x;
+                out.y += (typename VC::real)beta * cin[a][b].y;
             }
             C.set(gi, gj, out);
         }
