@@ -290,3 +290,32 @@ bm_status ctx_alloc(bm_ctx* c, void** p, size_t bytes);
 void ctx_free(bm_ctx* c, void* p);
 size_t request_bytes(int N, int form, int prec, int nb, int nrhs);  // api.cu
 void ctx_release(bm_ctx* c);                                        // api.cu
+
+// ---------------------------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with launch_pdl may start while the previous
+// kernel of its stream is still running.  It calls pdl_wait() before it touches any memory the
+// previous kernels may write or read (only data that stays fixed for the whole sequence, such as
+// factors during a solve, may be read before), which returns once the previous grid has completed
+// and its writes are visible; pdl_trigger() then lets the next kernel start launching.  In a
+// kernel launched without the attribute both are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Not for cluster launches: the panel kernels (clusters) keep plain stream ordering.
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+#endif

@@ -43,6 +43,8 @@ template <class VA, class VB, class VC, class R, bool AT, int BM, int BN>
 __global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, VA A, VB B, VC C, R alpha, R beta) {
     using CV = cplx_t<R>;
     constexpr int TM = BM / 16, TN = BN / 16;
+    pdl_wait();
+    pdl_trigger();
     __shared__ CV As[BK][BM + 1];
     __shared__ CV Bs[BK][BN + 1];
     const int t = threadIdx.x;
@@ -132,17 +134,15 @@ __global__ void __launch_bounds__(256) cgemm_simt_kernel(int m, int n, int k, VA
 template <class VA, class VB, class VC, class R, bool AT>
 cudaError_t launch_impl(cudaStream_t s, int m, int n, int k, VA A, VB B, VC C, R alpha, R beta) {
     if (m <= 0 || n <= 0) return cudaSuccess;
+    // every launch may overlap the previous kernel's tail: the kernel waits (pdl_wait) before it
+    // reads anything
+    auto go = [&](auto kern, dim3 grid) { return launch_pdl(kern, grid, dim3(256), 0, s, m, n, k, A, B, C, alpha, beta); };
     // Few right-hand sides (n <= 80, e.g. 65): one column tile covers them all, so A is streamed
     // once; 32-row tiles when 64-row ones would leave SMs idle.
     if (n > 32 && n <= 80) {
-        if ((long)ceil_div(m, 64) >= 2 * 152) {
-            cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 80><<<dim3(ceil_div(m, 64), 1), 256, 0, s>>>(m, n, k, A, B, C,
-                                                                                                alpha, beta);
-        } else {
-            cgemm_simt_kernel<VA, VB, VC, R, AT, 32, 80><<<dim3(ceil_div(m, 32), 1), 256, 0, s>>>(m, n, k, A, B, C,
-                                                                                                alpha, beta);
-        }
-        return cudaGetLastError();
+        if ((long)ceil_div(m, 64) >= 2 * 152)
+            return go(cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 80>, dim3(ceil_div(m, 64), 1));
+        return go(cgemm_simt_kernel<VA, VB, VC, R, AT, 32, 80>, dim3(ceil_div(m, 32), 1));
     }
     // otherwise the column tile with the least padding (ties go to the wider tile)
     int bn = 64;
@@ -154,17 +154,9 @@ cudaError_t launch_impl(cudaStream_t s, int m, int n, int k, VA A, VB B, VC C, R
             bn = cand;
         }
     }
-    if (bn == 16) {
-        dim3 grid(ceil_div(m, 64), ceil_div(n, 16));
-        cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 16><<<grid, 256, 0, s>>>(m, n, k, A, B, C, alpha, beta);
-    } else if (bn == 32) {
-        dim3 grid(ceil_div(m, 64), ceil_div(n, 32));
-        cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 32><<<grid, 256, 0, s>>>(m, n, k, A, B, C, alpha, beta);
-    } else {
-        dim3 grid(ceil_div(m, 64), ceil_div(n, 64));
-        cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 64><<<grid, 256, 0, s>>>(m, n, k, A, B, C, alpha, beta);
-    }
-    return cudaGetLastError();
+    if (bn == 16) return go(cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 16>, dim3(ceil_div(m, 64), ceil_div(n, 16)));
+    if (bn == 32) return go(cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 32>, dim3(ceil_div(m, 64), ceil_div(n, 32)));
+    return go(cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 64>, dim3(ceil_div(m, 64), ceil_div(n, 64)));
 }
 
 }  // namespace

@@ -45,14 +45,6 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // staged in shared memory: whole when it fits, else in chunks of ST_KC columns that the CTA's
 // warps step through together.  Optionally writes the solved rows as a K-major tensor-core pack
 // (column c -> row c - b0).  One warp per column.
-// Programmatic dependent launch.  A kernel launched with programmatic stream serialization may
-// start while the previous kernel of the stream is still running: it loads only data that no
-// kernel of the solve writes (factors, inverted blocks) before pdl_wait(), which returns once the
-// previous grid has completed and its writes are visible; pdl_trigger() then lets the next kernel
-// start its own prologue.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 // Asynchronous 4-byte global -> shared copies (cp.async, zero-filled when !full).
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool full) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -87,6 +79,8 @@ __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const Swa
     using CV = typename V::cv;
     using Rl = typename V::real;
     constexpr int QMAX = 8;  // rows per lane: tb <= 256
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char smraw[];
     CV* Ls = reinterpret_cast<CV*>(smraw);  // tb x tb, column-major
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -696,8 +690,8 @@ cudaError_t launch_swap_trsm(cudaStream_t s, V A, const SwapMap* map, int a0, in
         if (e != cudaSuccess) return e;
     }
     int grid = ceil_div(ncols, ST_WARPS * ST_COLS);
-    kern<<<grid, ST_WARPS * 32, smem, s>>>(A, map, a0, a1, b0, b1, t0, tb, Upr, Upi, ldk, split, l_in_smem);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3(grid), dim3(ST_WARPS * 32), smem, s, A, map, a0, a1, b0, b1, t0, tb, Upr, Upi, ldk,
+                      split, l_in_smem);
 }
 
 cudaError_t gemm_any(cudaStream_t s, int m, int n, int k, Z64 A, Z64 B, Z64 C) {
@@ -793,37 +787,24 @@ cudaError_t launch_trsv_step(cudaStream_t s, V F, V Y, V Z, int r0, int rb, int 
     return cudaGetLastError();
 }
 
-// Launch with programmatic stream serialization (the kernel calls pdl_wait before it reads or
-// writes anything the previous kernel of the stream may touch).
-template <class... KArgs, class... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
 template <class V, int BN>
 cudaError_t launch_trsv_g_step(cudaStream_t s, V F, V Y, int r0, int rb, int rest0, int nrest, int nrhs) {
     size_t smem = ((size_t)BN * TS_BM + (size_t)TS_BM * TS_BM) * sizeof(typename V::cv);
     dim3 grid(ceil_div(nrest, TS_BM), ceil_div(nrhs, BN));
-    return launch_pdl(trsv_g_step_kernel<V, BN>, grid, dim3(256), smem, s, F, Y, r0, rb, rest0, nrest, nrhs);
+    auto kern = trsv_g_step_kernel<V, BN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(kern, grid, dim3(256), smem, s, F, Y, r0, rb, rest0, nrest, nrhs);
 }
 
 template <class V, int BN>
 cudaError_t launch_trsv_diag(cudaStream_t s, V Y, V Z, int n, int nrhs, const typename V::cv* Tinv) {
     size_t smem = ((size_t)TS_BM * TS_BM + (size_t)BN * TS_BM) * sizeof(typename V::cv);
     dim3 grid(ceil_div(n, TS_BM), ceil_div(nrhs, BN));
-    return launch_pdl(trsv_diag_kernel<V, BN>, grid, dim3(256), smem, s, Y, Z, n, nrhs, Tinv);
+    auto kern = trsv_diag_kernel<V, BN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(kern, grid, dim3(256), smem, s, Y, Z, n, nrhs, Tinv);
 }
 
 // Solve L U X = Y in place (Y holds P B); Zw is an n x nrhs work buffer.
