@@ -146,25 +146,42 @@ __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const Swa
         int i = lane + 32 * q;
         x[q] = (do_trsm && i < tb) ? A.get((long)t0 + i, col) : czero<Rl>();
     }
-    // x -= L11 columns k < tb, one k at a time; lk(i, k) reads L(t0 + i, t0 + k) from wherever it
-    // is staged
-    auto step = [&](int k, auto lk) {
-        const int qk = k >> 5, lkn = k & 31;
-        CV xk = czero<Rl>();
+    // x -= L11 columns k in [kb, ke), all in one group of 32 (k = 32 QK + l); lk(i, k) reads
+    // L(t0 + i, t0 + k) from wherever it is staged.  With the group a compile-time constant, the
+    // value x_k comes straight from register x[QK] of lane l, and only rows of groups >= QK are
+    // touched, without per-row predicates beyond the diagonal group.
+    auto steps_q = [&](auto qc, int kb, int ke, auto lk) {
+        constexpr int QK = decltype(qc)::value;
+        for (int k = kb; k < ke; ++k) {
+            const int l = k & 31;
+            CV nx;
+            nx.x = -__shfl_sync(0xffffffffu, x[QK].x, l);
+            nx.y = -__shfl_sync(0xffffffffu, x[QK].y, l);
+            if (lane > l && lane + 32 * QK < tb) cfma(x[QK], lk(lane + 32 * QK, k), nx);
 #pragma unroll
-        for (int q = 0; q < QMAX; ++q)
-            if (q == qk) xk = x[q];
-        xk.x = __shfl_sync(0xffffffffu, xk.x, lkn);
-        xk.y = __shfl_sync(0xffffffffu, xk.y, lkn);
-        CV nx;
-        nx.x = -xk.x;
-        nx.y = -xk.y;
-#pragma unroll
-        for (int q = 0; q < QMAX; ++q) {
-            int i = lane + 32 * q;
-            if (q >= qk && i > k && i < tb) cfma(x[q], lk(i, k), nx);
+            for (int q = QK + 1; q < QMAX; ++q) {
+                const int i = lane + 32 * q;
+                if (i < tb) cfma(x[q], lk(i, k), nx);
+            }
         }
     };
+    auto steps = [&](int kb, int ke, auto lk) {
+        for (int g0 = kb; g0 < ke;) {
+            const int g1 = min(ke, (g0 & ~31) + 32);
+            switch (g0 >> 5) {
+                case 0: steps_q(std::integral_constant<int, 0>{}, g0, g1, lk); break;
+                case 1: steps_q(std::integral_constant<int, 1>{}, g0, g1, lk); break;
+                case 2: steps_q(std::integral_constant<int, 2>{}, g0, g1, lk); break;
+                case 3: steps_q(std::integral_constant<int, 3>{}, g0, g1, lk); break;
+                case 4: steps_q(std::integral_constant<int, 4>{}, g0, g1, lk); break;
+                case 5: steps_q(std::integral_constant<int, 5>{}, g0, g1, lk); break;
+                case 6: steps_q(std::integral_constant<int, 6>{}, g0, g1, lk); break;
+                default: steps_q(std::integral_constant<int, 7>{}, g0, g1, lk); break;
+            }
+            g0 = g1;
+        }
+    };
+    static_assert(QMAX == 8, "one case per group of 32 rows");
     if (l_in_smem == 2) {
         // L11 larger than the shared-memory budget: stage it ST_KC columns at a time, the whole
         // CTA stepping through the chunks together (warps without a column to solve only help)
@@ -175,9 +192,7 @@ __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const Swa
                     __syncthreads();
                     stage(k0, kc);
                     __syncthreads();
-                    if (do_trsm)
-                        for (int k = k0; k < k0 + kc; ++k)
-                            step(k, [&](int i, int kk) { return Ls[i + (kk - k0) * tb]; });
+                    if (do_trsm) steps(k0, k0 + kc, [&](int i, int kk) { return Ls[i + (kk - k0) * tb]; });
                 }
         } else if (cta_has_b) {
             // two buffers of ST_KC / 2 columns: the next chunk's cp.async copies run while the
@@ -197,16 +212,15 @@ __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const Swa
                 }
                 __syncthreads();  // chunk c is in shared memory for every warp
                 const CV* cur = (c & 1) ? buf1 : Ls;
-                if (do_trsm)
-                    for (int k = k0; k < k0 + kc; ++k) step(k, [&](int i, int kk) { return cur[i + (kk - k0) * tb]; });
+                if (do_trsm) steps(k0, k0 + kc, [&](int i, int kk) { return cur[i + (kk - k0) * tb]; });
                 __syncthreads();  // every warp is done with chunk c before its buffer is refilled
             }
         }
     } else if (do_trsm) {
-        for (int k = 0; k < tb; ++k)
-            step(k, [&](int i, int kk) {
-                return l_in_smem ? Ls[i + kk * tb] : A.get((long)t0 + i, (long)t0 + kk);
-            });
+        if (l_in_smem)
+            steps(0, tb, [&](int i, int kk) { return Ls[i + kk * tb]; });
+        else
+            steps(0, tb, [&](int i, int kk) { return A.get((long)t0 + i, (long)t0 + kk); });
     }
     if (do_trsm) {
 #pragma unroll
