@@ -575,7 +575,10 @@ __global__ void __launch_bounds__(256) trsv_g_step_kernel(V F, V Y, int r0, int 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < TN; ++c) acc[a][c] = czero<Rl>();
-    for (int k = 0; k < rb; ++k) {
+    // threads whose columns all lie past the last right-hand side (the ragged column tile, e.g.
+    // 65 = 4 x 16 + 1) skip the product, so their warps leave the SM early
+    const int kend = (ty < nc) ? rb : 0;
+    for (int k = 0; k < kend; ++k) {
         CV fv[4], yv[TN];
 #pragma unroll
         for (int a = 0; a < 4; ++a) fv[a] = Ft[k * B + tx + 16 * a];

@@ -44,6 +44,7 @@ __global__ void eta_kernel(const double2* __restrict__ R, const double2* __restr
     bool bad = false;
     // magnitudes in FP32 (the ratio needs a few digits; FP64 hypot would cost the FP64 pipe)
     float rf = 0.f, xf = 0.f, bf = 0.f;
+#pragma unroll 4
     for (int i = threadIdx.x; i < nsys; i += blockDim.x) {
         long o = i + (long)c * ld;
         double2 bv = B[o];
@@ -232,7 +233,8 @@ bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R,
 bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const double2* B, long ld, int nrhs,
                          double* d_eta) {
     SV_CUDA(cudaMemsetAsync(d_eta, 0, 2 * sizeof(double), c->stream));
-    eta_kernel<<<nrhs, 256, 0, c->stream>>>(R, X, B, ld, c->nsys, c->d_normA, d_eta);
+    // one CTA of 1024 threads per column (few columns: the loads in flight per SM set the time)
+    eta_kernel<<<nrhs, 1024, 0, c->stream>>>(R, X, B, ld, c->nsys, c->d_normA, d_eta);
     SV_CUDA(cudaGetLastError());
     return BM_OK;
 }
