@@ -11,10 +11,10 @@
 //   * the complex product uses three real products (Karatsuba / Gauss):
 //         P1 = re a re x,  P2 = im a im x,  P3 = (re a + im a)(re x + im x),
 //         re(a x) = P1 - P2,  im(a x) = P3 - P1 - P2,
-//     each summed over K as an unevaluated pair (s, t): the leading product hi_a * hi_x is formed
-//     exactly as p + e with one FMA (TwoProd) and added to s with TwoSum (Knuth), so the long sum
-//     keeps ~46 bits; the cross terms hi_a lo_x + lo_a hi_x (2^-24 of the total) and e are
-//     summed in plain FP32 and lo_a lo_x (2^-48) is dropped;
+//     each summed over K as an unevaluated pair (s, c): the leading product hi_a * hi_x is formed
+//     exactly as p + e with one FMA (TwoProd) and added to s with TwoSum (Knuth), whose rounding
+//     error goes to c together with e and the cross terms hi_a lo_x + lo_a hi_x (all ~2^-24 of
+//     the terms), so the long sum keeps ~46 bits; lo_a lo_x (2^-48) is dropped;
 //   * the three sums combine in FP64 at the end; the cancellation in P3 - P1 - P2 costs at most
 //     a factor ~4 on the ~1e-12 relative accuracy, far below what a backward error of 1e-9 needs.
 // 36 FP32 operations per complex multiply-add (four real products would take 48).
@@ -25,31 +25,32 @@ namespace {
 
 constexpr int BM = 64, BN = 16, BK = 16;  // 4 rows x 1 column per thread
 
-// (s, t) += a * b: exact product (TwoProd), compensated sum (TwoSum); the product's rounding
-// error goes to the plain FP32 sum c.  The _rn intrinsics keep the compiler from contracting these
-// steps into FMAs, which would break their exactness.
-__device__ __forceinline__ void acc2(float& s, float& t, float& c, float a, float b) {
+// s += a * b with exact product (TwoProd) and compensated sum (TwoSum); both rounding errors go
+// to the plain FP32 sum c, which also takes the cross terms (all three are ~2^-24 of the terms
+// they come from, so one FP32 sum carries them as well as two).  The _rn intrinsics keep the
+// compiler from contracting these steps into FMAs, which would break their exactness.
+__device__ __forceinline__ void acc2(float& s, float& c, float a, float b) {
     float p = __fmul_rn(a, b);
     float e = fmaf(a, b, -p);
     float u = __fadd_rn(s, p);
     float bb = __fsub_rn(u, s);
     float err = __fadd_rn(__fsub_rn(s, __fsub_rn(u, bb)), __fsub_rn(p, bb));
     s = u;
-    t += err;
+    c += err;
     c += e;
 }
 
-// Three compensated sums (P1, P2, P3) side by side, plus their FP32 cross-term sums.
+// Three compensated sums (P1, P2, P3) side by side: leading parts s, FP32 error/cross-term sums c.
 struct DfAcc {
-    float s1, t1, s2, t2, s3, t3;
+    float s1, s2, s3;
     float c1, c2, c3;
 };
 
 // a = (re_hi, re_lo, im_hi, im_lo), as = (sum_hi, sum_lo); x and xs likewise
 __device__ __forceinline__ void dfma(DfAcc& c, const float4& a, const float2& as, const float4& x, const float2& xs) {
-    acc2(c.s1, c.t1, c.c1, a.x, x.x);
-    acc2(c.s2, c.t2, c.c2, a.z, x.z);
-    acc2(c.s3, c.t3, c.c3, as.x, xs.x);
+    acc2(c.s1, c.c1, a.x, x.x);
+    acc2(c.s2, c.c2, a.z, x.z);
+    acc2(c.s3, c.c3, as.x, xs.x);
     c.c1 = fmaf(a.x, x.y, c.c1);
     c.c1 = fmaf(a.y, x.x, c.c1);
     c.c2 = fmaf(a.z, x.w, c.c2);
@@ -94,9 +95,10 @@ __global__ void __launch_bounds__(256, 3) resid_df_kernel(const __grid_constant_
     const int z = u % P.S, it = u / P.S;
     const int kb = (int)((long)z * k / P.S), ke = (int)((long)(z + 1) * k / P.S);
     const long i0 = (long)it * BM, j0 = (long)jt * BN;
+    const bool active = j0 + ty < n;
     DfAcc acc[TM];
 #pragma unroll
-    for (int a = 0; a < TM; ++a) acc[a] = DfAcc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int a = 0; a < TM; ++a) acc[a] = DfAcc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
         for (int e = t; e < BM * BK; e += 256) {
@@ -116,12 +118,16 @@ __global__ void __launch_bounds__(256, 3) resid_df_kernel(const __grid_constant_
             Ys[kk][jj] = in ? __ldg(P.XQ + gk + gj * P.ldx) : make_float2(0.f, 0.f);
         }
         __syncthreads();
+        // threads of columns past the last right-hand side (the ragged column tile: 65 = 4 x 16 + 1)
+        // only help with the loads
+        if (active) {
 #pragma unroll 4
-        for (int kk = 0; kk < BK; ++kk) {
-            const float4 xv = Xs[kk][ty];
-            const float2 yv = Ys[kk][ty];
+            for (int kk = 0; kk < BK; ++kk) {
+                const float4 xv = Xs[kk][ty];
+                const float2 yv = Ys[kk][ty];
 #pragma unroll
-            for (int a = 0; a < TM; ++a) dfma(acc[a], As[kk][tx + 16 * a], Qs[kk][tx + 16 * a], xv, yv);
+                for (int a = 0; a < TM; ++a) dfma(acc[a], As[kk][tx + 16 * a], Qs[kk][tx + 16 * a], xv, yv);
+            }
         }
         __syncthreads();
     }
@@ -132,9 +138,9 @@ __global__ void __launch_bounds__(256, 3) resid_df_kernel(const __grid_constant_
         long gi = i0 + tx + 16 * a;
         if (gi >= m) continue;
         const DfAcc& r = acc[a];
-        double p1 = ((double)r.s1 + (double)r.t1) + (double)r.c1;
-        double p2 = ((double)r.s2 + (double)r.t2) + (double)r.c2;
-        double p3 = ((double)r.s3 + (double)r.t3) + (double)r.c3;
+        double p1 = (double)r.s1 + (double)r.c1;
+        double p2 = (double)r.s2 + (double)r.c2;
+        double p3 = (double)r.s3 + (double)r.c3;
         const double re = p1 - p2, im = (p3 - p1) - p2;
         if (P.S == 1) {
             double2& c = P.C[gi + gj * P.ldc];
