@@ -350,12 +350,12 @@ struct PanelShape {
 
 // cluster size, rows per CTA, rows per thread and sub-panel width for a panel of m rows.  The
 // lane-per-column kernel (lane_col, C32 only) spreads the rows over as many CTAs as give each about
-// 128 rows (8 per warp: the per-column update shrinks with the rows per warp), up to the cluster
+// 64 rows (4 per warp: the per-column update shrinks with the rows per warp), up to the cluster
 // limit, and takes up to 256 rows per CTA (16 per warp); taller panels use the register-row kernel.
 template <class V>
 bool panel_shape(int m, int cl_max, bool lane_col, PanelShape& ps) {
     if (std::is_same<V, C32>::value && lane_col) {
-        const int CL = std::min(cl_max, std::max(1, ceil_div(m, 128)));
+        const int CL = std::min(cl_max, std::max(1, ceil_div(m, 64)));
         const int need = ceil_div(ceil_div(m, CL), PANEL_THREADS / 32);  // rows per warp
         int rpw = 2;
         while (rpw < need) rpw *= 2;
