@@ -21,7 +21,6 @@ constexpr int BK = 16;
 template <class R> BM_HD cplx_t<R> conv(double2 v);
 template <class R> BM_HD cplx_t<R> conv(float2 v);
 template <> BM_HD double2 conv<double>(double2 v) { return v; }
-template <> BM_HD double2 conv<double>(float2 v) { return make_double2(v.x, v.y); }
 template <> BM_HD float2 conv<float>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 template <> BM_HD float2 conv<float>(float2 v) { return v; }
 

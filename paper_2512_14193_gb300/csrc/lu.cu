@@ -3,15 +3,16 @@
 //
 // Right-looking blocked LU with two block sizes:
 //   for each big panel of NB columns (C32: 256, Z64: 64):
-//     for each sub-panel of nbp columns (nbp = 32/16/8 for C32, 16/8/4 for Z64 - wider when the
-//     rows below the diagonal are fewer):
-//        panel_kernel      : unblocked LU with partial pivoting of rows [j, n) x nbp columns.
-//                            Rows are spread over a cluster of up to 16 CTAs, one to four rows per
-//                            thread, held in registers.  Each column's pivot candidates (value,
-//                            index, whole row) are pushed to every CTA through distributed shared
-//                            memory; the cluster barrier is split into arrive/wait so that the
-//                            rank-1 update of all but the next column runs while it completes.
-//                            The last CTA work also builds the row-interchange maps.
+//     for each sub-panel of nbp columns:
+//        panel kernel      : unblocked LU with partial pivoting of rows [j, n) x nbp columns on a
+//                            cluster of up to 16 CTAs.  C32 panels of at most 4096 rows use the
+//                            lane-per-column kernel (panel_c32.cu: nbp = 32, lane k of every warp
+//                            holds column k of 4-16 rows, about 64-256 rows per CTA); taller C32
+//                            panels and all Z64 panels use the register-row kernel
+//                            (lu_internal.cuh: one to four rows per thread, nbp = 32/16/8 for C32,
+//                            16/8/4 for Z64).  Each column's pivot candidates (value, index, whole
+//                            row) go to every CTA through distributed shared memory; CTA 0 also
+//                            builds the row-interchange maps.
 //        swap_trsm_kernel  : row interchanges + unit-lower solve for the rest of the big panel
 //        gemm (SIMT)       : rank-nbp update of the rest of the big panel
 //     swap_trsm_kernel     : interchanges for all other columns, U12 = L11^{-1} A12 (and its
