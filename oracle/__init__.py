@@ -14,6 +14,8 @@ for Helmholtz transmission problems"), cited in its docstring:
 * ``geometry``  - equispaced Nystrom nodes on the curve (§4, Eq. dis_mixedBM setup)
 * ``operators`` - S_k, D_k, D*_k, N_k kernels (§2.2) with the 1-point
                   zeta-corrected diagonal (§4)
+* ``zeta``      - the high-order zeta-corrected rule of §5.3 (order 2p + 3; p = 14 is the
+                  paper's order 31), weights from the generalised Euler-Maclaurin expansion
 * ``systems``   - the 3N mixed system (Eq. dis_mixedBM, Theorem thm:LU blocks)
                   and the 2N ordinary system (Eq. dis_BM)
 * ``dense``     - unblocked LU with partial pivoting, the Schur path of
@@ -24,7 +26,8 @@ for Helmholtz transmission problems"), cited in its docstring:
 Pins (tests/test_oracle_*.py) tie each part to something other than itself:
 mpmath and Hankel-zero values printed in Table tb:ssm_eigenvalues for the
 special functions, circle closed forms and convergence rates for the
-quadrature, LAPACK for the dense LU, the Mie series and the optical theorem
+quadrature (both orders; the order-31 rule also against the eigenvalues the paper
+computed with it), LAPACK for the dense LU, the Mie series and the optical theorem
 for the physics.  Nothing here is "parity unpinned".
 """
 from .geometry import Geometry, nodes

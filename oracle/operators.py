@@ -69,8 +69,9 @@ def _diag(g: Geometry, k: complex, I: np.ndarray):
     return S, D, Ds, Nk + 0j
 
 
-def layer_operators(g: Geometry, k: complex) -> dict:
-    """Full N x N matrices S_k, D_k, D*_k, N_k (keys 'S', 'D', 'Ds', 'N')."""
+def layer_operators(g: Geometry, k: complex, zeta_p: int = 0) -> dict:
+    """Full N x N matrices S_k, D_k, D*_k, N_k (keys 'S', 'D', 'Ds', 'N').  zeta_p > 0 adds the
+    order-(2 zeta_p + 3) zeta corrections of ``oracle.zeta`` (the §5.3 high-order rule)."""
     N = g.N
     I, J = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
     off = I != J
@@ -81,6 +82,9 @@ def layer_operators(g: Geometry, k: complex) -> dict:
     dvals = _diag(g, k, np.arange(N))
     for key, v in zip(("S", "D", "Ds", "N"), dvals):
         out[key][np.arange(N), np.arange(N)] = v
+    if zeta_p > 0:
+        from .zeta import apply_corrections
+        out = apply_corrections(g, k, out, zeta_p)
     return out
 
 

@@ -67,24 +67,25 @@ def hankel_eigs(mu: np.ndarray, center: complex, radius: float, delta: float = 1
     return np.sort_complex(inside), omega, s
 
 
-def bie_solver(curve: W.Curve, N: int, k_ratio: complex, formulation: int):
+def bie_solver(curve: W.Curve, N: int, k_ratio: complex, formulation: int, zeta_p: int = 0):
     """solve(z, V) = T(z)^{-1} V for the discretised system at k_out = z, k_in = k_ratio z (so
-    eps1 = k_ratio^2 is fixed along the contour; beta = i / k_out)."""
+    eps1 = k_ratio^2 is fixed along the contour; beta = i / k_out).  zeta_p > 0 assembles with the
+    high-order zeta-corrected rule of §5.3 (order 2 zeta_p + 3, ``oracle.zeta``)."""
     g = nodes(curve, N)
 
     def solve(z, V):
         P = default_params(z, k_ratio * z)
         if formulation == W.MIXED:
-            A = mixed_matrix(mixed_blocks(g, P))
+            A = mixed_matrix(mixed_blocks(g, P, zeta_p))
         else:
-            A = ordinary_matrix(g, P)
+            A = ordinary_matrix(g, P, zeta_p=zeta_p)
         return np.linalg.solve(A, V)
 
     return solve
 
 
 def ssm(curve: W.Curve, N: int, k_ratio: complex, formulation: int, center: complex, radius: float, P: int, M: int,
-        V: np.ndarray, delta: float = 1e-12):
+        V: np.ndarray, delta: float = 1e-12, zeta_p: int = 0):
     """Eigenvalues of the discretised system inside the circle (block Hankel Sakurai-Sugiura)."""
-    mu = moments(bie_solver(curve, N, k_ratio, formulation), center, radius, P, M, V)
+    mu = moments(bie_solver(curve, N, k_ratio, formulation, zeta_p), center, radius, P, M, V)
     return hankel_eigs(mu, center, radius, delta)

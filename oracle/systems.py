@@ -47,11 +47,12 @@ def default_params(k_out, k_in, eps0=1.0, eps1=None, beta=None) -> Params:
     return Params(k0, k1, complex(eps0), complex(eps1), complex(beta))
 
 
-def mixed_blocks(g: Geometry, P: Params):
-    """M13, M23, M31, M32 of Theorem thm:LU (each N x N complex)."""
+def mixed_blocks(g: Geometry, P: Params, zeta_p: int = 0):
+    """M13, M23, M31, M32 of Theorem thm:LU (each N x N complex); zeta_p selects the quadrature
+    (0: the one-point rule of §4, p > 0: order 2p + 3, see ``oracle.zeta``)."""
     I = np.eye(g.N)
-    o0 = layer_operators(g, P.k0)
-    o1 = layer_operators(g, P.k1)
+    o0 = layer_operators(g, P.k0, zeta_p)
+    o1 = layer_operators(g, P.k1, zeta_p)
     M13 = -o1["S"]
     M23 = -(o1["Ds"] + 0.5 * I) / P.eps1
     M31 = o0["D"] - 0.5 * I + P.beta * o0["N"]
@@ -73,12 +74,12 @@ def mixed_matrix(blocks) -> np.ndarray:
     return A
 
 
-def ordinary_matrix(g: Geometry, P: Params, literal_ordinary: bool = False) -> np.ndarray:
+def ordinary_matrix(g: Geometry, P: Params, literal_ordinary: bool = False, zeta_p: int = 0) -> np.ndarray:
     """The 2N x 2N matrix of Eq. dis_BM (with the eps1 reading of its (2,2) block)."""
     N = g.N
     I = np.eye(N)
-    o0 = layer_operators(g, P.k0)
-    o1 = layer_operators(g, P.k1)
+    o0 = layer_operators(g, P.k0, zeta_p)
+    o1 = layer_operators(g, P.k1, zeta_p)
     A = np.zeros((2 * N, 2 * N), dtype=np.complex128)
     A[:N, :N] = o0["D"] - 0.5 * I + P.beta * o0["N"]
     A[:N, N:] = -P.eps0 * (o0["S"] + P.beta * (o0["Ds"] + 0.5 * I))
