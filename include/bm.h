@@ -98,7 +98,14 @@ typedef struct {
  *     BM_RESID_FP64_ALL (2): every residual in FP64.
  *  The updated residuals of modes 0 and 1 carry the FP32 product error of each update, so the
  *  backward error they track is reliable down to about 1e-12; refine_tol below 1e-12 needs
- *  BM_RESID_FP64_ALL (bm_assemble returns BM_EINVAL otherwise). */
+ *  BM_RESID_FP64_ALL (bm_assemble returns BM_EINVAL otherwise).
+ * zeta_p: quadrature.  0 (default) is the one-point zeta-corrected rule of section 4.  1..20 adds
+ *  the high-order zeta corrections of section 5.3 ("order 31" is zeta_p = 14): weights derived
+ *  from the Euler-Maclaurin expansion of the punctured trapezoid sum (zeta'(-2k) for the log
+ *  parts of S, D, D*, N; the two-term expansion of N's x^-2 part with a central second-derivative
+ *  stencil) on the 2 zeta_p + 1 (log parts) and 2 zeta_p + 3 (N) nodes around each diagonal, for
+ *  an O(h^(2 zeta_p + 3)) rule.  Needs N >= 2 zeta_p + 3, and |arg k| <= 60 degrees for both
+ *  wavenumbers unless |k| (zeta_p + 1) h max|x'| < 2.9 (BM_EINVAL otherwise). */
 typedef struct {
     double eps0;
     bm_c64 eps1;
@@ -110,6 +117,7 @@ typedef struct {
     int refine_maxit;
     int nb;
     int refine_residual;
+    int zeta_p;
 } bm_opts;
 
 typedef enum { BM_RESID_DF_UPDATE = 0, BM_RESID_FP64_UPDATE = 1, BM_RESID_FP64_ALL = 2 } bm_refine_residual;
@@ -134,7 +142,8 @@ bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size_t hbm_budg
 /* Assemble the Nystrom system (section 4, Eq. dis_mixedBM or Eq. dis_BM) for N nodes on the
  * curve, exterior/interior wavenumbers k_out = k0, k_in = k1 (complex; the principal branch is
  * used, Re k > 0 required).  Kernels of section 2.2 off the diagonal; the one-point
- * zeta-corrected diagonal of section 4 on it.  The right-hand side of a plane wave is made by
+ * zeta-corrected diagonal of section 4 on it (opts->zeta_p > 0: plus the high-order corrections
+ * on the band around it, see bm_opts).  The right-hand side of a plane wave is made by
  * bm_rhs_plane_wave.  Replaces any previous system and factorisation of the handle.
  * Errors: BM_EINVAL (N < 8, N > 65536, bad kind/params, Re k <= 0, |arg k| > 60 degrees),
  * BM_ENONFINITE, BM_ENOMEM (admission: the bytes the system and its factorisation need

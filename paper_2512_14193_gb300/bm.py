@@ -39,7 +39,7 @@ class bm_curve(C.Structure):
 class bm_opts(C.Structure):
     _fields_ = [("eps0", C.c_double), ("eps1", bm_c64), ("beta", bm_c64), ("eps_set", C.c_int),
                 ("beta_set", C.c_int), ("prec", C.c_int), ("refine_tol", C.c_double), ("refine_maxit", C.c_int),
-                ("nb", C.c_int), ("refine_residual", C.c_int)]
+                ("nb", C.c_int), ("refine_residual", C.c_int), ("zeta_p", C.c_int)]
 
 
 class bm_solve_info(C.Structure):
@@ -187,8 +187,9 @@ def bm_destroy(h) -> None:
 
 
 def make_opts(prec: int = BM_FP64, eps0: float = 1.0, eps1=None, beta=None, refine_tol: float = 1e-9,
-              refine_maxit: int = 30, nb: int = 0, residual: int = 0) -> bm_opts:
+              refine_maxit: int = 30, nb: int = 0, residual: int = 0, zeta_p: int = 0) -> bm_opts:
     o = bm_opts()
+    o.zeta_p = int(zeta_p)
     o.eps0 = float(eps0)
     o.prec = int(prec)
     o.refine_tol = float(refine_tol)

@@ -407,6 +407,35 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
         bm_set_error("nb must be a multiple of 32 in [32, 256]");
         return BM_EINVAL;
     }
+    const int zeta_p = opts ? opts->zeta_p : 0;
+    if (zeta_p < 0 || zeta_p > 20 || (zeta_p > 0 && N < 2 * zeta_p + 3)) {
+        bm_set_error("zeta_p must be in [0, 20] with N >= 2 zeta_p + 3");
+        return BM_EINVAL;
+    }
+    if (zeta_p > 0) {
+        // The corrections evaluate J0, J1 at k r on the stencil as (H(z) + conj H(conj z)) / 2; the
+        // conjugate argument stays in the supported sector when |arg k| <= 60 degrees, or when
+        // every |k r| on the stencil stays in the ascending-series zone (|z| < 3), for which any
+        // argument is exact.  r is at most the arc length (zeta_p + 1) h max|x'|.
+        double speed = 0.0;
+        const double* q = curve->p;
+        switch (curve->kind) {
+            case BM_CURVE_CIRCLE: speed = std::fabs(q[0]); break;
+            case BM_CURVE_ELLIPSE: speed = std::max(std::fabs(q[0]), std::fabs(q[1])); break;
+            case BM_CURVE_STAR: speed = std::hypot(std::fabs(q[0]) + std::fabs(q[1]), std::fabs(q[1] * q[2])); break;
+            case BM_CURVE_KITE: speed = std::hypot(1.0 + 2.0 * std::fabs(q[0]), q[1]); break;
+            default:
+                for (int j = 0; j < N; ++j) speed = std::max(speed, std::hypot(curve->user[6 * j + 2], curve->user[6 * j + 3]));
+        }
+        const double kmax = std::max(std::hypot(k_out.re, k_out.im), std::hypot(k_in.re, k_in.im));
+        const double zmax = kmax * (zeta_p + 1) * (2.0 * M_PI / N) * speed;
+        if (zmax >= 2.9)
+            for (bm_c64 k : {k_out, k_in})
+                if (std::fabs(std::atan2(k.im, k.re)) * deg > 60.0 + 1e-9) {
+                    bm_set_error("the high-order zeta corrections need |arg k| <= 60 degrees here");
+                    return BM_EINVAL;
+                }
+    }
     double eps0 = (opts && opts->eps0 != 0.0) ? opts->eps0 : 1.0;
     double2 k0 = d2(k_out), k1 = d2(k_in);
     double2 eps1, beta;
@@ -445,6 +474,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     c->form = form;
     c->prec = prec;
     c->nb = p.nb;
+    c->zeta_p = zeta_p;
     c->k0 = k0;
     c->k1 = k1;
     c->eps0 = make_double2(eps0, 0.0);
@@ -537,8 +567,9 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     }
     BM_CUDA_TRY(launch_geometry(st, curve->kind, curve->p, N, d_user, c->d_geom));
     BM_CUDA_TRY(launch_assemble(st, c));
+    BM_CUDA_TRY(launch_zeta_band(st, c));
     BM_CUDA_TRY(launch_normA(st, c));
-    c->launches += (form == BM_MIXED) ? 4 : 3;
+    c->launches += ((form == BM_MIXED) ? 4 : 3) + (c->zeta_p > 0 ? 1 : 0);
     if (c32) {
         if (form == BM_MIXED) {
             BM_CUDA_TRY(launch_pack_schur(st, c, prec == BM_CF32_3XTF32_IR));

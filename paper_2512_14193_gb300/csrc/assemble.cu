@@ -16,6 +16,8 @@
 // Blocks (Theorem thm:LU): M13 = -S1, M23 = -(D*1 + I/2)/eps1, M31 = D0 - I/2 + beta N0,
 // M32 = -eps0 (S0 + beta (D*0 + I/2)); ordinary (Eq. dis_BM, (2,2) block -eps1 S1):
 // [M31, M32; D1 + I/2, -eps1 S1].
+#include <cmath>
+
 #include "common.cuh"
 #include "hankel.cuh"
 #include "kernels.cuh"
@@ -439,6 +441,182 @@ __global__ void to_c32_kernel(const double2* __restrict__ A, long lda, int m, in
     Fi[i + (long)j * ldf] = (float)v.y;
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// High-order zeta corrections (the "order 31" rule of section 5.3; order 2p + 3 for all four
+// operators), added to the assembled blocks on the band |i - j| <= p + 1 around the diagonal.
+//
+// The punctured trapezoid sum of a kernel with an |x|^s singularity at the node x = 0 (x = s - t in
+// the curve parameter, equispaced nodes x = jh) has the expansion
+//     int |x|^s g dx = h sum_{j != 0} |jh|^s g(jh) - 2 sum_{k >= 0} zeta(-s-2k) h^(s+2k+1) g^(2k)(0) / (2k)!.
+//  * log|x| (the derivative in s at s = 0; zeta(-2k) = 0 for k >= 1): the correction is
+//    h ln(h/2pi) g(0) + 2 sum_{k>=1} zeta'(-2k) h^(2k+1) g^(2k)(0) / (2k)!, turned into weights
+//    h tau_m on g(mh), |m| <= p, exact for even polynomials of degree <= 2p:
+//        sum_{m=1..p} tau_m m^(2k) = zeta'(-2k), k = 1..p;  sigma_0 = -2 sum tau_m on the diagonal
+//    (beyond the ln(h/2pi) of the one-point rule).  The kernels' log parts come from the
+//    log(z/2) J_n(z) terms of Y_0, Y_1 (log r = log|x| + log(r/|x|), the second smooth):
+//        S: -(1/2pi) J0(kr) w        D: -(k/2pi) J1(kr) (d.nu_s)/r w     D*: +(k/2pi) J1(kr) (d.nu_t)/r w
+//        N: -(k/2pi) [k J0 (d.nu_t)(d.nu_s)/r^2 - 2 J1 (d.nu_t)(d.nu_s)/r^3 + J1 (nu_t.nu_s)/r] w
+//  * x^-2 (N; zeta(0) = -1/2 and the series stops): -(pi^2/3h) g(0) (the one-point rule) plus
+//    (h/2) g''(0), with g(x) = x^2 (N minus its log part) and g''(0) from the central stencil over
+//    |m| <= p + 1; g(0) = 1 / (2 pi |x'(t)|).
+// J_n(z) = (H_n(z) + conj(H_n(conj z))) / 2 reuses the Hankel evaluation (the conjugate argument
+// stays in the supported sector).  One thread per (row, offset); every entry is touched by one
+// thread.
+constexpr int ZETA_PMAX = 20;
+
+struct ZetaArgs {
+    int p;
+    double tau[ZETA_PMAX + 1];  // tau[0] = sigma_0, tau[m] for m = 1..p
+    double c2[ZETA_PMAX + 2];   // second-derivative stencil weights c_0 .. c_{p+1}
+};
+
+__device__ __forceinline__ void bessel01(double2 z, const HankelTable& T, double2& j0, double2& j1) {
+    double2 h0, h1, g0, g1;
+    hk::hankel01(z, T, h0, h1);
+    hk::hankel01(make_double2(z.x, -z.y), T, g0, g1);
+    j0 = make_double2(0.5 * (h0.x + g0.x), 0.5 * (h0.y - g0.y));
+    j1 = make_double2(0.5 * (h1.x + g1.x), 0.5 * (h1.y - g1.y));
+}
+
+template <int FORM>
+__global__ void zeta_band_kernel(AsmArgs a, ZetaArgs zc) {
+    const int W = 2 * zc.p + 3;
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)a.N * W) return;
+    const int N = a.N;
+    const int i = (int)(idx / W);
+    const int m = (int)(idx % W) - (zc.p + 1);
+    const int j = ((i + m) % N + N) % N;
+    const double* g = a.g;
+    const double twopi = 2.0 * PI;
+    double2 S0c = make_double2(0, 0), S1c = S0c, D0c = S0c, Ds0c = S0c, D1c = S0c, Ds1c = S0c, N0c = S0c;
+    if (m == 0) {
+        const double w = g[6 * N + i], sp = g[4 * N + i];
+        S0c = make_double2(zc.tau[0] * (-w / twopi), 0.0);
+        S1c = S0c;
+        N0c = cscale(cmul(a.k0, a.k0), zc.tau[0] * (-w / (2.0 * twopi)));
+        N0c.x += zc.c2[0] / (2.0 * a.h) / (twopi * sp);
+    } else {
+        const int am = m < 0 ? -m : m;
+        const double logw = am <= zc.p ? zc.tau[am] : 0.0;
+        const double xi = g[i], yi = g[N + i], nxi = g[2 * N + i], nyi = g[3 * N + i];
+        const double xj = g[j], yj = g[N + j], nxj = g[2 * N + j], nyj = g[3 * N + j], wj = g[6 * N + j];
+        const double dx = xi - xj, dy = yi - yj;
+        const double r = sqrt(dx * dx + dy * dy), ir = 1.0 / r;
+        const double dni = dx * nxi + dy * nyi, dnj = dx * nxj + dy * nyj, ninj = nxi * nxj + nyi * nyj;
+        const double pp = dni * dnj * ir * ir;
+        // wavenumber k0: log parts of S, D, D*, N and the full N entry
+        double2 h0, h1, j0, j1;
+        const double2 z0 = cscale(a.k0, r);
+        hk::hankel01(z0, a.T, h0, h1);
+        bessel01(z0, a.T, j0, j1);
+        const double2 c0 = cscale(a.k0, 1.0 / twopi);  // k0 / 2pi
+        const double2 AS0 = cscale(j0, -wj / twopi);
+        const double2 AD0 = cscale(cmul(c0, j1), -dnj * ir * wj);
+        const double2 ADs0 = cscale(cmul(c0, j1), dni * ir * wj);
+        double2 brJ = cscale(cmul(a.k0, j0), pp);
+        brJ = cadd(brJ, cscale(j1, (ninj - 2.0 * pp) * ir));
+        const double2 AN0 = cscale(cmul(c0, brJ), -wj);
+        double2 brH = cscale(cmul(a.k0, h0), pp);
+        brH = cadd(brH, cscale(h1, (ninj - 2.0 * pp) * ir));
+        const double2 Nfull = cscale(cmul(cscale(cmuli(a.k0), 0.25), brH), wj);
+        const double2 Nnonlog = csub(Nfull, cscale(AN0, log(am * a.h)));
+        S0c = cscale(AS0, logw);
+        D0c = cscale(AD0, logw);
+        Ds0c = cscale(ADs0, logw);
+        N0c = cadd(cscale(AN0, logw), cscale(Nnonlog, 0.5 * zc.c2[am] * (double)am * (double)am));
+        // wavenumber k1: log parts of S and D* (mixed) or D (ordinary)
+        if (logw != 0.0) {
+            bessel01(cscale(a.k1, r), a.T, j0, j1);
+            const double2 c1 = cscale(a.k1, 1.0 / twopi);
+            S1c = cscale(j0, -wj / twopi * logw);
+            D1c = cscale(cmul(c1, j1), -dnj * ir * wj * logw);
+            Ds1c = cscale(cmul(c1, j1), dni * ir * wj * logw);
+        }
+    }
+    const double2 M31 = cadd(D0c, cmul(a.beta, N0c));
+    const double2 M32 = cneg(cmul(a.eps0, cadd(S0c, cmul(a.beta, Ds0c))));
+    double2 out[4];
+    if (FORM == BM_MIXED) {
+        out[0] = cneg(S1c);
+        out[1] = cneg(cdiv(Ds1c, a.eps1));
+        out[2] = M31;
+        out[3] = M32;
+    } else {
+        out[0] = M31;
+        out[1] = M32;
+        out[2] = D1c;
+        out[3] = cneg(cmul(a.eps1, S1c));
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        double2* e = a.o[b] + (long)i + (long)j * a.ld[b];
+        *e = cadd(*e, out[b]);
+    }
+}
+
+// zeta(s), s >= 3 odd, by Euler-Maclaurin summation with 11 terms and 7 Bernoulli corrections
+double zeta_odd(int s) {
+    const int M = 12;
+    double sum = 0.0;
+    for (int n = M - 1; n >= 1; --n) sum += std::pow((double)n, -s);
+    const double Ms = std::pow((double)M, -s);
+    sum += M * Ms / (s - 1) + 0.5 * Ms;
+    const double B[7] = {1.0 / 6, -1.0 / 30, 1.0 / 42, -1.0 / 30, 5.0 / 66, -691.0 / 2730, 7.0 / 6};
+    double fact = 1.0, rising = s, Mp = Ms / M;
+    for (int j = 1; j <= 7; ++j) {
+        fact *= (2.0 * j - 1) * (2.0 * j);
+        sum += B[j - 1] / fact * rising * Mp;
+        rising *= (s + 2.0 * j - 1) * (s + 2.0 * j);
+        Mp /= (double)M * M;
+    }
+    return sum;
+}
+
+// Weights of the correction: tau_m solve sum_m (tau_m m^2) (m^2)^k = zeta'(-2(k+1)), k = 0..p-1,
+// a Vandermonde system in the nodes m^2 solved by the Bjorck-Pereyra algorithm (accurate to
+// rounding for positive increasing nodes); c_m is the closed form of the central second-derivative
+// stencil of half-width q: c_m = 2 (-1)^(m+1) (q!)^2 / (m^2 (q-m)! (q+m)!), c_0 = -2 sum c_m.
+ZetaArgs zeta_weights(int p) {
+    ZetaArgs z{};
+    z.p = p;
+    std::vector<double> x(p), b(p);
+    for (int m = 1; m <= p; ++m) x[m - 1] = (double)m * m;
+    double f2k = 1.0, tp2k = 1.0;  // (2k)!, (2 pi)^(2k)
+    for (int k = 1; k <= p; ++k) {
+        f2k *= (2.0 * k - 1) * (2.0 * k);
+        tp2k *= 4.0 * PI * PI;
+        b[k - 1] = ((k % 2) ? -1.0 : 1.0) * f2k * zeta_odd(2 * k + 1) / (2.0 * tp2k);
+    }
+    const int n = p - 1;
+    for (int k = 0; k < n; ++k)
+        for (int i = n; i > k; --i) b[i] -= x[k] * b[i - 1];
+    for (int k = n - 1; k >= 0; --k) {
+        for (int i = k + 1; i <= n; ++i) b[i] /= (x[i] - x[i - k - 1]);
+        for (int i = k; i < n; ++i) b[i] -= b[i + 1];
+    }
+    double sum = 0.0;
+    for (int m = 1; m <= p; ++m) {
+        z.tau[m] = b[m - 1] / x[m - 1];
+        sum += z.tau[m];
+    }
+    z.tau[0] = -2.0 * sum;
+    const int q = p + 1;
+    double fq = 1.0;
+    for (int t = 2; t <= q; ++t) fq *= t;
+    double csum = 0.0;
+    for (int m = 1; m <= q; ++m) {
+        double den = (double)m * m;
+        for (int t = 2; t <= q - m; ++t) den *= t;
+        for (int t = 2; t <= q + m; ++t) den *= t;
+        z.c2[m] = 2.0 * ((m % 2) ? 1.0 : -1.0) * fq * fq / den;
+        csum += z.c2[m];
+    }
+    z.c2[0] = -2.0 * csum;
+    return z;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------------
@@ -489,6 +667,44 @@ cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c) {
         if (e != cudaSuccess) return e;
         assemble_kernel<BM_ORDINARY><<<(unsigned)nblk, blk, smem, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zeta_band(cudaStream_t s, const bm_ctx* c) {
+    const int p = c->zeta_p;
+    if (p <= 0) return cudaSuccess;
+    AsmArgs a{};
+    a.N = c->N;
+    a.h = 2.0 * PI / c->N;
+    a.k0 = c->k0;
+    a.k1 = c->k1;
+    a.eps0 = c->eps0;
+    a.eps1 = c->eps1;
+    a.beta = c->beta;
+    a.T = c->htab;
+    a.g = c->d_geom;
+    long N = c->N;
+    if (c->form == BM_MIXED) {
+        a.o[0] = c->d_Mtop;
+        a.o[1] = c->d_Mtop + N;
+        a.o[2] = c->d_Mbot;
+        a.o[3] = c->d_Mbot + N * c->ldbot;
+        a.ld[0] = a.ld[1] = c->ldtop;
+        a.ld[2] = a.ld[3] = c->ldbot;
+    } else {
+        a.o[0] = c->d_A;
+        a.o[1] = c->d_A + N * c->ldA;
+        a.o[2] = c->d_A + N;
+        a.o[3] = c->d_A + N + N * c->ldA;
+        a.ld[0] = a.ld[1] = a.ld[2] = a.ld[3] = c->ldA;
+    }
+    const ZetaArgs z = zeta_weights(p);
+    const long total = N * (2L * p + 3);
+    const unsigned grid = (unsigned)ceil_div(total, 128);
+    if (c->form == BM_MIXED)
+        zeta_band_kernel<BM_MIXED><<<grid, 128, 0, s>>>(a, z);
+    else
+        zeta_band_kernel<BM_ORDINARY><<<grid, 128, 0, s>>>(a, z);
     return cudaGetLastError();
 }
 

@@ -178,6 +178,7 @@ struct bm_ctx {
     int refine_maxit = 30;
     int resid_mode = BM_RESID_DF_UPDATE;
     int nb = 0;
+    int zeta_p = 0;  // high-order zeta correction points (0: the one-point rule)
 
     // geometry (device, SoA of N each): x, y, nx, ny, speed, kappa, w
     double* d_geom = nullptr;

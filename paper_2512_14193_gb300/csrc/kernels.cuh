@@ -5,6 +5,7 @@
 // assemble.cu
 cudaError_t launch_geometry(cudaStream_t s, int kind, const double p[4], int N, const double* d_user, double* d_geom);
 cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c);
+cudaError_t launch_zeta_band(cudaStream_t s, const bm_ctx* c);  // high-order zeta corrections (zeta_p > 0)
 cudaError_t launch_normA(cudaStream_t s, const bm_ctx* c);
 cudaError_t launch_plane_wave(cudaStream_t s, const bm_ctx* c, const double* d_ang, int nrhs, double2* B, long ldb);
 cudaError_t launch_far_field(cudaStream_t s, const bm_ctx* c, const double2* X, long ldx, int nrhs, const double* d_ang,
