@@ -174,6 +174,20 @@ bm_status bm_rhs_plane_wave(bm_ctx* ctx, const double* angles, int nrhs, bm_c64*
 bm_status bm_solve(bm_ctx* ctx, int nrhs, const bm_c64* B, int ldb, bm_c64* X, int ldx,
                    int on_device, bm_solve_info* info);
 
+/* Solve the mixed system for the block-diagonal right-hand side diag(B1, B2, B3) of Corollary
+ * lem:block_LU (§4.1, toward the leaf level of a fast direct solver): B1, B2, B3 are N x c1,
+ * N x c2, N x c3 (ld >= N; a block with c = 0 may be NULL), X is 3N x (c1 + c2 + c3) (ldx >= 3N):
+ *   X = [ B1 - M13 Z31   -M13 Z32        -M13 Z33 ]    Z31 = -U33^{-1} M31 B1
+ *       [ -M23 Z31       B2 - M23 Z32    -M23 Z33 ]    Z32 = -U33^{-1} M32 B2
+ *       [ Z31            Z32             Z33      ]    Z33 =  U33^{-1} B3,  U33 = -M31 M13 - M32 M23,
+ * which is the Corollary lem:for_ssm_RHS solve of the block-diagonal columns: it runs as bm_solve
+ * on them (same precision and refinement; info as bm_solve's).  B and X on the host or (on_device)
+ * the device.  The device form stages the 3N x (c1 + c2 + c3) right-hand side in a buffer charged
+ * to the HBM budget.  Errors: BM_ESTATE (not factored, or the ordinary formulation), BM_EINVAL,
+ * BM_ENOMEM, and those of bm_solve. */
+bm_status bm_solve_block(bm_ctx* ctx, int c1, const bm_c64* B1, int ld1, int c2, const bm_c64* B2, int ld2, int c3,
+                         const bm_c64* B3, int ld3, bm_c64* X, int ldx, int on_device, bm_solve_info* info);
+
 /* Far-field pattern of solutions X (nrhs columns, as returned by bm_solve) at M observation
  * angles: u_inf(xhat) = e^{i pi/4}/sqrt(8 pi k0) sum_j w_j [-i k0 (xhat.nu_j) u_j - eps0 q_j]
  * exp(-i k0 xhat.x_j), from the exterior Green representation of the total field

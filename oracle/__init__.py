@@ -34,7 +34,8 @@ from .geometry import Geometry, nodes
 from .operators import hankel01, layer_operators, layer_entries
 from .systems import (Params, default_params, mixed_blocks, mixed_matrix, ordinary_matrix, incident, rhs_plane_wave,
                       mixed_rows, ordinary_rows)
-from .dense import lu_factor, lu_solve, dense_solve, schur_solve, mixed_residual, backward_error_mixed, backward_error_dense
+from .dense import (lu_factor, lu_solve, dense_solve, schur_solve, block_rhs_solve, mixed_residual,
+                    backward_error_mixed, backward_error_dense)
 from .mie import mie_coefficients, mie_boundary, mie_far_field
 from .farfield import far_field
 
@@ -42,6 +43,6 @@ __all__ = [
     "Geometry", "nodes", "hankel01", "layer_operators", "layer_entries", "Params", "default_params",
     "mixed_blocks", "mixed_matrix", "ordinary_matrix", "mixed_rows", "ordinary_rows", "incident", "rhs_plane_wave",
     "lu_factor",
-    "lu_solve", "dense_solve", "schur_solve", "mixed_residual", "backward_error_mixed",
+    "lu_solve", "dense_solve", "schur_solve", "block_rhs_solve", "mixed_residual", "backward_error_mixed",
     "backward_error_dense", "mie_coefficients", "mie_boundary", "mie_far_field", "far_field",
 ]

@@ -91,6 +91,26 @@ def schur_solve(blocks, B: np.ndarray, factor=None) -> np.ndarray:
     return X[:, 0] if vec else X
 
 
+def block_rhs_solve(blocks, B1: np.ndarray, B2: np.ndarray, B3: np.ndarray, factor=None) -> np.ndarray:
+    """Solution for the block-diagonal right-hand side diag(B1, B2, B3), Corollary lem:block_LU:
+    Z31 = -U33^{-1} M31 B1, Z32 = -U33^{-1} M32 B2, Z33 = U33^{-1} B3, then
+    X = [[B1 - M13 Z31, -M13 Z32, -M13 Z33], [-M23 Z31, B2 - M23 Z32, -M23 Z33], [Z31, Z32, Z33]]."""
+    M13, M23, M31, M32 = blocks
+    N = M13.shape[0]
+    B1, B2, B3 = (np.zeros((N, 0), np.complex128) if B is None else np.asarray(B, np.complex128).reshape(N, -1)
+                  for B in (B1, B2, B3))
+    if factor is None:
+        factor = lu_factor(schur_complement(blocks))
+    LU, piv = factor
+    Z31 = -lu_solve(LU, piv, M31 @ B1)
+    Z32 = -lu_solve(LU, piv, M32 @ B2)
+    Z33 = lu_solve(LU, piv, B3)
+    top = np.concatenate([B1 - M13 @ Z31, -M13 @ Z32, -M13 @ Z33], 1)
+    mid = np.concatenate([-M23 @ Z31, B2 - M23 @ Z32, -M23 @ Z33], 1)
+    bot = np.concatenate([Z31, Z32, Z33], 1)
+    return np.concatenate([top, mid, bot], 0)
+
+
 def mixed_residual(blocks, X: np.ndarray, B: np.ndarray) -> np.ndarray:
     """r = b - A x using the block structure of Eq. dis_mixedBM (identity/zero blocks not stored)."""
     M13, M23, M31, M32 = blocks

@@ -100,6 +100,7 @@ def lib():
     L.bm_factor.argtypes = [P, C.POINTER(I)]
     L.bm_rhs_plane_wave.argtypes = [P, C.POINTER(D), I, P, I, I]
     L.bm_solve.argtypes = [P, I, P, I, P, I, I, C.POINTER(bm_solve_info)]
+    L.bm_solve_block.argtypes = [P, I, P, I, I, P, I, I, P, I, P, I, I, C.POINTER(bm_solve_info)]
     L.bm_far_field.argtypes = [P, P, I, I, C.POINTER(D), I, P, I, I]
     L.bm_far_field_static.argtypes = [P, P, I, I, C.POINTER(D), I, P, I]
     L.bm_copy_block.argtypes = [P, I, P, I, I]
@@ -121,7 +122,8 @@ def lib():
     L.bm_strerror.restype = C.c_char_p
     L.bm_last_error.argtypes = []
     L.bm_last_error.restype = C.c_char_p
-    for name in ("bm_create", "bm_assemble", "bm_factor", "bm_rhs_plane_wave", "bm_solve", "bm_far_field",
+    for name in ("bm_create", "bm_assemble", "bm_factor", "bm_rhs_plane_wave", "bm_solve", "bm_solve_block",
+                 "bm_far_field",
                  "bm_far_field_static", "bm_ssm", "bm_server_create", "bm_server_submit", "bm_server_wait",
                  "bm_server_stats_get", "bm_server_destroy",
                  "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_memory", "bm_destroy",
@@ -242,6 +244,28 @@ def bm_solve(h, B, X, raise_on_notconv: bool = True) -> bm_solve_info:
     info = bm_solve_info()
     st = lib().bm_solve(h, nb, pb, ldb, px, ldx, devb, C.byref(info))
     _check(st, "bm_solve", ok=(BM_OK,) if raise_on_notconv else (BM_OK, BM_ENOTCONV))
+    return info
+
+
+def bm_solve_block(h, B1, B2, B3, X, raise_on_notconv: bool = True) -> bm_solve_info:
+    """X = solution for the block-diagonal right-hand side diag(B1, B2, B3) (Corollary lem:block_LU);
+    a block may be None (no columns).  All on the host or all CUDA tensors."""
+    args, keep, sides = [], [], set()
+    for B in (B1, B2, B3):
+        if B is None:
+            args += [0, None, 1]
+            continue
+        p, ld, n, dev, k = _colmajor(B, 0, writable=False)
+        args += [n, p, ld]
+        keep.append(k)
+        sides.add(dev)
+    px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=True)
+    sides.add(devx)
+    if len(sides) != 1:
+        raise ValueError("B1, B2, B3 and X must all live on the same side")
+    info = bm_solve_info()
+    st = lib().bm_solve_block(h, *args, px, ldx, devx, C.byref(info))
+    _check(st, "bm_solve_block", ok=(BM_OK,) if raise_on_notconv else (BM_OK, BM_ENOTCONV))
     return info
 
 

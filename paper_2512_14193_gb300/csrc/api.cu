@@ -917,6 +917,56 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
     return st;
 }
 
+// Corollary lem:block_LU: the block-diagonal right-hand side diag(B1, B2, B3) solved as its 3N
+// columns by the Corollary lem:for_ssm_RHS path of bm_solve.
+extern "C" bm_status bm_solve_block(bm_ctx* c, int c1, const bm_c64* B1, int ld1, int c2, const bm_c64* B2, int ld2,
+                                    int c3, const bm_c64* B3, int ld3, bm_c64* X, int ldx, int on_device,
+                                    bm_solve_info* info) {
+    if (c == nullptr || X == nullptr) return BM_EINVAL;
+    if (!c->assembled || c->form != BM_MIXED) return BM_ESTATE;
+    const int N = c->N;
+    const int cs[3] = {c1, c2, c3};
+    const bm_c64* Bs[3] = {B1, B2, B3};
+    const int lds[3] = {ld1, ld2, ld3};
+    long C = 0;
+    for (int b = 0; b < 3; ++b) {
+        if (cs[b] < 0 || (cs[b] > 0 && (Bs[b] == nullptr || lds[b] < N))) return BM_EINVAL;
+        C += cs[b];
+    }
+    if (C < 1 || C > (1 << 20) || ldx < 3 * N) return BM_EINVAL;
+    const long ldb = 3L * N;
+    if (!on_device) {
+        std::vector<bm_c64> B((size_t)(ldb * C), bm_c64{0.0, 0.0});
+        long col = 0;
+        for (int b = 0; b < 3; ++b)
+            for (int j = 0; j < cs[b]; ++j, ++col)
+                std::memcpy(&B[(size_t)(col * ldb + (long)b * N)], Bs[b] + (size_t)j * lds[b], sizeof(bm_c64) * N);
+        return bm_solve(c, (int)C, B.data(), (int)ldb, X, ldx, 0, info);
+    }
+    bm_c64* dB = nullptr;
+    bm_status s = alloc_t(c, &dB, sizeof(bm_c64) * (size_t)(ldb * C));
+    if (s != BM_OK) return s;
+    cudaStream_t st = c->stream;
+    cudaError_t e = cudaMemsetAsync(dB, 0, sizeof(bm_c64) * (size_t)(ldb * C), st);
+    long col = 0;
+    for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
+        if (cs[b] > 0)
+            e = cudaMemcpy2DAsync(dB + col * ldb + (long)b * N, sizeof(bm_c64) * ldb, Bs[b], sizeof(bm_c64) * lds[b],
+                                  sizeof(bm_c64) * N, cs[b], cudaMemcpyDeviceToDevice, st);
+        col += cs[b];
+    }
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        ctx_free(c, dB);
+        bm_set_error(std::string("bm_solve_block staging: ") + cudaGetErrorString(e));
+        return BM_ECUDA;
+    }
+    s = bm_solve(c, (int)C, dB, (int)ldb, X, ldx, 1, info);
+    cudaStreamSynchronize(st);
+    ctx_free(c, dB);
+    return s;
+}
+
 // ------------------------------------------------------------------------------------------------
 extern "C" bm_status bm_rhs_plane_wave(bm_ctx* c, const double* angles, int nrhs, bm_c64* B, int ldb, int on_device) {
     if (c == nullptr || angles == nullptr || B == nullptr || nrhs < 1) return BM_EINVAL;

@@ -84,3 +84,21 @@ def test_backward_error_definition():
     Xp[0, 0] += 1e-6
     eta = O.backward_error_dense(A, Xp, B)
     assert 1e-9 < eta < 1e-6
+
+
+def test_block_rhs_corollary_equals_dense_3N():
+    # Corollary lem:block_LU against LAPACK on the full 3N matrix with the block-diagonal
+    # right-hand side diag(B1, B2, B3) (widths 2, 3, 1), and with an empty block
+    N = 40
+    g = O.nodes(W.star(1.0, 0.25, 4), N)
+    blocks = O.mixed_blocks(g, O.default_params(3.0 - 0.1j, 4.5))
+    A = O.mixed_matrix(blocks)
+    B1, B2, B3 = _rand(N, 2, seed=11), _rand(N, 3, seed=12), _rand(N, 1, seed=13)
+    Bd = np.zeros((3 * N, 6), dtype=complex)
+    Bd[:N, :2], Bd[N:2 * N, 2:5], Bd[2 * N:, 5:] = B1, B2, B3
+    X = O.block_rhs_solve(blocks, B1, B2, B3)
+    Xr = np.linalg.solve(A, Bd)
+    assert X.shape == (3 * N, 6)
+    assert np.linalg.norm(X - Xr) / np.linalg.norm(Xr) < 1e-12
+    X2 = O.block_rhs_solve(blocks, None, B2, B3)
+    assert np.linalg.norm(X2 - Xr[:, 2:]) / np.linalg.norm(Xr[:, 2:]) < 1e-12
