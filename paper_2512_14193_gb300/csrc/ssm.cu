@@ -201,6 +201,10 @@ extern "C" bm_status bm_ssm(int device, const bm_curve* curve, int N, bm_formula
                      "cap >= L M)");
         return BM_EINVAL;
     }
+    if (opts && (opts->zeta_p < 0 || opts->zeta_p > 20 || (opts->zeta_p > 0 && N < 2 * opts->zeta_p + 3))) {
+        bm_set_error("bm_ssm: zeta_p must be in [0, 20] with N >= 2 zeta_p + 3");
+        return BM_EINVAL;
+    }
     if (!std::isfinite(so.center.re) || !std::isfinite(so.center.im) || !std::isfinite(so.k_ratio.re) ||
         !std::isfinite(so.k_ratio.im))
         return BM_ENONFINITE;

@@ -88,3 +88,33 @@ def test_contour_and_server_argument_checks_need_no_gpu(bmlib):
     assert bmlib.lib().bm_server_create(ctypes.byref(srv), 0, ctypes.byref(o)) == bmlib.BM_EINVAL
     o.slots = 33
     assert bmlib.lib().bm_server_create(ctypes.byref(srv), 0, ctypes.byref(o)) == bmlib.BM_EINVAL
+
+
+def test_zeta_order_and_block_solve_argument_checks_need_no_gpu(bmlib):
+    # the quadrature order is checked before any device work (bm_ssm validates its bm_opts), and
+    # bm_solve_block rejects a missing handle
+    import ctypes
+    import numpy as np
+    cv = bmlib.bm_curve()
+    cv.kind = bmlib.BM_CURVE_CIRCLE
+    cv.p[0] = 0.5
+    so = bmlib.bm_ssm_opts()
+    so.center = bmlib.bm_c64(0.43, -1.28)
+    so.radius = 0.05
+    so.npoints = 32
+    so.nmoments = 4
+    so.k_ratio = bmlib.bm_c64(2.0, 0.0)
+    N, L = 64, 4
+    V = np.zeros((3 * N, L), dtype=np.complex128, order="F")
+    om = np.zeros(L * 4, dtype=np.complex128)
+    info = bmlib.bm_ssm_info()
+    for p in (-1, 21, 31):                        # 31: N = 64 < 2 p + 3
+        o = bmlib.make_opts(zeta_p=p)
+        st = bmlib.lib().bm_ssm(0, ctypes.byref(cv), N, bmlib.BM_MIXED, ctypes.byref(o), ctypes.byref(so),
+                                ctypes.c_void_p(V.ctypes.data), 3 * N, L, ctypes.c_void_p(om.ctypes.data), L * 4,
+                                None, ctypes.byref(info))
+        assert st == bmlib.BM_EINVAL, p
+    X = np.zeros((3 * N, 1), dtype=np.complex128, order="F")
+    st = bmlib.lib().bm_solve_block(None, 1, ctypes.c_void_p(X.ctypes.data), 3 * N, 0, None, 1, 0, None, 1,
+                                    ctypes.c_void_p(X.ctypes.data), 3 * N, 0, None)
+    assert st == bmlib.BM_EINVAL
