@@ -176,3 +176,20 @@ def test_order_31_rule_reproduces_the_paper_table():
         assert inside.size == 2
         assert np.abs(inside - target).max() < 6e-11          # the table's 10 printed digits
         assert np.abs(inside - tab[key]).max() < 2e-11        # the paper's computed value
+
+
+@pytest.mark.parametrize("p,order", [(0, 1), (3, 9)])
+def test_calderon_identities_on_the_ellipse(p, order):
+    # Calderon relations (§2.2): S N = D^2 - I/4 and N S = D*^2 - I/4 for the same wavenumber.
+    # Applied to a smooth density the discrete defect vanishes at the rule's order (O(h) with the
+    # one-point rule, whose N is first order; O(h^(2p+3)) with the corrections), which ties N to S
+    # and D on a non-circular curve.
+    errs = []
+    for N in (64, 128, 256):
+        g = O.nodes(W.ellipse(1.0, 0.6), N)
+        o = O.layer_operators(g, 2.0 + 0.1j, p)
+        phi = np.exp(2j * g.t) * (1 + 0.3 * np.cos(3 * g.t))
+        d1 = np.abs(o["S"] @ (o["N"] @ phi) - (o["D"] @ (o["D"] @ phi) - 0.25 * phi)).max()
+        d2 = np.abs(o["N"] @ (o["S"] @ phi) - (o["Ds"] @ (o["Ds"] @ phi) - 0.25 * phi)).max()
+        errs.append(max(d1, d2) / np.abs(phi).max())
+    assert min(_order(errs)) > order - 0.3, errs
