@@ -188,6 +188,12 @@ bm_status bm_solve(bm_ctx* ctx, int nrhs, const bm_c64* B, int ldb, bm_c64* X, i
 bm_status bm_solve_block(bm_ctx* ctx, int c1, const bm_c64* B1, int ld1, int c2, const bm_c64* B2, int ld2, int c3,
                          const bm_c64* B3, int ld3, bm_c64* X, int ldx, int on_device, bm_solve_info* info);
 
+/* Diagnostic (host only, no GPU needed): the weights of the high-order zeta corrections for
+ * zeta_p = p (1..20), as bm_assemble uses them.  tau[0..p]: tau[0] = sigma_0 = -2 sum tau_m (the
+ * diagonal's log weight beyond ln(h/2pi)), tau[m] the log-part weight at offset +-m; c2[0..p+1]:
+ * the central second-derivative stencil applied to N's x^-2 part.  Errors: BM_EINVAL. */
+bm_status bm_zeta_weights(int p, double* tau, double* c2);
+
 /* Far-field pattern of solutions X (nrhs columns, as returned by bm_solve) at M observation
  * angles: u_inf(xhat) = e^{i pi/4}/sqrt(8 pi k0) sum_j w_j [-i k0 (xhat.nu_j) u_j - eps0 q_j]
  * exp(-i k0 xhat.x_j), from the exterior Green representation of the total field

@@ -112,6 +112,7 @@ def lib():
     L.bm_ssm.argtypes = [I, C.POINTER(bm_curve), I, I, C.POINTER(bm_opts), C.POINTER(bm_ssm_opts), P, I, I, P, I,
                          C.POINTER(D), C.POINTER(bm_ssm_info)]
     L.bm_hankel01.argtypes = [P, P, I, P, P, I]
+    L.bm_zeta_weights.argtypes = [I, C.POINTER(D), C.POINTER(D)]
     L.bm_hankel_anchor_table.argtypes = [C.POINTER(D), I, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(D),
                                          C.POINTER(D)]
     L.bm_memory.argtypes = [P, C.POINTER(S), C.POINTER(S)]
@@ -126,7 +127,8 @@ def lib():
                  "bm_far_field",
                  "bm_far_field_static", "bm_ssm", "bm_server_create", "bm_server_submit", "bm_server_wait",
                  "bm_server_stats_get", "bm_server_destroy",
-                 "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_memory", "bm_destroy",
+                 "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_zeta_weights", "bm_memory",
+                 "bm_destroy",
                  "bm_kernel_launches", "bm_enqueue_probe"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -383,6 +385,15 @@ def bm_hankel01(h, z):
     _check(lib().bm_hankel01(h, C.c_void_p(zz.ctypes.data), int(zz.size), C.c_void_p(h0.ctypes.data),
                              C.c_void_p(h1.ctypes.data), 0), "bm_hankel01")
     return h0, h1
+
+
+def bm_zeta_weights(p: int):
+    """(tau[0..p], c2[0..p+1]): the library's high-order zeta correction weights (host only)."""
+    tau = np.zeros(p + 1)
+    c2 = np.zeros(p + 2)
+    _check(lib().bm_zeta_weights(int(p), tau.ctypes.data_as(C.POINTER(C.c_double)),
+                                 c2.ctypes.data_as(C.POINTER(C.c_double))), "bm_zeta_weights")
+    return tau, c2
 
 
 def bm_hankel_anchor_table():

@@ -708,6 +708,15 @@ cudaError_t launch_zeta_band(cudaStream_t s, const bm_ctx* c) {
     return cudaGetLastError();
 }
 
+// Host diagnostic: the correction weights the band kernel uses (no device work).
+extern "C" bm_status bm_zeta_weights(int p, double* tau, double* c2) {
+    if (p < 1 || p > ZETA_PMAX || tau == nullptr || c2 == nullptr) return BM_EINVAL;
+    const ZetaArgs z = zeta_weights(p);
+    for (int m = 0; m <= p; ++m) tau[m] = z.tau[m];
+    for (int m = 0; m <= p + 1; ++m) c2[m] = z.c2[m];
+    return BM_OK;
+}
+
 cudaError_t launch_normA(cudaStream_t s, const bm_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->d_normA, 0, sizeof(double), s);
     if (e != cudaSuccess) return e;

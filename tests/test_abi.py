@@ -1,9 +1,11 @@
 """CPU checks of the C-ABI library: it builds, loads, exports every symbol include/bm.h declares,
-and its host-built Hankel anchor table matches scipy (no GPU needed for any of this)."""
+its host-built Hankel anchor table matches scipy and its high-order zeta weights match the
+oracle's, and its argument checks run before any device work (no GPU needed for any of this)."""
 import os
 import re
 
 import numpy as np
+import pytest
 from scipy import special as sp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -118,3 +120,20 @@ def test_zeta_order_and_block_solve_argument_checks_need_no_gpu(bmlib):
     st = bmlib.lib().bm_solve_block(None, 1, ctypes.c_void_p(X.ctypes.data), 3 * N, 0, None, 1, 0, None, 1,
                                     ctypes.c_void_p(X.ctypes.data), 3 * N, 0, None)
     assert st == bmlib.BM_EINVAL
+
+
+def test_library_zeta_weights_match_the_oracle(bmlib):
+    # the library builds the high-order correction weights on the host with a construction of its
+    # own (Euler-Maclaurin zeta(2k+1), Bjorck-Pereyra Vandermonde solve, closed-form stencil);
+    # the oracle's come from scipy's zeta and exact rational elimination
+    import numpy as np
+    from oracle import zeta
+    for p in (1, 2, 5, 14, 20):
+        tau, c2 = bmlib.bm_zeta_weights(p)
+        ref_tau = np.array(zeta.log_weights(p))
+        assert np.abs(tau[1:] - ref_tau).max() <= 1e-14 * np.abs(ref_tau).max()
+        assert abs(tau[0] + 2 * ref_tau.sum()) <= 1e-14
+        ref_c2 = np.array(zeta.second_derivative_weights(p + 1))
+        assert np.abs(c2 - ref_c2).max() <= 1e-13 * np.abs(ref_c2).max()
+    with pytest.raises(bmlib.BMError):
+        bmlib.bm_zeta_weights(21)
