@@ -19,7 +19,8 @@ for Helmholtz transmission problems"), cited in its docstring:
 * ``systems``   - the 3N mixed system (Eq. dis_mixedBM, Theorem thm:LU blocks)
                   and the 2N ordinary system (Eq. dis_BM)
 * ``dense``     - unblocked LU with partial pivoting, the Schur path of
-                  Theorem thm:LU / Corollary lem:for_ssm_RHS, backward error
+                  Theorem thm:LU / Corollary lem:for_ssm_RHS, the block-diagonal
+                  right-hand sides of Corollary lem:block_LU, backward error
 * ``mie``       - Bessel-series solution on a circle (§5.1 analytical solution)
 * ``farfield``  - far-field pattern from boundary data
 
