@@ -105,7 +105,21 @@ typedef struct {
  *  parts of S, D, D*, N; the two-term expansion of N's x^-2 part with a central second-derivative
  *  stencil) on the 2 zeta_p + 1 (log parts) and 2 zeta_p + 3 (N) nodes around each diagonal, for
  *  an O(h^(2 zeta_p + 3)) rule.  Needs N >= 2 zeta_p + 3, and |arg k| <= 60 degrees for both
- *  wavenumbers unless |k| (zeta_p + 1) h max|x'| < 2.9 (BM_EINVAL otherwise). */
+ *  wavenumbers unless |k| (zeta_p + 1) h max|x'| < 2.9 (BM_EINVAL otherwise).
+ * Launch and diagnostic settings (0 selects the default for each; none changes a result beyond
+ * rounding order, except test_wait_timeout):
+ *  eager             : 1 launches every kernel of bm_factor and of the refinement corrections directly
+ *                      instead of replaying the CUDA graphs captured on first use (for profilers that
+ *                      cannot replay graph-captured cluster launches).
+ *  panel_cluster_max : cap on the CTAs of one LU panel cluster, 1 .. 16 (0: as many as the device
+ *                      co-schedules).  Fewer CTAs put more rows on each thread.
+ *  panel_kernel      : 0 runs FP32 panels on the lane-per-column kernel wherever it fits; 1 keeps them
+ *                      on the register-row kernel (the kernel the FP64 path always uses).
+ *  test_wait_timeout : test hook for the device-wait error path.  1 makes every tensor-core product
+ *                      wait on a barrier that nothing completes; the wait gives up after about 1 ms,
+ *                      the product skips its output and bm_factor returns BM_ETIMEOUT (the FP64
+ *                      precision, which has no tensor-core product, is unaffected).  Nothing is left
+ *                      running on the device, and the handle stays usable after a new bm_assemble. */
 typedef struct {
     double eps0;
     bm_c64 eps1;
@@ -118,6 +132,10 @@ typedef struct {
     int nb;
     int refine_residual;
     int zeta_p;
+    int eager;
+    int panel_cluster_max;
+    int panel_kernel;
+    int test_wait_timeout;
 } bm_opts;
 
 typedef enum { BM_RESID_DF_UPDATE = 0, BM_RESID_FP64_UPDATE = 1, BM_RESID_FP64_ALL = 2 } bm_refine_residual;
@@ -198,7 +216,8 @@ bm_status bm_zeta_weights(int p, double* tau, double* c2);
  * angles: u_inf(xhat) = e^{i pi/4}/sqrt(8 pi k0) sum_j w_j [-i k0 (xhat.nu_j) u_j - eps0 q_j]
  * exp(-i k0 xhat.x_j), from the exterior Green representation of the total field
  * (section 3.1), normalised so that u_sc ~ e^{i k0 r} r^{-1/2} u_inf.  Uinf is M x nrhs,
- * column-major, ldu >= M.  angles is a host array. */
+ * column-major, ldu >= M.  angles is a host array.  Errors: BM_EINVAL, BM_ESTATE, BM_ENONFINITE (an
+ * angle is not finite), BM_ENOMEM, BM_ECUDA. */
 bm_status bm_far_field(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const double* angles,
                        int M, bm_c64* Uinf, int ldu, int on_device);
 
@@ -214,12 +233,13 @@ bm_status bm_far_field(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const do
  *  Uinf : device array, M x nrhs column-major output (ldu >= M), fully overwritten.
  *  angles: host array of M observation angles (radians), 1 <= M <= BM_FAR_FIELD_STATIC_MAX_ANGLES.
  * Nothing in the fixed array needs to start at zero: each call writes the M angles it reads.
- * The first call on a device looks up the array's device address once for that device; make it
- * before any stream capture starts on the device.  The array is shared by all handles and threads
+ * The first call on a device looks up the array's device address once for that device (and again
+ * after the device's context has been replaced, e.g. by cudaDeviceReset); make it before any
+ * stream capture starts on the device.  The array is shared by all handles and threads
  * on a device: calls that overlap in time race on it.  The call waits for the handle's stream
  * before it returns, so calls made one after another are safe.
  * Errors: BM_EINVAL (M above the limit - bm_last_error says so -, bad sizes or pointers),
- * BM_ESTATE (nothing assembled), BM_ECUDA. */
+ * BM_ENONFINITE (an angle is not finite), BM_ESTATE (nothing assembled), BM_ECUDA. */
 #define BM_FAR_FIELD_STATIC_MAX_ANGLES 8192
 bm_status bm_far_field_static(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, const double* angles,
                               int M, bm_c64* Uinf, int ldu);

@@ -39,7 +39,8 @@ class bm_curve(C.Structure):
 class bm_opts(C.Structure):
     _fields_ = [("eps0", C.c_double), ("eps1", bm_c64), ("beta", bm_c64), ("eps_set", C.c_int),
                 ("beta_set", C.c_int), ("prec", C.c_int), ("refine_tol", C.c_double), ("refine_maxit", C.c_int),
-                ("nb", C.c_int), ("refine_residual", C.c_int), ("zeta_p", C.c_int)]
+                ("nb", C.c_int), ("refine_residual", C.c_int), ("zeta_p", C.c_int), ("eager", C.c_int),
+                ("panel_cluster_max", C.c_int), ("panel_kernel", C.c_int), ("test_wait_timeout", C.c_int)]
 
 
 class bm_solve_info(C.Structure):
@@ -141,6 +142,20 @@ def _check(st: int, where: str, ok=(BM_OK,)):
     return st
 
 
+# rows of the assembled system per handle (3N mixed, 2N ordinary), for the shape checks below: the
+# library sees leading dimensions only, so an array with too few rows or columns must be caught here
+_nsys = {}
+
+
+def _hkey(h) -> int:
+    return int(h.value) if isinstance(h, C.c_void_p) and h.value is not None else id(h)
+
+
+def _need(cond: bool, msg: str) -> None:
+    if not cond:
+        raise ValueError(msg)
+
+
 def _c64(z) -> bm_c64:
     z = complex(z)
     return bm_c64(z.real, z.imag)
@@ -187,13 +202,19 @@ def bm_create(device: int = 0, stream: int | None = None, budget_bytes: int = 0)
 
 
 def bm_destroy(h) -> None:
+    _nsys.pop(_hkey(h), None)
     _check(lib().bm_destroy(h), "bm_destroy")
 
 
 def make_opts(prec: int = BM_FP64, eps0: float = 1.0, eps1=None, beta=None, refine_tol: float = 1e-9,
-              refine_maxit: int = 30, nb: int = 0, residual: int = 0, zeta_p: int = 0) -> bm_opts:
+              refine_maxit: int = 30, nb: int = 0, residual: int = 0, zeta_p: int = 0, eager: bool = False,
+              panel_cluster_max: int = 0, panel_kernel: int = 0, test_wait_timeout: bool = False) -> bm_opts:
     o = bm_opts()
     o.zeta_p = int(zeta_p)
+    o.eager = int(bool(eager))
+    o.panel_cluster_max = int(panel_cluster_max)
+    o.panel_kernel = int(panel_kernel)
+    o.test_wait_timeout = int(bool(test_wait_timeout))
     o.eps0 = float(eps0)
     o.prec = int(prec)
     o.refine_tol = float(refine_tol)
@@ -222,6 +243,7 @@ def bm_assemble(h, kind: int, params, N: int, k_out, k_in, formulation: int = BM
         cv.user = keep.ctypes.data_as(C.POINTER(C.c_double))
     _check(lib().bm_assemble(h, C.byref(cv), int(N), _c64(k_out), _c64(k_in), int(formulation),
                              C.byref(opts) if opts is not None else None), "bm_assemble")
+    _nsys[_hkey(h)] = (3 if int(formulation) == BM_MIXED else 2) * int(N)
 
 
 def bm_factor(h) -> int:
@@ -234,6 +256,8 @@ def bm_factor(h) -> int:
 def bm_rhs_plane_wave(h, angles, B) -> None:
     ang = np.ascontiguousarray(angles, dtype=np.float64)
     ptr, ld, ncols, dev, _keep = _colmajor(B, 0, writable=True)
+    _need(ncols >= ang.size, "B needs a column per incidence angle")
+    _need(_keep.shape[0] >= _nsys.get(_hkey(h), 0), "B has fewer rows than the system")
     _check(lib().bm_rhs_plane_wave(h, ang.ctypes.data_as(C.POINTER(C.c_double)), int(ang.size), ptr, ld, dev),
            "bm_rhs_plane_wave")
 
@@ -243,6 +267,8 @@ def bm_solve(h, B, X, raise_on_notconv: bool = True) -> bm_solve_info:
     px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=True)
     if devb != devx or nb != nx:
         raise ValueError("B and X must live on the same side and have the same number of columns")
+    ns = _nsys.get(_hkey(h), 0)
+    _need(_kb.shape[0] >= ns and _kx.shape[0] >= ns, "B and X need at least the system's rows")
     info = bm_solve_info()
     st = lib().bm_solve(h, nb, pb, ldb, px, ldx, devb, C.byref(info))
     _check(st, "bm_solve", ok=(BM_OK,) if raise_on_notconv else (BM_OK, BM_ENOTCONV))
@@ -263,6 +289,10 @@ def bm_solve_block(h, B1, B2, B3, X, raise_on_notconv: bool = True) -> bm_solve_
         sides.add(dev)
     px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=True)
     sides.add(devx)
+    _need(nx == sum(a for a in args[0::3]), "X needs one column per column of B1, B2, B3")
+    _need(_kx.shape[0] >= _nsys.get(_hkey(h), 0), "X has fewer rows than the system")
+    for B, k in zip([b for b in (B1, B2, B3) if b is not None], keep):
+        _need(k.shape[0] * 3 >= _nsys.get(_hkey(h), 0), "each block needs N rows")
     if len(sides) != 1:
         raise ValueError("B1, B2, B3 and X must all live on the same side")
     info = bm_solve_info()
@@ -271,10 +301,20 @@ def bm_solve_block(h, B1, B2, B3, X, raise_on_notconv: bool = True) -> bm_solve_
     return info
 
 
+def _far_field_shapes(h, kx, nx, ku, nu, ang) -> None:
+    # the kernel writes M x nrhs values into U and reads nrhs columns of X: U must have a column per
+    # column of X and a row per angle, X the system's rows
+    _need(nu == nx, f"U has {nu} columns for {nx} solutions")
+    _need(ku.shape[0] >= ang.size, f"U has {ku.shape[0]} rows for {ang.size} angles")
+    _need(kx.shape[0] >= _nsys.get(_hkey(h), 0), "X has fewer rows than the system")
+
+
 def bm_far_field(h, X, angles, U) -> None:
     px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=False)
     pu, ldu, nu, devu, _ku = _colmajor(U, 0, writable=True)
     ang = np.ascontiguousarray(angles, dtype=np.float64)
+    _far_field_shapes(h, _kx, nx, _ku, nu, ang)
+    _need(devx == devu, "X and U must live on the same side")
     _check(lib().bm_far_field(h, px, ldx, nx, ang.ctypes.data_as(C.POINTER(C.c_double)), int(ang.size), pu, ldu,
                               devx), "bm_far_field")
 
@@ -286,6 +326,7 @@ def bm_far_field_static(h, X, angles, U) -> None:
     if not (devx and devu):
         raise ValueError("bm_far_field_static takes device arrays only")
     ang = np.ascontiguousarray(angles, dtype=np.float64)
+    _far_field_shapes(h, _kx, nx, _ku, nu, ang)
     _check(lib().bm_far_field_static(h, px, ldx, nx, ang.ctypes.data_as(C.POINTER(C.c_double)), int(ang.size), pu,
                                      ldu), "bm_far_field_static")
 

@@ -407,6 +407,14 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
         bm_set_error("nb must be a multiple of 32 in [32, 256]");
         return BM_EINVAL;
     }
+    const int cl_cap = opts ? opts->panel_cluster_max : 0;
+    const int pkern = opts ? opts->panel_kernel : 0;
+    const bool eager = opts && opts->eager != 0;
+    const int test_wait = (opts && opts->test_wait_timeout) ? 1 : 0;
+    if (cl_cap < 0 || cl_cap > 16 || pkern < 0 || pkern > 1) {
+        bm_set_error("panel_cluster_max must be in [0, 16] and panel_kernel 0 or 1");
+        return BM_EINVAL;
+    }
     const int zeta_p = opts ? opts->zeta_p : 0;
     if (zeta_p < 0 || zeta_p > 20 || (zeta_p > 0 && N < 2 * zeta_p + 3)) {
         bm_set_error("zeta_p must be in [0, 20] with N >= 2 zeta_p + 3");
@@ -462,6 +470,12 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     const bool reuse = c->assembled && c->N == N && c->form == form && c->prec == prec && c->nb == p.nb &&
                        curve->kind != BM_CURVE_USER;
     if (!reuse) free_problem(c);
+    // the captured factorisation depends on the launch settings: capture again when they change
+    if (reuse && (eager != c->eager || cl_cap != c->opt_cluster_cap || pkern != c->opt_panel_kernel))
+        drop_graphs(c);
+    c->eager = eager;
+    c->opt_cluster_cap = cl_cap;
+    c->opt_panel_kernel = pkern;
     c->bs_solve = 64;
     if (!reuse && c->held + p.bytes > c->budget) {
         bm_set_error("admission: system needs " + std::to_string(p.bytes) + " bytes, budget leaves " +
@@ -572,10 +586,10 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     c->launches += ((form == BM_MIXED) ? 4 : 3) + (c->zeta_p > 0 ? 1 : 0);
     if (c32) {
         if (form == BM_MIXED) {
-            BM_CUDA_TRY(launch_pack_schur(st, c, prec == BM_CF32_3XTF32_IR));
+            BM_CUDA_TRY(launch_pack_solve(st, c, prec == BM_CF32_3XTF32_IR));
             BM_CUDA_TRY(launch_split_planes(st, c->d_Mtop, c->ldtop, 2 * N, N, c->d_Ptop, c->d_Qtop, c->ldtop));
             BM_CUDA_TRY(launch_split_planes(st, c->d_Mbot, c->ldbot, N, 2 * N, c->d_Pbot, c->d_Qbot, c->ldbot));
-            c->launches += 6;
+            c->launches += 3;
         } else {
             BM_CUDA_TRY(launch_split_planes(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_PA, c->d_QA, c->ldA));
             c->launches += 1;
@@ -583,7 +597,10 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     }
     BM_CUDA_TRY(cudaStreamSynchronize(st));
     if (d_user) ctx_free(c, d_user);
-    BM_TRY(lu_setup(c));
+    BM_TRY(lu_setup(c, cl_cap, pkern));
+    // test hook read by the tensor-core products (d_err[1])
+    BM_CUDA_TRY(cudaMemcpyAsync(c->d_info + 2, &test_wait, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c32) {
         const bool split = prec == BM_CF32_3XTF32_IR;
         if (form == BM_MIXED) {
@@ -626,6 +643,8 @@ bm_status factor_sequence(bm_ctx* c) {
         }
     } else {
         if (c->form == BM_MIXED) {
+            // the FP32 operands of the Schur product, then U33 = -[M31 M32] [M13; M23]
+            BM_CUDA_TRY(launch_pack_schur(s, c, c->prec == BM_CF32_3XTF32_IR));
             long kext = (c->prec == BM_CF32_3XTF32_IR) ? 3L * c->kseg_schur : c->kseg_schur;
             BM_CUDA_TRY(gemm_tc(s, c->tm_schur[0], c->tm_schur[1], c->tm_schur[2], c->tm_schur[3], c->d_F32r,
                                 c->d_F32i, c->ldF, c->N, c->N, (int)kext, -1.0f, 0.0f, c->d_err));
@@ -634,11 +653,6 @@ bm_status factor_sequence(bm_ctx* c) {
         }
     }
     return lu_factor_enqueue(c);
-}
-
-bool graphs_enabled() {
-    const char* e = getenv("BM_NO_GRAPHS");
-    return !(e && e[0] == '1');
 }
 
 int count_kernel_nodes(cudaGraph_t g) {
@@ -657,7 +671,7 @@ int count_kernel_nodes(cudaGraph_t g) {
 // Run `fn` through a cached CUDA graph (captured on first use), or eagerly if graphs are off.
 template <class Fn>
 bm_status run_captured(bm_ctx* c, bm_ctx::GraphSlot* slot, Fn fn) {
-    if (!graphs_enabled()) return fn();
+    if (c->eager) return fn();
     if (slot->exec == nullptr) {
         cudaGraph_t g = nullptr;
         BM_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -923,7 +937,10 @@ extern "C" bm_status bm_solve_block(bm_ctx* c, int c1, const bm_c64* B1, int ld1
                                     int c3, const bm_c64* B3, int ld3, bm_c64* X, int ldx, int on_device,
                                     bm_solve_info* info) {
     if (c == nullptr || X == nullptr) return BM_EINVAL;
-    if (!c->assembled || c->form != BM_MIXED) return BM_ESTATE;
+    if (!c->assembled || c->form != BM_MIXED || !c->factored || c->singular) {
+        bm_set_error("bm_solve_block needs a factored, non-singular mixed system");
+        return BM_ESTATE;
+    }
     const int N = c->N;
     const int cs[3] = {c1, c2, c3};
     const bm_c64* Bs[3] = {B1, B2, B3};
@@ -943,6 +960,7 @@ extern "C" bm_status bm_solve_block(bm_ctx* c, int c1, const bm_c64* B1, int ld1
                 std::memcpy(&B[(size_t)(col * ldb + (long)b * N)], Bs[b] + (size_t)j * lds[b], sizeof(bm_c64) * N);
         return bm_solve(c, (int)C, B.data(), (int)ldb, X, ldx, 0, info);
     }
+    BM_CUDA_TRY(cudaSetDevice(c->device));
     bm_c64* dB = nullptr;
     bm_status s = alloc_t(c, &dB, sizeof(bm_c64) * (size_t)(ldb * C));
     if (s != BM_OK) return s;
@@ -1009,6 +1027,11 @@ extern "C" bm_status bm_far_field(bm_ctx* c, const bm_c64* X, int ldx, int nrhs,
     if (c == nullptr || X == nullptr || angles == nullptr || Uinf == nullptr || nrhs < 1 || M < 1) return BM_EINVAL;
     if (!c->assembled) return BM_ESTATE;
     if (ldx < c->nsys || ldu < M) return BM_EINVAL;
+    for (int i = 0; i < M; ++i)
+        if (!std::isfinite(angles[i])) {
+            bm_set_error("bm_far_field: angle " + std::to_string(i) + " is not finite");
+            return BM_ENONFINITE;
+        }
     BM_CUDA_TRY(cudaSetDevice(c->device));
     cudaStream_t s = c->stream;
     double* d_ang = nullptr;

@@ -747,6 +747,8 @@ cudaError_t launch_hankel_probe(cudaStream_t s, const bm_ctx* c, const double2* 
     return cudaGetLastError();
 }
 
+// Operands of the Schur-complement product (part of the factorisation, like the FP32 copy of the
+// ordinary matrix): A = [M31 M32] row-major, B = [M13; M23] column by column.
 cudaError_t launch_pack_schur(cudaStream_t s, const bm_ctx* c, int split) {
     int N = c->N;
     int K = 2 * N;
@@ -759,8 +761,15 @@ cudaError_t launch_pack_schur(cudaStream_t s, const bm_ctx* c, int split) {
     long total = (long)N * c->ldk_schur;
     pack_colmajor_kernel<<<ceil_div(total, 256), 256, 0, s>>>(c->d_Mtop, c->ldtop, K, N, split, c->d_Bp_r, c->d_Bp_i,
                                                                c->ldk_schur);
-    // rows of [M13; M23] (2N x N) for the skinny products [M13; M23] z of the solve; only the
-    // tensor maps read this pack, which stop at K, so its padding columns stay unset
+    return cudaGetLastError();
+}
+
+// Rows of [M13; M23] (2N x N) for the skinny products [M13; M23] z of the solve (made once at
+// assembly, like the split planes of the residual); only the tensor maps read this pack, which
+// stop at K, so its padding columns stay unset.
+cudaError_t launch_pack_solve(cudaStream_t s, const bm_ctx* c, int split) {
+    int N = c->N;
+    dim3 blk(32, 8);
     dim3 gridc(ceil_div(N, 32), ceil_div(2 * N, 32));
     pack_rowmajor_kernel<<<gridc, blk, 0, s>>>(c->d_Mtop, c->ldtop, 2 * N, N, split, c->d_Cp_r, c->d_Cp_i, c->ldk_c);
     return cudaGetLastError();

@@ -282,8 +282,13 @@ struct bm_ctx {
     int num_sms = 0;
 
     // panel launch configuration
-    int panel_cluster = 0;   // max cluster size the device allows for the panel kernel
+    int panel_cluster_c32 = 0;   // max cluster size the device co-schedules for the FP32 / FP64
+    int panel_cluster_z64 = 0;   //   panel kernels (queried once per handle)
+    int panel_cluster = 0;       // cluster size used (the device's, capped by bm_opts.panel_cluster_max)
     bool panel_lane_col = true;  // FP32 panels on the lane-per-column kernel where it fits
+    bool eager = false;          // bm_opts.eager: no CUDA graphs
+    int opt_cluster_cap = 0;     // bm_opts.panel_cluster_max / panel_kernel of the assembled system
+    int opt_panel_kernel = 0;
 };
 
 // allocation helpers (api.cu)

@@ -14,9 +14,11 @@
 // array has to start at zero and the call clears none of it.
 //
 // Set-up: the first call on a device, with that device current, looks up the device address of
-// the array (cudaGetSymbolAddress) and keeps it for later calls on that device.  The lookup can
-// load the library's device code onto the device, so make this first call before any stream
-// capture starts on the device.
+// the array (cudaGetSymbolAddress) and keeps it for later calls on that device, together with the
+// CUDA context it belongs to.  The lookup can load the library's device code onto the device, so
+// make this first call before any stream capture starts on the device.  If the device's context
+// has been replaced since (cudaDeviceReset, then new work), the address is looked up again: an
+// address from the old context would no longer belong to the array.
 //
 // Overlapping calls race: the array is shared by every handle and host thread that uses the
 // device, so two calls running at the same time can overwrite each other's angles before the
@@ -25,6 +27,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <cmath>
 #include <mutex>
 
 static __device__ __align__(256) double g_ff_angles[BM_FAR_FIELD_STATIC_MAX_ANGLES];
@@ -34,15 +37,37 @@ namespace {
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mu;
 double* g_angles_ptr[MAX_DEVICES] = {};
+void* g_angles_ctx[MAX_DEVICES] = {};  // the context each address was looked up in
 
-// Device address of g_ff_angles on `dev` (the current device), looked up once per device.
+// The calling thread's current CUDA context (driver API, reached through the runtime's entry-point
+// query so the library needs no link-time dependence on libcuda); nullptr if unavailable.
+void* current_context() {
+    using GetCurrent = int (*)(void**);
+    static GetCurrent fn = []() -> GetCurrent {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<GetCurrent>(p);
+    }();
+    void* ctx = nullptr;
+    if (fn == nullptr || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+// Device address of g_ff_angles on `dev` (the current device), looked up once per device and
+// context.
 bm_status angles_scratch(int dev, double** out) {
     if (dev < 0 || dev >= MAX_DEVICES) {
         bm_set_error("bm_far_field_static: device index " + std::to_string(dev) + " out of range");
         return BM_EINVAL;
     }
+    void* ctx = current_context();
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (g_angles_ptr[dev] == nullptr) {
+    if (g_angles_ptr[dev] == nullptr || ctx == nullptr || ctx != g_angles_ctx[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_ff_angles);
         if (e != cudaSuccess || p == nullptr) {
@@ -51,6 +76,7 @@ bm_status angles_scratch(int dev, double** out) {
             return BM_ECUDA;
         }
         g_angles_ptr[dev] = static_cast<double*>(p);
+        g_angles_ctx[dev] = ctx;
     }
     *out = g_angles_ptr[dev];
     return BM_OK;
@@ -68,6 +94,11 @@ extern "C" bm_status bm_far_field_static(bm_ctx* c, const bm_c64* X, int ldx, in
     }
     if (!c->assembled) return BM_ESTATE;
     if (ldx < c->nsys || ldu < M) return BM_EINVAL;
+    for (int i = 0; i < M; ++i)
+        if (!std::isfinite(angles[i])) {
+            bm_set_error("bm_far_field_static: angle " + std::to_string(i) + " is not finite");
+            return BM_ENONFINITE;
+        }
     BM_CUDA_TRY(cudaSetDevice(c->device));
     double* d_ang = nullptr;
     BM_TRY(angles_scratch(c->device, &d_ang));

@@ -16,7 +16,9 @@
 // and update C with coalesced column-major stores.  For C = C + alpha A B^T (the LU trailing
 // updates) a six-warp form loads the C tile into the upper half of TMEM during the main loop, so
 // the epilogue only stores.  Every mbarrier wait is bounded (2 s by the global timer); a timeout
-// sets *err, skips the epilogue, waits for issued copies and frees TMEM.
+// sets *err, skips the epilogue, waits for issued copies and products and frees TMEM.  err[1] is
+// a test hook: when it is set the MMA warp first waits on a barrier that nothing completes, gives
+// up after 1 ms and takes that timeout path without issuing any product.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -34,6 +36,7 @@ constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 2 * BN;  // Dr, Di
 constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr uint64_t TEST_WAIT_NS = 1000000ull;  // the test hook's wait limit
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -169,8 +172,9 @@ __global__ void __launch_bounds__(192, 1)
                     int m, int n, int kext, int S, float alpha, float beta, int* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    // full[S], empty[S], done, never (the test hook's barrier: initialised, never arrived on)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tm = blockIdx.x, tn = blockIdx.y;
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(192, 1)
     const int kb_begin = (int)((long)blockIdx.z * nkb_all / S);
     const int nkb = (int)((long)(blockIdx.z + 1) * nkb_all / S) - kb_begin;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+    const uint32_t never = smem_u32(bars + 2 * STAGES + 1);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -186,6 +191,7 @@ __global__ void __launch_bounds__(192, 1)
             mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(done, 1);
+        mbar_init(never, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -224,7 +230,14 @@ __global__ void __launch_bounds__(192, 1)
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idp = idesc_tf32(0), idn = idesc_tf32(1);
-        for (int kb = 0; kb < nkb; ++kb) {
+        if (err[1] != 0) {
+            // test hook: a wait that nothing ends, bounded like every other wait
+            const uint64_t t0 = gtimer();
+            while (!mbar_try(never, 0u) && gtimer() - t0 < TEST_WAIT_NS) {
+            }
+            *abort_flag = 1;
+        }
+        for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
             const int s = kb % STAGES;
             const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
             if (!mbar_wait(full0 + 8 * s, ph, abort_flag)) break;
@@ -245,6 +258,13 @@ __global__ void __launch_bounds__(192, 1)
             mma_commit(empty0 + 8 * s);
         }
         mma_commit(done);
+        if (*abort_flag) {
+            // the products already issued finish (and the commit lands) before TMEM and shared
+            // memory are released
+            const uint64_t t0 = gtimer();
+            while (!mbar_try(done, 0u) && gtimer() - t0 < WAIT_NS) {
+            }
+        }
     }
     __syncwarp();
     if (OUT == OUT_C32_PRE && warp >= 2) {

@@ -11,7 +11,8 @@ cudaError_t launch_plane_wave(cudaStream_t s, const bm_ctx* c, const double* d_a
 cudaError_t launch_far_field(cudaStream_t s, const bm_ctx* c, const double2* X, long ldx, int nrhs, const double* d_ang,
                              int M, double2* U, long ldu);
 cudaError_t launch_hankel_probe(cudaStream_t s, const bm_ctx* c, const double2* z, int n, double2* h0, double2* h1);
-cudaError_t launch_pack_schur(cudaStream_t s, const bm_ctx* c, int split);
+cudaError_t launch_pack_schur(cudaStream_t s, const bm_ctx* c, int split);  // Schur operands (in bm_factor)
+cudaError_t launch_pack_solve(cudaStream_t s, const bm_ctx* c, int split);  // [M13; M23] rows (assembly)
 cudaError_t launch_to_c32(cudaStream_t s, const double2* A, long lda, int m, int n, float* Fr, float* Fi, long ldf);
 
 // gemm_simt.cu
@@ -40,7 +41,7 @@ cudaError_t launch_pack_b(cudaStream_t s, const float* Vr, const float* Vi, long
                           float* Br, float* Bi, long ldk);
 
 // lu.cu
-bm_status lu_setup(bm_ctx* c);
+bm_status lu_setup(bm_ctx* c, int cluster_cap, int panel_kernel);
 bm_status lu_factor_enqueue(bm_ctx* c);       // factor d_F64 / d_F32 in place (stream-ordered)
 size_t swap_map_bytes();
 bm_status getrs_z64(bm_ctx* c, double2* Y, long ldy, int nrhs);   // in place; Y holds P B (rows gathered by perm)

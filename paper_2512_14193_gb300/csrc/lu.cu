@@ -874,19 +874,15 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* din
 
 }  // namespace
 
-bm_status lu_setup(bm_ctx* c) {
-    if (c->panel_cluster == 0) {
-        c->panel_cluster = (c->prec == BM_FP64) ? query_cluster_max_z64() : query_cluster_max_c32();
-        // BM_PANEL_CLUSTER_MAX caps the panel cluster (1..16); fewer CTAs put more rows on
-        // each thread, which selects the narrower sub-panel variants
-        if (const char* e = getenv("BM_PANEL_CLUSTER_MAX")) {
-            int v = atoi(e);
-            if (v >= 1 && v <= 16) c->panel_cluster = std::min(c->panel_cluster, v);
-        }
-        // BM_PANEL_KERNEL=rows keeps FP32 panels on the register-row kernel
-        const char* pk = getenv("BM_PANEL_KERNEL");
-        c->panel_lane_col = !(pk != nullptr && std::string(pk) == "rows");
-    }
+// Panel launch configuration of the handle: the largest cluster the device co-schedules (queried
+// once), capped by bm_opts.panel_cluster_max (fewer CTAs put more rows on each thread, which selects
+// the narrower sub-panel variants), and the panel kernel bm_opts.panel_kernel selects.
+bm_status lu_setup(bm_ctx* c, int cluster_cap, int panel_kernel) {
+    int& dev_max = (c->prec == BM_FP64) ? c->panel_cluster_z64 : c->panel_cluster_c32;
+    if (dev_max == 0) dev_max = (c->prec == BM_FP64) ? query_cluster_max_z64() : query_cluster_max_c32();
+    c->panel_cluster = dev_max;
+    if (cluster_cap >= 1 && cluster_cap <= MAX_CLUSTER) c->panel_cluster = std::min(c->panel_cluster, cluster_cap);
+    c->panel_lane_col = panel_kernel == 0;
     return BM_OK;
 }
 

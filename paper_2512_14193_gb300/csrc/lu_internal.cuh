@@ -262,9 +262,14 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
                 pq = q;
             }
         }
+        bool sing = !(pv > (Rl)0);
+        if (pi < c || pi >= m) {  // no usable candidate (a column of NaNs): keep row c, singular
+            pi = c;
+            pq = 0;
+            sing = true;
+        }
         const CV* u = &cand_row[par][pq][0];
         const CV* drow = &diag_row[par][0];
-        const bool sing = !(pv > (Rl)0);
         if (tid < NBP) ucur[par][tid] = u[tid];
         if (cta == 0 && tid == 0) {
             ipiv[j0 + c] = j0 + pi;

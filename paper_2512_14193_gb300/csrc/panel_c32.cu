@@ -188,11 +188,17 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
             piu = e.y;
         }
         warp_best(pvb, piu);
-        const int pi = (int)piu;
-        const int pq = (pi != INT_MAX) ? pi / R : 0;  // the CTA that owns the pivot row
+        int pi = (int)piu;
+        bool sing = !(__uint_as_float(pvb) > 0.f);
+        // no usable candidate (a column of NaNs, or data lost to a timed-out wait): keep row c and
+        // report the column as singular, so every index stays inside the panel
+        if (pi < c || pi >= m) {
+            pi = c;
+            sing = true;
+        }
+        const int pq = pi / R;  // the CTA that owns the pivot row
         const float2 u = cand_buf[par][pq][lane];
         const float2 dr = diag_buf[par][lane];
-        const bool sing = !(__uint_as_float(pvb) > 0.f);
         if (cta == 0 && threadIdx.x == 0) {
             ipiv[j0 + c] = j0 + pi;
             if (sing && info != nullptr && *info == 0) *info = j0 + c + 1;

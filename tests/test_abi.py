@@ -137,3 +137,23 @@ def test_library_zeta_weights_match_the_oracle(bmlib):
         assert np.abs(c2 - ref_c2).max() <= 1e-13 * np.abs(ref_c2).max()
     with pytest.raises(bmlib.BMError):
         bmlib.bm_zeta_weights(21)
+
+
+def test_binding_rejects_outputs_too_small_for_the_write(bmlib):
+    # The library sees leading dimensions only; the binding checks that U has a column per solution
+    # and a row per angle (and X the system's rows) before any call, so no device write can run past
+    # an array.  No handle or GPU is needed: the checks fire first.
+    import torch
+    X = torch.zeros((3, 30), dtype=torch.complex128).t()          # 30 x 3 (host tensors)
+    th = np.linspace(0.0, 1.0, 7)
+    for U in (torch.zeros((2, 7), dtype=torch.complex128).t(),     # too few columns
+              torch.zeros((3, 6), dtype=torch.complex128).t()):    # too few rows
+        with pytest.raises(ValueError):
+            bmlib.bm_far_field(None, X, th, U)
+        with pytest.raises(ValueError):
+            bmlib.bm_far_field_static(None, X, th, U)
+    B = np.zeros((30, 2), dtype=np.complex128, order="F")
+    with pytest.raises(ValueError):
+        bmlib.bm_rhs_plane_wave(None, [0.0, 1.0, 2.0], B)          # a column per angle
+    with pytest.raises(ValueError):
+        bmlib.bm_solve(None, B, np.zeros((30, 3), dtype=np.complex128, order="F"))

@@ -73,3 +73,75 @@ def test_tight_tolerance_needs_fp64_residuals(bmlib, handle):
     assert e.value.status == bmlib.BM_EINVAL
     bmlib.bm_assemble(handle, curve.kind, curve.params4(), 64, 2.0, 3.0, bmlib.BM_MIXED,
                       bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=1e-14, residual=2))
+
+
+@pytest.mark.gpu
+def test_refinement_cap_reports_not_converged(bmlib, handle):
+    # one TF32 correction cannot reach 1e-12: BM_ENOTCONV, with the last iterate in X
+    curve, N = W.kite(), 200
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, 6.0, 9.0, bmlib.BM_MIXED,
+                      bmlib.make_opts(bmlib.BM_CF32_TF32_IR, refine_tol=1e-12, refine_maxit=1))
+    assert bmlib.bm_factor(handle) == 0
+    B = np.zeros((3 * N, 1), dtype=np.complex128, order="F")
+    bmlib.bm_rhs_plane_wave(handle, [0.0], B)
+    X = np.zeros_like(B, order="F")
+    with pytest.raises(bmlib.BMError) as e:
+        bmlib.bm_solve(handle, B, X)
+    assert e.value.status == bmlib.BM_ENOTCONV
+    info = bmlib.bm_solve(handle, B, X, raise_on_notconv=False)
+    assert info.iterations == 1 and 1e-12 < info.backward_error < 1e-3
+    assert np.isfinite(X).all() and np.abs(X).max() > 0
+    # the handle goes on: a looser target on the same factors converges
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, 6.0, 9.0, bmlib.BM_MIXED,
+                      bmlib.make_opts(bmlib.BM_CF32_TF32_IR))
+    assert bmlib.bm_factor(handle) == 0
+    assert bmlib.bm_solve(handle, B, X).backward_error <= 1e-9
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", [0, 1])
+def test_device_wait_timeout_is_reported_and_the_device_stays_usable(bmlib, form):
+    # The test hook makes every tensor-core product wait on a barrier nothing completes; the wait
+    # gives up after ~1 ms, the product skips its output, and bm_factor reports BM_ETIMEOUT.  No
+    # kernel is left running: the same handle and a fresh one then factor and solve correctly.
+    curve, N = W.ellipse(1.0, 0.6), 300
+    nsys = 3 * N if form == 0 else 2 * N
+    h = bmlib.bm_create(0)
+    try:
+        bmlib.bm_assemble(h, curve.kind, curve.params4(), N, 5.0, 7.5, form,
+                          bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, test_wait_timeout=True))
+        with pytest.raises(bmlib.BMError) as e:
+            bmlib.bm_factor(h)
+        assert e.value.status == bmlib.BM_ETIMEOUT
+        B = np.zeros((nsys, 1), dtype=np.complex128, order="F")
+        X = np.zeros_like(B, order="F")
+        with pytest.raises(bmlib.BMError) as e:
+            bmlib.bm_solve(h, B, X)                  # not factored
+        assert e.value.status == bmlib.BM_ESTATE
+        for hh in (h, None):
+            g = hh if hh is not None else bmlib.bm_create(0)
+            try:
+                bmlib.bm_assemble(g, curve.kind, curve.params4(), N, 5.0, 7.5, form,
+                                  bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR))
+                assert bmlib.bm_factor(g) == 0
+                bmlib.bm_rhs_plane_wave(g, [0.0], B)
+                assert bmlib.bm_solve(g, B, X).backward_error <= 1e-9
+            finally:
+                if hh is None:
+                    bmlib.bm_destroy(g)
+    finally:
+        bmlib.bm_destroy(h)
+
+
+@pytest.mark.gpu
+def test_nonfinite_far_field_angles(bmlib, handle):
+    torch = pytest.importorskip("torch")
+    N = 64
+    bmlib.bm_assemble(handle, W.CIRCLE, (1.0, 0, 0), N, 2.0, 3.0, bmlib.BM_MIXED, bmlib.make_opts())
+    assert bmlib.bm_factor(handle) == 0
+    X = torch.zeros((1, 3 * N), dtype=torch.complex128, device="cuda").t()
+    U = torch.zeros((1, 3), dtype=torch.complex128, device="cuda").t()
+    for fn in (bmlib.bm_far_field, bmlib.bm_far_field_static):
+        with pytest.raises(bmlib.BMError) as e:
+            fn(handle, X, [0.0, float("inf"), 1.0], U)
+        assert e.value.status == bmlib.BM_ENONFINITE

@@ -107,18 +107,16 @@ def test_mixed_precision_refinement(bmlib, handle, prec, form, resid):
 @pytest.mark.parametrize("prec", [0, 2])
 @pytest.mark.parametrize("clmax,N,kernel", [(1, 600, ""), (1, 1100, ""), (2, 1100, ""), (2, 500, ""),
                                             (16, 1100, "rows")])
-def test_panel_variants_match_oracle(bmlib, monkeypatch, prec, clmax, N, kernel):
+def test_panel_variants_match_oracle(bmlib, prec, clmax, N, kernel):
     # Capping the panel cluster puts 2 (N=600, cap 1; N=1100, cap 2) or 4 (N=1100, cap 1) rows on
     # each thread of the register-row panel kernel, which selects its narrower sub-panel variants;
     # FP32 panels of at most 256 rows per CTA run on the lane-per-column kernel (N=500, cap 2: 16
     # rows per warp).  kernel="rows" keeps every FP32 panel on the register-row kernel.
-    monkeypatch.setenv("BM_PANEL_CLUSTER_MAX", str(clmax))
-    if kernel:
-        monkeypatch.setenv("BM_PANEL_KERNEL", kernel)
     h = bmlib.bm_create(0)
     try:
         curve, k0, k1 = W.ellipse(1.0, 0.6), 6.0 - 0.1j, 9.0 - 0.15j
-        bmlib.bm_assemble(h, curve.kind, curve.params4(), N, k0, k1, bmlib.BM_MIXED, bmlib.make_opts(prec))
+        opts = bmlib.make_opts(prec, panel_cluster_max=clmax, panel_kernel=1 if kernel == "rows" else 0)
+        bmlib.bm_assemble(h, curve.kind, curve.params4(), N, k0, k1, bmlib.BM_MIXED, opts)
         assert bmlib.bm_factor(h) == 0
         g, P = O.nodes(curve, N), O.default_params(k0, k1)
         B = _rhs(g, P, N, W.MIXED, 3, full=True, seed=5)
