@@ -149,64 +149,128 @@ class ClockSampler:
 # --------------------------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------------------------
-_ORACLE_CACHE = {}
-
-
-def oracle_sample(w: W.Workload, n_sample: int, reps: int):
-    """Time the oracle's factor+solve (Theorem thm:LU path: numpy matmul Schur complement,
-    unblocked LU, Corollary lem:for_ssm_RHS solve) of the same scatterer at N = n_sample with the
-    workload's nrhs, and scale the time by (N / n_sample)^3 to the workload's N.  The oracle's
-    assembly of the sample system is done once and not timed (the metric is factor + solve)."""
+def oracle_problem(w: W.Workload):
+    """The oracle's assembled blocks of the workload's mixed system and its right-hand sides (the
+    plane wave and the seeded Gaussian columns), built on the host; not timed."""
     import oracle as O
-    from oracle.dense import lu_factor, lu_solve, schur_complement
-    ws = W.scaled(w, n_sample)
-    if n_sample not in _ORACLE_CACHE:
-        g = O.nodes(ws.curve, ws.N)
-        P = O.default_params(ws.k_out, ws.k_in)
-        blocks = O.mixed_blocks(g, P)
-        Bp = O.rhs_plane_wave(g, P, [0.0], W.MIXED)
-        Bg = W.place_rhs(W.gaussian_g(ws.N, ws.n_gauss, ws.seed), ws.N, W.MIXED)
-        _ORACLE_CACHE[n_sample] = (blocks, np.concatenate([Bp, Bg], 1))
-    blocks, B = _ORACLE_CACHE[n_sample]
+    g = O.nodes(w.curve, w.N)
+    P = O.default_params(w.k_out, w.k_in)
+    blocks = O.mixed_blocks(g, P)
+    Bp = O.rhs_plane_wave(g, P, [0.0], W.MIXED)
+    Bg = W.place_rhs(W.gaussian_g(w.N, w.n_gauss, w.seed), w.N, W.MIXED)
+    return blocks, np.concatenate([Bp, Bg], 1)
+
+
+def _column_work(n: int) -> np.ndarray:
+    """Relative cost of eliminating column k of an n x n matrix by the oracle's unblocked LU: the
+    rank-1 update touches (n - k - 1)^2 entries (plus a per-column constant for the pivot search,
+    row swap and scaling, taken as 4 n entries' worth)."""
+    k = np.arange(n, dtype=np.float64)
+    return (n - k - 1.0) ** 2 + 4.0 * n
+
+
+def oracle_factor_solve_steps(blocks, B, nsteps: int):
+    """The oracle's whole factor + solve of the mixed system (Theorem thm:LU: Schur complement by
+    numpy matmul; unblocked LU with partial pivoting; Corollary lem:for_ssm_RHS solve), run as
+    `nsteps` consecutive pieces of about equal LU work.  A generator: yields after each piece, so a
+    caller can time the pieces one by one; their times add up to the time of the whole run."""
+    from oracle.dense import lu_factor_columns, lu_solve, schur_complement
     M13, M23, M31, M32 = blocks
-    times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        LU, piv = lu_factor(schur_complement(blocks))
-        b1, b2, b3 = B[:ws.N], B[ws.N:2 * ws.N], B[2 * ws.N:]
-        z3 = lu_solve(LU, piv, b3 - M31 @ b1 - M32 @ b2)
-        _x = np.concatenate([b1 - M13 @ z3, b2 - M23 @ z3, z3], 0)
-        times.append(time.perf_counter() - t0)
-    scale = (w.N / n_sample) ** 3
-    t_full = float(np.median(times)) * scale
-    return {"value": w.nrhs / t_full, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle factor+solve at N={n_sample} (same star, k, nrhs={w.nrhs}), median of {reps}, "
-                      f"scaled by (N/{n_sample})^3 = {scale:.0f} to N={w.N}; numpy BLAS matmul on all cores, "
-                      f"unblocked LU loop in one thread",
-            "seconds_sample": float(np.median(times)), "seconds_scaled": t_full}
+    N = M13.shape[0]
+    cw = np.cumsum(_column_work(N))
+    bounds = [int(np.searchsorted(cw, cw[-1] * (i + 1) / nsteps)) + 1 for i in range(nsteps)]
+    bounds[-1] = N
+    gen = lu_factor_columns(schur_complement(blocks))
+    done = 0
+    result = None
+    for i in range(nsteps):
+        while done < bounds[i]:
+            try:
+                next(gen)
+                done += 1
+            except StopIteration as fin:
+                result = fin.value
+                done = N
+        if i == nsteps - 1:
+            if result is None:
+                try:
+                    next(gen)
+                except StopIteration as fin:
+                    result = fin.value
+            LU, piv = result
+            b1, b2, b3 = B[:N], B[N:2 * N], B[2 * N:]
+            z3 = lu_solve(LU, piv, b3 - M31 @ b1 - M32 @ b2)
+            np.concatenate([b1 - M13 @ z3, b2 - M23 @ z3, z3], 0)
+        yield i
+
+
+def oracle_sample(w: W.Workload, ncols: int):
+    """Bounded sample of the oracle's factor + solve of the workload itself (same N): the whole
+    Schur complement, the first `ncols` columns of the unblocked LU, and a full Corollary solve
+    (its cost does not depend on the values), each timed; the remaining LU columns are charged at
+    the measured rate per unit of column work (n - k - 1)^2 + 4n."""
+    from oracle.dense import lu_factor_columns, lu_solve, schur_complement
+    blocks, B = oracle_problem(w)
+    M13, M23, M31, M32 = blocks
+    N = w.N
+    t0 = time.perf_counter()
+    U = schur_complement(blocks)
+    t_schur = time.perf_counter() - t0
+    gen = lu_factor_columns(U)
+    t0 = time.perf_counter()
+    for _ in range(ncols):
+        next(gen)
+    t_cols = time.perf_counter() - t0
+    cw = _column_work(N)
+    t_lu = t_cols * cw.sum() / cw[:ncols].sum()
+    piv = np.arange(N)
+    t0 = time.perf_counter()
+    b1, b2, b3 = B[:N], B[N:2 * N], B[2 * N:]
+    z3 = lu_solve(U, piv, b3 - M31 @ b1 - M32 @ b2)
+    np.concatenate([b1 - M13 @ z3, b2 - M23 @ z3, z3], 0)
+    t_solve = time.perf_counter() - t0
+    total = t_schur + t_lu + t_solve
+    return {"value": w.nrhs / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle at the workload's own N={N}: Schur complement (numpy matmul, all cores) "
+                      f"{t_schur:.2f} s, the first {ncols} of {N} unblocked-LU columns {t_cols:.2f} s "
+                      f"(one thread; the other columns charged at that rate per unit of column work "
+                      f"(n-k-1)^2+4n: {t_lu:.1f} s), Corollary solve of {w.nrhs} RHS {t_solve:.2f} s",
+            "seconds_measured": t_schur + t_cols + t_solve, "seconds_total": total}
 
 
 def run_reference(args, ws, rank):
-    w = W.STAR_N4096
+    """The reference arm: the CPU oracle's whole factor + solve of the benchmark workload, measured
+    directly (no extrapolation), split into --steps pieces of about equal LU work; --warmup untimed
+    full factor + solves of the same scatterer at N = 256 come first."""
     if rank != 0:
         return
-    n_sample = 768 if args.quick else 1024
-    t0 = time.perf_counter()
+    w = W.scaled(W.STAR_N4096, 1024) if args.quick else W.STAR_N4096
+    t_wall = time.perf_counter()
+    small = W.scaled(w, 256)
+    sb, sB = oracle_problem(small)
+    for _ in range(args.warmup):
+        for _i in oracle_factor_solve_steps(sb, sB, 1):
+            pass
+    blocks, B = oracle_problem(w)
     per = []
-    for i in range(args.warmup + args.steps):
-        r = oracle_sample(w, n_sample, 1)
-        if i >= args.warmup:
-            per.append(r["seconds_scaled"])
-    t_step = float(np.median(per))
-    val = w.nrhs / t_step
+    gen = oracle_factor_solve_steps(blocks, B, args.steps)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        next(gen)
+        per.append(time.perf_counter() - t0)
+    total = float(np.sum(per))
+    val = w.nrhs / total
+    sample = (f"the oracle's whole factor+solve of the workload (N={w.N}, nrhs={w.nrhs}) measured directly: "
+              f"numpy matmul Schur complement (all cores), unblocked LU (one thread), Corollary solve; "
+              f"{args.steps} steps of equal LU work, {total:.1f} s in all")
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c128 (f64, numpy)", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64, numpy)", "data": "synthetic",
             "config": workload_cfg(w, "fp64 oracle"), "impl": "reference",
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": time.perf_counter() - t0}
+            "seconds_factor_solve": total, "step_seconds": per, "wall_s": time.perf_counter() - t_wall}
     print(json.dumps(line), flush=True)
 
 
@@ -232,6 +296,79 @@ def colmajor_copy(B, torch):
     out = torch.zeros((B.shape[1], B.shape[0]), dtype=torch.complex128, device=B.device).t()
     out.copy_(B)
     return out
+
+
+def lu_work(n: int, NB: int = 256, nbp: int = 32) -> dict:
+    """Algorithmic work of the blocked LU of an n x n complex matrix as the library blocks it (outer
+    panels of NB columns, sub-panels of nbp): real flops (8 per complex multiply-add) of the
+    sub-panel factorisations, of the rank-nbp updates inside each outer panel and of the trailing
+    updates; and the bytes of the outer panels' row interchanges and U12 blocks (8-byte complex,
+    read and written once)."""
+    panel = inner = trail = 0.0
+    swap_bytes = 0.0
+    for J in range(0, n, NB):
+        jb = min(NB, n - J)
+        for j in range(J, J + jb, nbp):
+            ib = min(nbp, J + jb - j)
+            m = n - j
+            panel += 8.0 * sum((m - c - 1) * (ib - c) for c in range(ib))
+            rest = J + jb - j - ib
+            if rest > 0:
+                inner += 8.0 * (m - ib) * ib * rest
+        mm = n - J - jb
+        trail += 8.0 * mm * mm * jb
+        swap_bytes += 16.0 * (2.0 * jb * (n - jb) + jb * mm)
+    return {"panel": panel, "inner": inner, "trailing": trail, "swap_bytes": swap_bytes}
+
+
+def roofline_from_profile(prof, N: int, nrhs: int, prec: int, iters: int, peaks: dict, src: str):
+    """Roofline of the kernel with the largest summed device time in one mixed factor + solve
+    (prof: (name, launches, ms) from bm_profile, largest first).  achieved = the kernel's algorithmic
+    work in the step / its summed time (= work per launch / average launch time); the work of each
+    kernel is its share of the method's arithmetic (real flops, 8 per complex multiply-add) or of
+    its compulsory memory traffic, never the implementation's instruction count."""
+    sm = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fp32 = 152 * 128 * 2 * sm / 1e12                       # FP32 FMA TFLOP/s, unit counts x clock
+    tf32 = peaks["bf16_tflops"] * (1.1 / 2.25)             # measured bf16 x nominal tf32/bf16 ratio
+    hbm = peaks["hbm_gbs"]
+    lw = lu_work(N)
+    work = {
+        "resid_df_kernel (+ split-K reduction)": ("alu", 8.0 * 4 * N * N * nrhs, fp32, "TFLOP/s",
+                                                  "4N^2 nrhs complex MACs x 8 real flops vs the FP32 FMA rate "
+                                                  "(152 SMs x 128 lanes x 2 x clock)"),
+        "cgemm_tc_kernel (Schur complement)": ("tensor", 16.0 * N ** 3, tf32, "TFLOP/s",
+                                               "16 N^3 real flops (4M) vs the TF32 figure (measured bf16 x 1.1/2.25)"),
+        "cgemm_tc_kernel (trailing update)": ("tensor", lw["trailing"], tf32, "TFLOP/s",
+                                              "sum over outer panels of 8 m^2 NB real flops vs the TF32 figure"),
+        "panel_lc_kernel": ("alu", lw["panel"], fp32, "TFLOP/s",
+                            "unblocked LU flops of the 32-column sub-panels vs the FP32 FMA rate"),
+        "panel_kernel": ("alu", lw["panel"], fp32, "TFLOP/s",
+                         "unblocked LU flops of the sub-panels vs the FP32 FMA rate"),
+        "cgemm_simt_kernel (panel update)": ("alu", lw["inner"], fp32, "TFLOP/s",
+                                             "rank-32 updates inside the outer panels vs the FP32 FMA rate"),
+        "swap_trsm_kernel (block row)": ("hbm", lw["swap_bytes"], hbm, "GB/s",
+                                         "row interchanges of the outer panels' 2 NB rows and the U12 blocks, "
+                                         "8-byte complex read + written"),
+        "trsv_g_step_kernel": ("hbm", float(iters) * N * N * 8, hbm, "GB/s",
+                               "the FP32 factors (N^2 x 8 bytes) read once per triangular-solve pair"),
+        "cgemm_tc_kernel (skinny, + split-K reduction)": ("hbm", float(iters) * 4 * N * N * 8, hbm, "GB/s",
+                                                          "[M31 M32] and [M13; M23] in complex FP32 read once per "
+                                                          "correction"),
+    }
+    rows = []
+    for name, launches, ms in prof:
+        if name not in work:
+            continue
+        bound, amount, peak, unit, how = work[name]
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        achieved = amount / (ms * 1e-3) / scale
+        rows.append({"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": None, "launches": launches, "ms_total": ms,
+                     "ms_per_launch": ms / launches, "work_per_step": amount, "work": how,
+                     "frac_note": src})
+    top_name = prof[0][0] if prof else None
+    roof = next((r for r in rows if r["kernel"] == top_name), rows[0] if rows else None)
+    return roof, {"kernels": [r for r in rows if r is not roof]}
 
 
 def run_ours(args, ws, rank, local):
@@ -333,49 +470,29 @@ def run_ours(args, ws, rank, local):
                    "backward_error_mixed": float(max(r[1] for r in rec)),
                    "backward_error_ordinary": float(max(r[2] for r in rec))})
 
-    # ---- roofline of the hot kernels (own events on the library's stream) ----
-    roof = {}
+    # ---- per-kernel breakdown of one factor + solve, and the roofline of the dominant kernel ----
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         src = "of measured"
     except (OSError, ValueError):
-        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
         src = "of fallback"
     N = w.N
+    prof_m = bm.bm_profile(hm, Bm, Xm)
+    prof_o = bm.bm_profile(ho, Bo, Xo)
+    iters_m = int(rec[-1][3])
+    roof, extra = roofline_from_profile(prof_m, N, w.nrhs, prec, iters_m, peaks, src)
+    extra["profile_mixed"] = [{"kernel": k, "launches": l, "ms": m} for k, l, m in prof_m]
+    extra["profile_ordinary"] = [{"kernel": k, "launches": l, "ms": m} for k, l, m in prof_o]
+    # the residual and the Schur product also timed alone, in their normal launch configuration
     reps = 5
-    # FP64 residual (2 complex GEMMs per residual: [M13;M23] x3 and [M31 M32] [x1;x2])
     torch.cuda.synchronize()
     a, b = ev(), ev()
     a.record(stream)
     bm.bm_enqueue_probe(hm, bm.BM_PROBE_RESIDUAL, reps)
     b.record(stream)
     torch.cuda.synchronize()
-    t_res = a.elapsed_time(b) / reps
-    cmacs = 4.0 * N * N * w.nrhs                  # complex multiply-adds of one residual b - A x
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    if prec != 0:
-        # double-float on the FP32 pipe: 36 FP32 instructions per complex multiply-add
-        # (3 real products (re a re x, im a im x, (re a + im a)(re x + im x)) x [TwoProd 2 +
-        # TwoSum 6 + 2 accumulate] + 6 cross-term FMAs); peak = 152 SMs x 128 FP32 lanes x SM
-        # clock (FMA, add and multiply each issue once per lane per cycle)
-        ops = 36.0 * cmacs
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-        roof_res = {"kernel": "resid_df_kernel (double-float residual b - A x on the FP32 pipe, all products in "
-                              "one launch; timed with its iterate split and split-K reduction)", "bound": "alu",
-                    "achieved": ops / (t_res * 1e-3) / 1e12, "peak": peak, "unit": "T FP32-instr/s",
-                    "frac": ops / (t_res * 1e-3) / 1e12 / peak,
-                    "traffic": profiled_traffic("resid_df_star_n2048.md", N), "ms_per_launch": t_res,
-                    "traffic_note": "dram bytes read+written per launch, ncu at N=2048 scaled by (N/2048)^2 "
-                                    "(operator planes); null once the kernel source changed",
-                    "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (unit counts x clock)"}
-    else:
-        flops_res = 8.0 * cmacs
-        peak = 152 * 4 * sm_mhz * 1e6 / 1e12      # 2 DFMA per SM per cycle (1.19 TFLOP/s measured)
-        roof_res = {"kernel": "cgemm_simt_kernel<Z64> x2 (FP64 residual b - A x)", "bound": "alu",
-                    "achieved": flops_res / (t_res * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "frac": flops_res / (t_res * 1e-3) / 1e12 / peak, "traffic": None, "ms_per_launch": t_res / 2,
-                    "peak_source": f"152 SMs x 2 DFMA/cycle x {sm_mhz:.0f} MHz (unit counts x clock)"}
-    # Schur complement on the tensor cores (overwrites U33: re-factor afterwards)
+    extra["residual_alone_ms_per_launch"] = a.elapsed_time(b) / reps
     if prec != 0:
         torch.cuda.synchronize()
         a, b = ev(), ev()
@@ -384,25 +501,11 @@ def run_ours(args, ws, rank, local):
         b.record(stream)
         torch.cuda.synchronize()
         t_schur = a.elapsed_time(b) / reps
-        nprod = 3 if prec == 2 else 1
-        flops = 16.0 * N ** 3 * nprod            # 2N^3 complex MACs x 8 real flops x TF32 products
-        tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
-        roof_tc = {"kernel": "cgemm_tc_kernel (tcgen05 kind::tf32, Schur complement U33)", "bound": "tensor",
-                   "achieved": flops / (t_schur * 1e-3) / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
-                   "frac": flops / (t_schur * 1e-3) / 1e12 / tf32_peak, "traffic": None, "ms_per_launch": t_schur,
-                   "peak_source": f"bf16 burst {src} x 1.1/2.25 (nominal tf32/bf16 dense ratio)",
-                   "flop_count": f"16 N^3 x {nprod} TF32 product(s) per complex 4M product"}
+        tf32 = peaks["bf16_tflops"] * (1.1 / 2.25)
+        extra["schur_alone"] = {"ms_per_launch": t_schur, "tflops_algorithmic_4m": 16.0 * N ** 3 / (t_schur * 1e-3) / 1e12,
+                                "frac_tf32": 16.0 * N ** 3 / (t_schur * 1e-3) / 1e12 / tf32,
+                                "tflops_issued": 16.0 * N ** 3 * (3 if prec == 2 else 1) / (t_schur * 1e-3) / 1e12}
         bm.bm_factor(hm)
-    # dominant kernel of the mixed factor+solve: the one with the larger share of the step
-    share_res = 2 * t_res / (f_m + s_m)
-    if prec != 0 and (t_schur / (f_m + s_m)) > share_res:
-        roof = roof_tc
-        extra = {"fp64_residual": roof_res}
-    else:
-        roof = roof_res
-        extra = {"tensor_schur": roof_tc} if prec != 0 else {}
-    roof = dict(roof)
-    roof["frac_note"] = src
 
     # ---- end to end through the C ABI with pinned host buffers ----
     Bh = colmajor_dev(3 * N, w.nrhs, torch, pinned=True)
@@ -420,15 +523,28 @@ def run_ours(args, ws, rank, local):
     e2e_s = allmax(ws, float(np.median(e2e)))
     hbytes = 3 * N * w.nrhs * 16
 
+    # ---- accuracy against the FP64 path, and the other precisions / residual modes of config 2 ----
+    extras = {}
+    if ws == 1 and not args.no_extras:
+        extras["fp64_path"] = fp64_compare(bm, local, stream, w, Bm, Xm, torch, ev)
+        extras["resid_fp64_all"] = mode_timing(bm, local, stream, w, Bm, torch, ev, prec, bm.BM_RESID_FP64_ALL)
+    asm_evals = float(w.N) * (w.N - 1)          # (H0, H1) pairs: N(N-1)/2 unordered pairs x 2 wavenumbers
+    phases["assembly_mixed_hankel_evals_per_s"] = asm_evals / (phases["assemble_mixed_ms"] * 1e-3)
+    phases["assembly_mixed_write_gbs"] = 4.0 * w.N * w.N * 16 / (phases["assemble_mixed_ms"] * 1e-3) / 1e9
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(W.STAR_N4096, 768 if args.quick else 1024, 2)
-        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu = oracle_sample(w, 64 if args.quick else 128)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "seconds_measured")}
 
     bm.bm_destroy(hm)
     bm.bm_destroy(ho)
+    if ws == 1 and not args.no_extras:
+        extras["circle_n256"] = circle_latency(bm, local, stream, torch, ev)
+        if not args.quick:
+            extras["kite_n16384"] = kite_large(bm, local, stream, torch, ev, args.config5_fp64)
     ssm = None if args.no_ssm else ssm_measure(bm, local)
-    serve = None if args.no_serve else serve_measure(bm, local)
+    serve = None if args.no_serve else serve_measure(bm, local, n_req=args.serve_requests)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -443,11 +559,121 @@ def run_ours(args, ws, rank, local):
                     "d2h_bytes_per_step": hbytes, "ms": e2e_s * 1e3,
                     "path": "bm_factor + bm_solve with pinned host B/X (copies inside bm_solve)"},
             "clocks": clk.summary(), "gpu_launches": int(launches)}
+    line.update(extras)
     if ssm is not None:
         line["ssm"] = ssm
     if serve is not None:
         line["serving"] = serve
     print(json.dumps(line), flush=True)
+
+
+def _time_factor_solve(bm, h, B, X, stream, torch, ev, steps: int, warmup: int = 1):
+    """Median factor + solve device time (ms) of a handle, with the last solve's report."""
+    info = None
+    for _ in range(warmup):
+        bm.bm_factor(h)
+        info = bm.bm_solve(h, B, X)
+    t = []
+    for _ in range(steps):
+        a, b, c = ev(), ev(), ev()
+        a.record(stream)
+        assert bm.bm_factor(h) == 0
+        b.record(stream)
+        info = bm.bm_solve(h, B, X)
+        c.record(stream)
+        torch.cuda.synchronize()
+        t.append((a.elapsed_time(b), b.elapsed_time(c)))
+    f = float(np.median([x[0] for x in t]))
+    s = float(np.median([x[1] for x in t]))
+    return f, s, info
+
+
+def fp64_compare(bm, device, stream, w, Bm, Xm, torch, ev):
+    """The FP64 path on the same system and right-hand sides: its factor + solve time, and the
+    forward relative error of the benchmark's refined CF32 solution against it (per column, the
+    largest), which is the metric's "relerr"."""
+    h = bm.bm_create(device, stream.cuda_stream)
+    try:
+        bm.bm_assemble(h, w.curve.kind, w.curve.params4(), w.N, w.k_out, w.k_in, bm.BM_MIXED, bm.make_opts(0))
+        X64 = colmajor_dev(3 * w.N, w.nrhs, torch)
+        f, s, info = _time_factor_solve(bm, h, Bm, X64, stream, torch, ev, steps=3)
+        d = (Xm - X64).abs().pow(2).sum(0).sqrt() / X64.abs().pow(2).sum(0).sqrt()
+        return {"factor_ms": f, "solve_ms": s, "ms": f + s, "solves_per_s": w.nrhs / ((f + s) * 1e-3),
+                "backward_error": info.backward_error,
+                "relerr_cf32_vs_fp64_max_col": float(d.max().item()),
+                "relerr_cf32_vs_fp64_plane_wave": float(d[0].item()),
+                "note": "relerr = ||x_cf32 - x_fp64||_2 / ||x_fp64||_2 per right-hand side over all 3N unknowns"}
+    finally:
+        bm.bm_destroy(h)
+
+
+def mode_timing(bm, device, stream, w, Bm, torch, ev, prec, resid_mode):
+    """Factor + solve of config 2 with another refinement-residual mode (every residual in FP64)."""
+    h = bm.bm_create(device, stream.cuda_stream)
+    try:
+        bm.bm_assemble(h, w.curve.kind, w.curve.params4(), w.N, w.k_out, w.k_in, bm.BM_MIXED,
+                       bm.make_opts(prec, residual=resid_mode))
+        X = colmajor_dev(3 * w.N, w.nrhs, torch)
+        f, s, info = _time_factor_solve(bm, h, Bm, X, stream, torch, ev, steps=3)
+        return {"refine_residual": int(resid_mode), "factor_ms": f, "solve_ms": s, "ms": f + s,
+                "solves_per_s": w.nrhs / ((f + s) * 1e-3), "iterations": info.iterations,
+                "backward_error": info.backward_error, "t_residual_ms": info.t_residual_ms}
+    finally:
+        bm.bm_destroy(h)
+
+
+def circle_latency(bm, device, stream, torch, ev):
+    """Config 1 (section 5.1 shape): circle R = 1, N = 256, k0 = 2, k1 = 3, one plane wave, FP64;
+    factor + solve latency of the direct-indirect (768 unknowns, Schur path) and ordinary (512)
+    systems, median of 20 after 3 warm-ups."""
+    out = {"workload": "circle R=1, N=256, k_out=2, k_in=3, 1 plane wave, FP64"}
+    for name, form in (("mixed", bm.BM_MIXED), ("ordinary", bm.BM_ORDINARY)):
+        h = bm.bm_create(device, stream.cuda_stream)
+        try:
+            bm.bm_assemble(h, W.CIRCLE, (1.0, 0.0, 0.0, 0.0), 256, 2.0, 3.0, form, bm.make_opts(0))
+            nsys = 768 if form == bm.BM_MIXED else 512
+            B = colmajor_dev(nsys, 1, torch)
+            bm.bm_rhs_plane_wave(h, [0.0], B)
+            X = colmajor_dev(nsys, 1, torch)
+            f, s, info = _time_factor_solve(bm, h, B, X, stream, torch, ev, steps=20, warmup=3)
+            out[name] = {"factor_us": f * 1e3, "solve_us": s * 1e3, "us": (f + s) * 1e3,
+                         "backward_error": info.backward_error}
+        finally:
+            bm.bm_destroy(h)
+    out["speedup_mixed_over_ordinary"] = out["ordinary"]["us"] / out["mixed"]["us"]
+    return out
+
+
+def kite_large(bm, device, stream, torch, ev, with_fp64: bool):
+    """Config 5: kite, N = 16384 (mixed 49152 unknowns as four 16384^2 blocks; ordinary 32768^2),
+    k0 = 100, k1 = 150, 1 plane wave + 7 Gaussian RHS (seed 0); complex 3xTF32 factors + refinement
+    to 1e-9 for both formulations (and the FP64 mixed path when asked: about a minute)."""
+    w = W.KITE_N16384
+    out = {"workload": "kite N=16384, k_out=100, k_in=150, 1 plane wave + 7 Gaussian RHS (seed 0)"}
+    runs = [("mixed_3xtf32", bm.BM_MIXED, 2), ("ordinary_3xtf32", bm.BM_ORDINARY, 2)]
+    if with_fp64:
+        runs.append(("mixed_fp64", bm.BM_MIXED, 0))
+    for name, form, prec in runs:
+        h = bm.bm_create(device, stream.cuda_stream)
+        try:
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(stream)
+            bm.bm_assemble(h, w.curve.kind, w.curve.params4(), w.N, w.k_out, w.k_in, form, bm.make_opts(prec))
+            b.record(stream)
+            torch.cuda.synchronize()
+            B = build_rhs(bm, h, w, form, torch)
+            X = colmajor_dev(B.shape[0], w.nrhs, torch)
+            steps = 1 if prec == 0 else 3
+            f, s, info = _time_factor_solve(bm, h, B, X, stream, torch, ev, steps=steps, warmup=1)
+            out[name] = {"assemble_ms": a.elapsed_time(b), "factor_ms": f, "solve_ms": s, "ms": f + s,
+                         "solves_per_s": w.nrhs / ((f + s) * 1e-3), "iterations": info.iterations,
+                         "backward_error": info.backward_error, "steps": steps}
+        finally:
+            bm.bm_destroy(h)
+            torch.cuda.synchronize()
+    out["speedup_mixed_over_ordinary_3xtf32"] = out["ordinary_3xtf32"]["ms"] / out["mixed_3xtf32"]["ms"]
+    return out
 
 
 def ssm_measure(bm, device: int):
@@ -474,12 +700,12 @@ def ssm_measure(bm, device: int):
     return out
 
 
-def serve_measure(bm, device: int, n_req: int = 120, slots: int = 8):
+def serve_measure(bm, device: int, n_req: int = 300, slots: int = 8, loads=(0.5, 0.8, 1.0)):
     """Serving stream (first n_req requests of workloads.serving_stream, seed 0: star curves, N in
     {256 .. 8192}, complex k_out, k_in = 1.5 k_out, 1..64 Gaussian right-hand sides each, mixed
     system, 3xTF32 + refinement to 1e-9).  Capacity: all requests submitted at once, wall time to
-    drain.  Latency: the same requests arriving as a Poisson process at 0.8 x that capacity;
-    p50 / p99 of submit-to-done."""
+    drain.  Latency: the same requests arriving as a Poisson process at each load x that capacity;
+    p50 / p99 of submit-to-done per load."""
     reqs = W.serving_stream(n_req, seed=0)
     Bs = [np.asfortranarray(W.place_rhs(W.gaussian_g(r["N"], r["nrhs"], 1000 + i), r["N"], W.MIXED))
           for i, r in enumerate(reqs)]
@@ -506,19 +732,25 @@ def serve_measure(bm, device: int, n_req: int = 120, slots: int = 8):
     res, wall, st = run([0.0] * n_req)
     cap = n_req / wall
     nrhs_tot = sum(r["nrhs"] for r in reqs)
-    lam = 0.8 * cap
-    arrivals = [r["t"] / lam for r in reqs]
-    res2, wall2, st2 = run(arrivals)
-    lat = np.array([r.t_queue_ms + r.t_service_ms for r in res2])
-    return {"workload": f"first {n_req} requests of the serving stream (seed 0): star curves, N in "
+    sweep = []
+    worst = max(r.backward_error for r in res)
+    mif, mifb = st.max_in_flight, st.max_in_flight_bytes
+    for load in loads:
+        lam = load * cap
+        res2, wall2, st2 = run([r["t"] / lam for r in reqs])
+        lat = np.array([r.t_queue_ms + r.t_service_ms for r in res2])
+        sweep.append({"load": load, "rate_requests_per_s": lam, "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "solves_per_s": nrhs_tot / wall2})
+        worst = max(worst, max(r.backward_error for r in res2))
+        mif, mifb = max(mif, st2.max_in_flight), max(mifb, st2.max_in_flight_bytes)
+    at08 = min(sweep, key=lambda x: abs(x["load"] - 0.8))
+    return {"workload": f"first {n_req} of the 2000 requests of the serving stream (seed 0): star curves, N in "
                         "{256..8192}, Re k_out in [2, 40], Im in [-0.5, 0], k_in = 1.5 k_out, nrhs 1..64; "
                         "mixed system, 3xTF32 + refinement to 1e-9",
             "slots": slots, "capacity_requests_per_s": cap, "capacity_solves_per_s": nrhs_tot / wall,
-            "poisson_rate_requests_per_s": lam, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "solves_per_s_at_rate": nrhs_tot / wall2,
-            "max_backward_error": max(r.backward_error for r in res + res2),
-            "max_in_flight": max(st.max_in_flight, st2.max_in_flight),
-            "max_in_flight_gb": max(st.max_in_flight_bytes, st2.max_in_flight_bytes) / 1e9,
+            "poisson_rate_requests_per_s": at08["rate_requests_per_s"], "p50_ms": at08["p50_ms"],
+            "p99_ms": at08["p99_ms"], "solves_per_s_at_rate": at08["solves_per_s"], "load_sweep": sweep,
+            "max_backward_error": worst, "max_in_flight": mif, "max_in_flight_gb": mifb / 1e9,
             "budget_gb": st.budget_bytes / 1e9}
 
 
@@ -532,6 +764,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ssm", action="store_true", help="skip the contour-batch (Sakurai-Sugiura) timing")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-stream timing")
+    ap.add_argument("--serve-requests", type=int, default=300, help="requests of the serving stream to run")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 comparison, the residual-mode timing and configs 1 and 5")
+    ap.add_argument("--config5-fp64", action="store_true", help="also time the FP64 mixed path at N=16384")
     ap.add_argument("--quick", action="store_true", help="N=1024 instead of 4096 (smoke-sized)")
     ap.add_argument("--n", type=int, default=0, help="another N for the same star workload (profiling sizes)")
     args = ap.parse_args()

@@ -378,6 +378,22 @@ bm_status bm_hankel_anchor_table(double* out, int cap_anchors, int* nx, int* ny,
 enum { BM_PROBE_SCHUR = 0, BM_PROBE_RESIDUAL = 1 };
 bm_status bm_enqueue_probe(bm_ctx* ctx, int which, int reps);
 
+/* Per-kernel device times of one factorisation and solve (a diagnostic; the paper has no
+ * counterpart).  Runs bm_factor, then bm_solve(nrhs, B, ldb, X, ldx, on_device), with every kernel
+ * launched directly (no graph replay) and each launch bracketed by two events on the handle's
+ * stream, and reports the launches grouped by kernel name: count and summed device time.  The
+ * factors and X are those of a normal call; the times add up to the serial device time of the two
+ * calls (kernels that a normal call overlaps are timed one after another here).
+ *  out: cap entries (may be NULL to query the count); *count receives the number of groups.
+ * Errors: those of bm_factor and bm_solve. */
+typedef struct {
+    char name[64];
+    int launches;
+    double ms;
+} bm_kernel_time;
+bm_status bm_profile(bm_ctx* ctx, int nrhs, const bm_c64* B, int ldb, bm_c64* X, int ldx, int on_device,
+                     bm_kernel_time* out, int cap, int* count);
+
 /* Number of CUDA kernels this handle has launched so far (kernel nodes of every replayed CUDA
  * graph plus kernels launched outside graphs). */
 bm_status bm_kernel_launches(bm_ctx* ctx, unsigned long long* count);

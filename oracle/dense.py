@@ -25,9 +25,11 @@ class SingularMatrix(Exception):
         self.col = col
 
 
-def lu_factor(A: np.ndarray):
-    """In-place style unblocked LU with partial pivoting: returns (LU, piv) with
-    P A = L U, L unit lower (strictly below the diagonal of LU), piv[k] = row swapped with k."""
+def lu_factor_columns(A: np.ndarray):
+    """The elimination of ``lu_factor`` one column at a time: a generator that yields the column
+    index k after eliminating column k, and finally returns (LU, piv) (as StopIteration.value).
+    The arithmetic is exactly lu_factor's; the generator form only lets a caller time or pause the
+    factorisation between columns."""
     LU = np.array(A, dtype=np.complex128, copy=True)
     n = LU.shape[0]
     piv = np.arange(n)
@@ -41,7 +43,19 @@ def lu_factor(A: np.ndarray):
             LU[[k, p], :] = LU[[p, k], :]
         LU[k + 1:, k] /= LU[k, k]
         LU[k + 1:, k + 1:] -= np.outer(LU[k + 1:, k], LU[k, k + 1:])
+        yield k
     return LU, piv
+
+
+def lu_factor(A: np.ndarray):
+    """In-place style unblocked LU with partial pivoting: returns (LU, piv) with
+    P A = L U, L unit lower (strictly below the diagonal of LU), piv[k] = row swapped with k."""
+    g = lu_factor_columns(A)
+    while True:
+        try:
+            next(g)
+        except StopIteration as done:
+            return done.value
 
 
 def lu_solve(LU: np.ndarray, piv: np.ndarray, B: np.ndarray) -> np.ndarray:

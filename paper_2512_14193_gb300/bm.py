@@ -72,6 +72,10 @@ class bm_result(C.Structure):
                 ("t_queue_ms", C.c_double), ("t_service_ms", C.c_double), ("bytes", C.c_size_t)]
 
 
+class bm_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 64), ("launches", C.c_int), ("ms", C.c_double)]
+
+
 class bm_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_ulonglong), ("completed", C.c_ulonglong), ("max_in_flight_bytes", C.c_size_t),
                 ("max_in_flight", C.c_int), ("budget_bytes", C.c_size_t)]
@@ -119,6 +123,7 @@ def lib():
     L.bm_memory.argtypes = [P, C.POINTER(S), C.POINTER(S)]
     L.bm_kernel_launches.argtypes = [P, C.POINTER(C.c_ulonglong)]
     L.bm_enqueue_probe.argtypes = [P, I, I]
+    L.bm_profile.argtypes = [P, I, P, I, P, I, I, C.POINTER(bm_kernel_time), I, C.POINTER(I)]
     L.bm_destroy.argtypes = [P]
     L.bm_strerror.argtypes = [I]
     L.bm_strerror.restype = C.c_char_p
@@ -130,7 +135,7 @@ def lib():
                  "bm_server_stats_get", "bm_server_destroy",
                  "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_zeta_weights", "bm_memory",
                  "bm_destroy",
-                 "bm_kernel_launches", "bm_enqueue_probe"):
+                 "bm_kernel_launches", "bm_enqueue_probe", "bm_profile"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -473,3 +478,19 @@ def bm_strerror(status: int) -> str:
 
 def bm_last_error() -> str:
     return lib().bm_last_error().decode()
+
+
+def bm_profile(h, B, X):
+    """Per-kernel device times of one bm_factor + bm_solve(B, X): a list of (name, launches, ms),
+    largest first (every kernel launched directly and bracketed by events)."""
+    pb, ldb, nb, devb, _kb = _colmajor(B, 0, writable=False)
+    px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=True)
+    if devb != devx or nb != nx:
+        raise ValueError("B and X must live on the same side and have the same number of columns")
+    ns = _nsys.get(_hkey(h), 0)
+    _need(_kb.shape[0] >= ns and _kx.shape[0] >= ns, "B and X need at least the system's rows")
+    cap = 64
+    out = (bm_kernel_time * cap)()
+    n = C.c_int(0)
+    _check(lib().bm_profile(h, nb, pb, ldb, px, ldx, devb, out, cap, C.byref(n)), "bm_profile")
+    return [(out[i].name.decode(), int(out[i].launches), float(out[i].ms)) for i in range(min(n.value, cap))]

@@ -636,19 +636,26 @@ bm_status factor_sequence(bm_ctx* c) {
         Z64 F{c->d_F64, c->ldF};
         if (c->form == BM_MIXED) {
             // U33 = -[M31 M32] [M13; M23]
+            BM_PROF(c, "cgemm_simt_kernel<Z64> (Schur complement)");
             BM_CUDA_TRY(gemm_z64(s, c->N, c->N, 2 * c->N, -1.0, Z64{c->d_Mbot, c->ldbot}, false,
                                  Z64{c->d_Mtop, c->ldtop}, 0.0, F));
         } else {
+            BM_PROF(c, "copy_z64_kernel");
             BM_CUDA_TRY(launch_copy_z64(s, c->d_A, c->ldA, c->n, c->n, c->d_F64, c->ldF));
         }
     } else {
         if (c->form == BM_MIXED) {
             // the FP32 operands of the Schur product, then U33 = -[M31 M32] [M13; M23]
-            BM_CUDA_TRY(launch_pack_schur(s, c, c->prec == BM_CF32_3XTF32_IR));
+            {
+                BM_PROF(c, "pack_schur (pack_rowmajor/colmajor_kernel)");
+                BM_CUDA_TRY(launch_pack_schur(s, c, c->prec == BM_CF32_3XTF32_IR));
+            }
             long kext = (c->prec == BM_CF32_3XTF32_IR) ? 3L * c->kseg_schur : c->kseg_schur;
+            BM_PROF(c, "cgemm_tc_kernel (Schur complement)");
             BM_CUDA_TRY(gemm_tc(s, c->tm_schur[0], c->tm_schur[1], c->tm_schur[2], c->tm_schur[3], c->d_F32r,
                                 c->d_F32i, c->ldF, c->N, c->N, (int)kext, -1.0f, 0.0f, c->d_err));
         } else {
+            BM_PROF(c, "to_c32_kernel");
             BM_CUDA_TRY(launch_to_c32(s, c->d_A, c->ldA, c->n, c->n, c->d_F32r, c->d_F32i, c->ldF));
         }
     }
@@ -671,7 +678,7 @@ int count_kernel_nodes(cudaGraph_t g) {
 // Run `fn` through a cached CUDA graph (captured on first use), or eagerly if graphs are off.
 template <class Fn>
 bm_status run_captured(bm_ctx* c, bm_ctx::GraphSlot* slot, Fn fn) {
-    if (c->eager) return fn();
+    if (c->eager || c->prof) return fn();
     if (slot->exec == nullptr) {
         cudaGraph_t g = nullptr;
         BM_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -1138,5 +1145,49 @@ extern "C" bm_status bm_hankel01(bm_ctx* c, const bm_c64* z, int n, bm_c64* h0, 
         bm_set_error(std::string("hankel probe: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
         return BM_ECUDA;
     }
+    return BM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+extern "C" bm_status bm_profile(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_c64* X, int ldx, int on_device,
+                                bm_kernel_time* out, int cap, int* count) {
+    if (c == nullptr || count == nullptr || cap < 0) return BM_EINVAL;
+    *count = 0;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    std::vector<bm_ctx::ProfRec> recs;
+    c->prof = &recs;
+    int info = 0;
+    bm_status st = bm_factor(c, &info);
+    if (st == BM_OK) st = bm_solve(c, nrhs, B, ldb, X, ldx, on_device, nullptr);
+    c->prof = nullptr;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    std::vector<std::pair<std::string, std::pair<int, double>>> groups;
+    for (auto& r : recs) {
+        float ms = 0.f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, r.a, r.b);
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+        auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& g) { return g.first == r.name; });
+        if (it == groups.end()) {
+            groups.push_back({r.name, {1, (double)ms}});
+        } else {
+            it->second.first += 1;
+            it->second.second += ms;
+        }
+    }
+    if (st != BM_OK) return st;
+    if (e != cudaSuccess) {
+        bm_set_error(std::string("bm_profile: ") + cudaGetErrorString(e));
+        return BM_ECUDA;
+    }
+    std::sort(groups.begin(), groups.end(), [](const auto& a, const auto& b) { return a.second.second > b.second.second; });
+    *count = (int)groups.size();
+    if (out)
+        for (int i = 0; i < std::min(cap, (int)groups.size()); ++i) {
+            std::memset(out[i].name, 0, sizeof(out[i].name));
+            std::strncpy(out[i].name, groups[i].first.c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = groups[i].second.first;
+            out[i].ms = groups[i].second.second;
+        }
     return BM_OK;
 }

@@ -289,7 +289,37 @@ struct bm_ctx {
     bool eager = false;          // bm_opts.eager: no CUDA graphs
     int opt_cluster_cap = 0;     // bm_opts.panel_cluster_max / panel_kernel of the assembled system
     int opt_panel_kernel = 0;
+
+    // per-kernel timing (bm_profile): while set, every launch is bracketed by two events on the
+    // handle's stream and recorded here (graphs are bypassed)
+    struct ProfRec {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    std::vector<ProfRec>* prof = nullptr;
 };
+
+// Brackets the launches of its scope with events when the handle is profiling (else nothing).
+struct ProfScope {
+    bm_ctx* c;
+    const char* name;
+    cudaEvent_t a = nullptr;
+    ProfScope(bm_ctx* c_, const char* n) : c(c_), name(n) {
+        if (c->prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, c->stream);
+    }
+    ~ProfScope() {
+        cudaEvent_t b = nullptr;
+        if (c->prof && a && cudaEventCreate(&b) == cudaSuccess) {
+            cudaEventRecord(b, c->stream);
+            c->prof->push_back({name, a, b});
+        }
+    }
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+};
+#define BM_PROF_CAT2(a, b) a##b
+#define BM_PROF_CAT(a, b) BM_PROF_CAT2(a, b)
+#define BM_PROF(ctx, name) ProfScope BM_PROF_CAT(bm_prof_, __LINE__)(ctx, name)
 
 // allocation helpers (api.cu)
 bm_status ctx_alloc(bm_ctx* c, void** p, size_t bytes);

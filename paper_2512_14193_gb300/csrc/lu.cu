@@ -727,8 +727,11 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
     const int cl_max = c->panel_cluster;
     SwapMap* d_map = reinterpret_cast<SwapMap*>(c->d_maps);  // big-panel map
     SwapMap* d_map2 = d_map + 1;                              // sub-panel map
-    iota_kernel<<<ceil_div(n, 256), 256, 0, s>>>(c->d_perm, n);
-    LU_CUDA(cudaGetLastError());
+    {
+        BM_PROF(c, "iota");
+        iota_kernel<<<ceil_div(n, 256), 256, 0, s>>>(c->d_perm, n);
+        LU_CUDA(cudaGetLastError());
+    }
     for (int J = 0; J < n; J += NB) {
         const int jb = std::min(NB, n - J);
         for (int j = J; j < J + jb;) {
@@ -738,31 +741,48 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
                 return BM_EINVAL;
             }
             const int ib = std::min(ps.nbp, J + jb - j);
-            LU_CUDA(launch_panel(s, F, ps, j, n - j, ib, c->d_ipiv, c->d_info, J, jb, d_map2, d_map, c->d_perm));
+            {
+                BM_PROF(c, ps.RPW ? "panel_lc_kernel" : "panel_kernel");
+                LU_CUDA(launch_panel(s, F, ps, j, n - j, ib, c->d_ipiv, c->d_info, J, jb, d_map2, d_map, c->d_perm));
+            }
             if (jb > ib) {
-                LU_CUDA(launch_swap_trsm<V>(s, F, d_map2, J, j, j + ib, J + jb, j, ib, nullptr, nullptr, 0, 0));
-                if (j + ib < J + jb)
+                {
+                    BM_PROF(c, "swap_trsm_kernel (sub-panel)");
+                    LU_CUDA(launch_swap_trsm<V>(s, F, d_map2, J, j, j + ib, J + jb, j, ib, nullptr, nullptr, 0, 0));
+                }
+                if (j + ib < J + jb) {
+                    BM_PROF(c, "cgemm_simt_kernel (panel update)");
                     LU_CUDA(gemm_any(s, n - j - ib, J + jb - j - ib, ib, F.sub(j + ib, j), F.sub(j, j + ib),
                                      F.sub(j + ib, j + ib)));
+                }
             }
             j += ib;
         }
         const bool pack = tc && (J + jb < n);
-        LU_CUDA(launch_swap_trsm<V>(s, F, d_map, 0, J, J + jb, n, J, jb, pack ? c->d_Up_r : nullptr,
-                                    pack ? c->d_Up_i : nullptr, c->ldk_lu, split));
+        {
+            BM_PROF(c, "swap_trsm_kernel (block row)");
+            LU_CUDA(launch_swap_trsm<V>(s, F, d_map, 0, J, J + jb, n, J, jb, pack ? c->d_Up_r : nullptr,
+                                        pack ? c->d_Up_i : nullptr, c->ldk_lu, split));
+        }
         if (J + jb < n) {
             const int mm = n - J - jb;
             if (tc) {
                 if constexpr (std::is_same<V, C32>::value) {
                     dim3 blk(32, 8), grid(ceil_div(jb, 32), ceil_div(mm, 32));
-                    pack_L_kernel<<<grid, blk, 0, s>>>(F, J + jb, J, mm, jb, split, c->d_Lp_r, c->d_Lp_i, c->ldk_lu);
-                    LU_CUDA(cudaGetLastError());
+                    {
+                        BM_PROF(c, "pack_L_kernel");
+                        pack_L_kernel<<<grid, blk, 0, s>>>(F, J + jb, J, mm, jb, split, c->d_Lp_r, c->d_Lp_i,
+                                                           c->ldk_lu);
+                        LU_CUDA(cudaGetLastError());
+                    }
                     int kext = split ? 3 * jb : jb;
                     C32 Cv = F.sub(J + jb, J + jb);
+                    BM_PROF(c, "cgemm_tc_kernel (trailing update)");
                     LU_CUDA(gemm_tc(s, c->tm_lu[0], c->tm_lu[1], c->tm_lu[2], c->tm_lu[3], Cv.re, Cv.im, Cv.ld, mm, mm,
                                     kext, -1.0f, 1.0f, c->d_err));
                 }
             } else {
+                BM_PROF(c, "cgemm_simt_kernel (trailing update)");
                 LU_CUDA(gemm_any(s, mm, mm, jb, F.sub(J + jb, J), F.sub(J, J + jb), F.sub(J + jb, J + jb)));
             }
         }
@@ -778,11 +798,15 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
     using CV = typename V::cv;
     LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tri_inv_kernel<V, false><<<nblk, 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvL));
-    tri_inv_kernel<V, true><<<nblk, 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvU));
-    LU_CUDA(cudaGetLastError());
+    {
+        BM_PROF(c, "tri_inv_kernel");
+        tri_inv_kernel<V, false><<<nblk, 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvL));
+        tri_inv_kernel<V, true><<<nblk, 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvU));
+        LU_CUDA(cudaGetLastError());
+    }
     if constexpr (std::is_same<V, C32>::value) {
         if (nblk > 1) {
+            BM_PROF(c, "g_form_kernel");
             const size_t gsm = 2 * (size_t)TS_BM * TS_BM * sizeof(CV);
             LU_CUDA(cudaFuncSetAttribute(g_form_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
             g_form_kernel<V><<<dim3(nblk, nblk), 256, gsm, s>>>(F, n, reinterpret_cast<const CV*>(c->d_dinvL),
@@ -847,13 +871,19 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* din
         };
         for (int b = 0; b + 1 < nblk; ++b) {  // Y[below b] -= G_L Y_b
             int r0 = b * bs, rb = std::min(bs, n - r0);
+            BM_PROF(c, "trsv_g_step_kernel");
             LU_CUDA(gstep(Y, r0, rb, r0 + rb, n - r0 - rb));
         }
-        LU_CUDA(diag(Y, Zw, dinvL));  // Zw = L^{-1} P B
+        {
+            BM_PROF(c, "trsv_diag_kernel");
+            LU_CUDA(diag(Y, Zw, dinvL));  // Zw = L^{-1} P B
+        }
         for (int b = nblk - 1; b > 0; --b) {  // Zw[above b] -= G_U Zw_b
             int r0 = b * bs, rb = std::min(bs, n - r0);
+            BM_PROF(c, "trsv_g_step_kernel");
             LU_CUDA(gstep(Zw, r0, rb, 0, r0));
         }
+        BM_PROF(c, "trsv_diag_kernel");
         LU_CUDA(diag(Zw, Y, dinvU));  // Y = U^{-1} Zw
     } else {
         auto step = [&](V Yv, V Zv, int r0, int rb, int rest0, int nrest, const typename V::cv* T) {
@@ -862,10 +892,12 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* din
         };
         for (int b = 0; b < nblk; ++b) {  // Zw = L^{-1} Y
             int r0 = b * bs, rb = std::min(bs, n - r0);
+            BM_PROF(c, "trsv_step_kernel");
             LU_CUDA(step(Y, Zw, r0, rb, r0 + rb, n - r0 - rb, dinvL + (long)b * bs * bs));
         }
         for (int b = nblk - 1; b >= 0; --b) {  // Y = U^{-1} Zw
             int r0 = b * bs, rb = std::min(bs, n - r0);
+            BM_PROF(c, "trsv_step_kernel");
             LU_CUDA(step(Zw, Y, r0, rb, 0, r0, dinvU + (long)b * bs * bs));
         }
     }

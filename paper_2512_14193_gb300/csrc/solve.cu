@@ -164,20 +164,44 @@ bm_status solve_fp64(bm_ctx* c, const double2* B, double2* X, long ld, int nrhs)
     const long ldy = c->n;
     if (c->form == BM_MIXED) {
         // t3 = b3 - [M31 M32] [b1; b2]
-        SV_CUDA(copy_z64(s, B + 2 * N, ld, N, nrhs, c->d_Y64b, ldy));
-        SV_CUDA(gemm_z64(s, N, nrhs, 2 * N, -1.0, Z64{c->d_Mbot, c->ldbot}, false, Z64{const_cast<double2*>(B), ld},
-                         1.0, Z64{c->d_Y64b, ldy}));
-        SV_CUDA(launch_gather_rows_z64(s, c->d_perm, N, nrhs, c->d_Y64b, ldy, c->d_Y64, ldy));
+        {
+            BM_PROF(c, "copy_z64_kernel");
+            SV_CUDA(copy_z64(s, B + 2 * N, ld, N, nrhs, c->d_Y64b, ldy));
+        }
+        {
+            BM_PROF(c, "cgemm_simt_kernel<Z64> (solve product)");
+            SV_CUDA(gemm_z64(s, N, nrhs, 2 * N, -1.0, Z64{c->d_Mbot, c->ldbot}, false, Z64{const_cast<double2*>(B), ld},
+                             1.0, Z64{c->d_Y64b, ldy}));
+        }
+        {
+            BM_PROF(c, "gather_rows_kernel");
+            SV_CUDA(launch_gather_rows_z64(s, c->d_perm, N, nrhs, c->d_Y64b, ldy, c->d_Y64, ldy));
+        }
         BM_TRY(getrs_z64(c, c->d_Y64, ldy, nrhs));
-        SV_CUDA(copy_z64(s, c->d_Y64, ldy, N, nrhs, X + 2 * N, ld));
+        {
+            BM_PROF(c, "copy_z64_kernel");
+            SV_CUDA(copy_z64(s, c->d_Y64, ldy, N, nrhs, X + 2 * N, ld));
+        }
         // [x1; x2] = [b1; b2] - [M13; M23] z3
-        SV_CUDA(copy_z64(s, B, ld, 2 * N, nrhs, X, ld));
-        SV_CUDA(gemm_z64(s, 2 * N, nrhs, N, -1.0, Z64{c->d_Mtop, c->ldtop}, false, Z64{X + 2 * N, ld}, 1.0,
-                         Z64{X, ld}));
+        {
+            BM_PROF(c, "copy_z64_kernel");
+            SV_CUDA(copy_z64(s, B, ld, 2 * N, nrhs, X, ld));
+        }
+        {
+            BM_PROF(c, "cgemm_simt_kernel<Z64> (solve product)");
+            SV_CUDA(gemm_z64(s, 2 * N, nrhs, N, -1.0, Z64{c->d_Mtop, c->ldtop}, false, Z64{X + 2 * N, ld}, 1.0,
+                             Z64{X, ld}));
+        }
     } else {
-        SV_CUDA(launch_gather_rows_z64(s, c->d_perm, c->n, nrhs, B, ld, c->d_Y64, ldy));
+        {
+            BM_PROF(c, "gather_rows_kernel");
+            SV_CUDA(launch_gather_rows_z64(s, c->d_perm, c->n, nrhs, B, ld, c->d_Y64, ldy));
+        }
         BM_TRY(getrs_z64(c, c->d_Y64, ldy, nrhs));
-        SV_CUDA(copy_z64(s, c->d_Y64, ldy, c->n, nrhs, X, ld));
+        {
+            BM_PROF(c, "copy_z64_kernel");
+            SV_CUDA(copy_z64(s, c->d_Y64, ldy, c->n, nrhs, X, ld));
+        }
     }
     return BM_OK;
 }
@@ -188,8 +212,12 @@ bm_status residual_fp64(bm_ctx* c, const double2* B, const double2* X, double2* 
     const int N = c->N;
     long t = (long)c->nsys * nrhs;
     int nsub = (c->form == BM_MIXED) ? 2 * N : 0;
-    resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
-    SV_CUDA(cudaGetLastError());
+    {
+        BM_PROF(c, "resid_init_kernel");
+        resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
+        SV_CUDA(cudaGetLastError());
+    }
+    BM_PROF(c, "cgemm_simt_kernel<Z64> (FP64 residual)");
     if (c->form == BM_MIXED) {
         SV_CUDA(gemm_z64(s, 2 * N, nrhs, N, -1.0, Z64{c->d_Mtop, c->ldtop}, false,
                          Z64{const_cast<double2*>(X) + 2 * N, ld}, 1.0, Z64{R, ld}));
@@ -210,10 +238,17 @@ bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R,
     const int N = c->N;
     long t = (long)c->nsys * nrhs;
     int nsub = (c->form == BM_MIXED) ? 2 * N : 0;
-    resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
-    SV_CUDA(cudaGetLastError());
+    {
+        BM_PROF(c, "resid_init_kernel");
+        resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
+        SV_CUDA(cudaGetLastError());
+    }
     const long ldp = c->nsys;
-    SV_CUDA(launch_split_planes(s, X, ld, c->nsys, nrhs, c->d_XP, c->d_XQ, ldp));
+    {
+        BM_PROF(c, "split_planes_kernel (iterate)");
+        SV_CUDA(launch_split_planes(s, X, ld, c->nsys, nrhs, c->d_XP, c->d_XQ, ldp));
+    }
+    BM_PROF(c, "resid_df_kernel (+ split-K reduction)");
     // K splits chosen so every work unit spans K = N: the K = 2N products are split in two
     int nl = 0;
     if (c->form == BM_MIXED) {
@@ -234,6 +269,7 @@ bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const do
                          double* d_eta) {
     SV_CUDA(cudaMemsetAsync(d_eta, 0, 2 * sizeof(double), c->stream));
     // one CTA of 1024 threads per column (few columns: the loads in flight per SM set the time)
+    BM_PROF(c, "eta_kernel");
     eta_kernel<<<nrhs, 1024, 0, c->stream>>>(R, X, B, ld, c->nsys, c->d_normA, d_eta);
     SV_CUDA(cudaGetLastError());
     return BM_OK;
@@ -250,8 +286,11 @@ bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int n
     float* Vi = c->d_W2i;
     const long ldv = c->n;
     long t = (long)c->nsys * nrhs;
-    to_c32_kernel<<<ceil_div(t, 256), 256, 0, s>>>(R, ld, c->nsys, nrhs, Wr, Wi, ldw);
-    SV_CUDA(cudaGetLastError());
+    {
+        BM_PROF(c, "to_c32_kernel");
+        to_c32_kernel<<<ceil_div(t, 256), 256, 0, s>>>(R, ld, c->nsys, nrhs, Wr, Wi, ldw);
+        SV_CUDA(cudaGetLastError());
+    }
     const bool split = (c->prec == BM_CF32_3XTF32_IR);
     if (c->form == BM_MIXED && c->tc_skinny) {
         // the two skinny products on the tensor cores, split over K (few output tiles)
@@ -259,18 +298,34 @@ bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int n
         int nl = 0;
         // W3 -= [M31 M32] [W1; W2]
         const long k1 = split ? 3L * K : (long)K;
-        SV_CUDA(launch_pack_b(s, Wr, Wi, ldw, K, nrhs, split, c->d_Bx1r, c->d_Bx1i, c->ldk_schur));
-        SV_CUDA(gemm_tc_split(s, c->tm_schur[0], c->tm_schur[1], c->tm_skinny[2], c->tm_skinny[3], N, nrhs, (int)k1,
-                              -1.f, 1.f, TcDest{Wr + 2 * N, Wi + 2 * N, nullptr, ldw},
-                              skinny_split(c, N, nrhs, (int)k1), c->d_Pkr, c->d_Pki, c->d_err, &nl));
-        SV_CUDA(launch_gather_rows_c32(s, c->d_perm, N, nrhs, Wr + 2 * N, Wi + 2 * N, ldw, Vr, Vi, ldv));
+        {
+            BM_PROF(c, "pack_b_kernel");
+            SV_CUDA(launch_pack_b(s, Wr, Wi, ldw, K, nrhs, split, c->d_Bx1r, c->d_Bx1i, c->ldk_schur));
+        }
+        {
+            BM_PROF(c, "cgemm_tc_kernel (skinny, + split-K reduction)");
+            SV_CUDA(gemm_tc_split(s, c->tm_schur[0], c->tm_schur[1], c->tm_skinny[2], c->tm_skinny[3], N, nrhs, (int)k1,
+                                  -1.f, 1.f, TcDest{Wr + 2 * N, Wi + 2 * N, nullptr, ldw},
+                                  skinny_split(c, N, nrhs, (int)k1), c->d_Pkr, c->d_Pki, c->d_err, &nl));
+        }
+        {
+            BM_PROF(c, "gather_rows_kernel");
+            SV_CUDA(launch_gather_rows_c32(s, c->d_perm, N, nrhs, Wr + 2 * N, Wi + 2 * N, ldw, Vr, Vi, ldv));
+        }
         BM_TRY(getrs_c32(c, Vr, Vi, ldv, nrhs));
         // [W1; W2] -= [M13; M23] z3; the pack of z3 stays for the next residual update
         const long k2 = split ? 3L * N : (long)N;
-        SV_CUDA(launch_pack_b(s, Vr, Vi, ldv, N, nrhs, split, c->d_Bx2r, c->d_Bx2i, c->ldk_c));
-        SV_CUDA(gemm_tc_split(s, c->tm_skinny[0], c->tm_skinny[1], c->tm_skinny[4], c->tm_skinny[5], 2 * N, nrhs,
-                              (int)k2, -1.f, 1.f, TcDest{Wr, Wi, nullptr, ldw},
-                              skinny_split(c, 2 * N, nrhs, (int)k2), c->d_Pkr, c->d_Pki, c->d_err, &nl));
+        {
+            BM_PROF(c, "pack_b_kernel");
+            SV_CUDA(launch_pack_b(s, Vr, Vi, ldv, N, nrhs, split, c->d_Bx2r, c->d_Bx2i, c->ldk_c));
+        }
+        {
+            BM_PROF(c, "cgemm_tc_kernel (skinny, + split-K reduction)");
+            SV_CUDA(gemm_tc_split(s, c->tm_skinny[0], c->tm_skinny[1], c->tm_skinny[4], c->tm_skinny[5], 2 * N, nrhs,
+                                  (int)k2, -1.f, 1.f, TcDest{Wr, Wi, nullptr, ldw},
+                                  skinny_split(c, 2 * N, nrhs, (int)k2), c->d_Pkr, c->d_Pki, c->d_err, &nl));
+        }
+        BM_PROF(c, "add_c32_kernel");
         long t2 = (long)K * nrhs;
         add_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(X, ld, 0, K, nrhs, Wr, Wi, ldw);
         long t3 = (long)N * nrhs;
@@ -303,8 +358,12 @@ bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int n
         add_c32_kernel<<<ceil_div(t3, 256), 256, 0, s>>>(X, ld, 2 * N, N, nrhs, Vr, Vi, ldv);
         SV_CUDA(cudaGetLastError());
     } else {
-        SV_CUDA(launch_gather_rows_c32(s, c->d_perm, c->n, nrhs, Wr, Wi, ldw, Vr, Vi, ldv));
+        {
+            BM_PROF(c, "gather_rows_kernel");
+            SV_CUDA(launch_gather_rows_c32(s, c->d_perm, c->n, nrhs, Wr, Wi, ldw, Vr, Vi, ldv));
+        }
         BM_TRY(getrs_c32(c, Vr, Vi, ldv, nrhs));
+        BM_PROF(c, "add_c32_kernel");
         long t2 = (long)c->n * nrhs;
         add_c32_kernel<<<ceil_div(t2, 256), 256, 0, s>>>(X, ld, 0, c->n, nrhs, Vr, Vi, ldv);
         SV_CUDA(cudaGetLastError());
@@ -320,6 +379,7 @@ bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int n
 bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs) {
     cudaStream_t s = c->stream;
     const int N = c->N;
+    BM_PROF(c, "residual update (FP32 products)");
     const long ldw = c->nsys, ldv = c->n;
     if (c->form == BM_MIXED && c->tc_skinny && c->prec == BM_CF32_3XTF32_IR) {
         // 3xTF32 products on the tensor cores (FP32-level accuracy, as the SIMT FP32 update):

@@ -208,3 +208,25 @@ def test_device_arrays_and_repeat_calls(bmlib, handle):
     Xh = np.zeros_like(Bh, order="F")
     bmlib.bm_solve(handle, Bh, Xh)
     assert np.array_equal(X1, Xh)
+
+
+@pytest.mark.gpu
+def test_profile_reports_every_kernel_and_the_same_solution(bmlib, handle):
+    # bm_profile runs the factorisation and solve with every launch timed: the solution is the one a
+    # normal call gives, and the groups cover the method's kernels with positive times
+    curve, N = W.star(1.0, 0.3, 5), 600
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, 6.0, 9.0, bmlib.BM_MIXED,
+                      bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR))
+    assert bmlib.bm_factor(handle) == 0
+    B = np.asfortranarray(W.gaussian_full(3 * N, 3, 2))
+    X1 = np.zeros_like(B, order="F")
+    bmlib.bm_solve(handle, B, X1)
+    X2 = np.zeros_like(B, order="F")
+    prof = bmlib.bm_profile(handle, B, X2)
+    assert np.array_equal(X1, X2)
+    names = {k for k, _, _ in prof}
+    for k in ("cgemm_tc_kernel (Schur complement)", "panel_lc_kernel", "cgemm_tc_kernel (trailing update)",
+              "trsv_g_step_kernel", "resid_df_kernel (+ split-K reduction)", "eta_kernel"):
+        assert k in names, k
+    assert all(l >= 1 and ms > 0 for _, l, ms in prof)
+    assert [ms for _, _, ms in prof] == sorted([ms for _, _, ms in prof], reverse=True)
