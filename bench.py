@@ -336,6 +336,9 @@ def roofline_from_profile(prof, N: int, nrhs: int, prec: int, iters: int, peaks:
         "resid_df_kernel (+ split-K reduction)": ("alu", 8.0 * 4 * N * N * nrhs, fp32, "TFLOP/s",
                                                   "4N^2 nrhs complex MACs x 8 real flops vs the FP32 FMA rate "
                                                   "(152 SMs x 128 lanes x 2 x clock)"),
+        "resid_tc_kernel (+ split-K reduction)": ("hbm", 16.0 * 4 * N * N, hbm, "GB/s",
+                                                  "the FP64 operator (4N^2 complex entries x 16 bytes) read once per "
+                                                  "residual vs the measured copy bandwidth"),
         "cgemm_tc_kernel (Schur complement)": ("tensor", 16.0 * N ** 3, tf32, "TFLOP/s",
                                                "16 N^3 real flops (4M) vs the TF32 figure (measured bf16 x 1.1/2.25)"),
         "cgemm_tc_kernel (trailing update)": ("tensor", lw["trailing"], tf32, "TFLOP/s",

@@ -90,13 +90,18 @@ typedef struct {
  *  refine_maxit  : refinement iteration cap (default 30).
  *  nb            : outer LU block size, a multiple of 32 in [32, 256] (0 = library default).
  *  refine_residual: how refinement forms r = b - A x (bm_refine_residual):
- *     BM_RESID_DF_UPDATE (0, default): the first residual in double-float arithmetic on the FP32
- *        cores (each FP64 operand split into two FP32 parts, exact products, compensated sums:
- *        ~1e-12 of |A||x|), later ones updated as r -= A d with the product in FP32 (d, the last
- *        correction, is small by then, so the update error stays far below refine_tol);
+ *     BM_RESID_TC_UPDATE (0, default): the first residual from exact integer products on the
+ *        tensor cores - A (once, after assembly) and x split into seven base-128 digits per row /
+ *        column scale, digit pairs multiplied in bf16 with exact FP32 sums over chunks of 256 and
+ *        double-float sums across chunks (FP64-level accuracy, ~1e-15 of |A||x|); later ones
+ *        updated as r -= A d with the product in FP32 (d, the last correction, is small by then,
+ *        so the update error stays far below refine_tol);
  *     BM_RESID_FP64_UPDATE (1): the first residual in FP64, later ones updated as above;
- *     BM_RESID_FP64_ALL (2): every residual in FP64.
- *  The updated residuals of modes 0 and 1 carry the FP32 product error of each update, so the
+ *     BM_RESID_FP64_ALL (2): every residual in FP64;
+ *     BM_RESID_DF_UPDATE (3): the first residual in double-float arithmetic on the FP32 cores (each
+ *        FP64 operand split into two FP32 parts, exact products, compensated sums: ~1e-12 of
+ *        |A||x|), later ones updated as in mode 0.
+ *  The updated residuals of modes 0, 1 and 3 carry the FP32 product error of each update, so the
  *  backward error they track is reliable down to about 1e-12; refine_tol below 1e-12 needs
  *  BM_RESID_FP64_ALL (bm_assemble returns BM_EINVAL otherwise).
  * zeta_p: quadrature.  0 (default) is the one-point zeta-corrected rule of section 4.  1..20 adds
@@ -138,7 +143,9 @@ typedef struct {
     int test_wait_timeout;
 } bm_opts;
 
-typedef enum { BM_RESID_DF_UPDATE = 0, BM_RESID_FP64_UPDATE = 1, BM_RESID_FP64_ALL = 2 } bm_refine_residual;
+typedef enum {
+    BM_RESID_TC_UPDATE = 0, BM_RESID_FP64_UPDATE = 1, BM_RESID_FP64_ALL = 2, BM_RESID_DF_UPDATE = 3
+} bm_refine_residual;
 
 /* Per-solve report.  Times are device times (CUDA events) of the solve's phases. */
 typedef struct {

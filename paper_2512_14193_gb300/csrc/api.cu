@@ -122,6 +122,12 @@ void free_solve_ws(bm_ctx* c) {
     FREE(c->d_XP);
     FREE(c->d_XQ);
     FREE(c->d_Wdf);
+    for (int q = 0; q < 2; ++q) {
+        FREE(c->d_dx[q]);
+        FREE(c->d_dxe[q]);
+    }
+    FREE(c->d_rtw);
+    c->rtw_elems = 0;
     c->pk_elems = 0;
     c->ws_nrhs = 0;
     c->last_nrhs = 0;
@@ -158,6 +164,10 @@ void free_problem(bm_ctx* c) {
     FREE(c->d_Up_i);
     FREE(c->d_Cp_r);
     FREE(c->d_Cp_i);
+    for (int q = 0; q < 2; ++q) {
+        FREE(c->d_dg[q]);
+        FREE(c->d_dge[q]);
+    }
     c->assembled = c->factored = c->singular = false;
     c->tm_ok = false;
     c->tc_skinny = false;
@@ -210,6 +220,13 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
         long kl = split ? 3L * p.nb : p.nb;
         p.ldk_lu = round_up(kl, 32);
         b += 2 * (size_t)p.n * p.ldk_lu * 8;
+        // digit planes of the operator for the tensor-core residual, their row exponents, and the
+        // row-maximum scratch of their construction
+        const size_t planes = (size_t)rt_digit_planes() * 2;
+        if (form == BM_MIXED)
+            b += planes * (2L * N * rt_ldk(N) + (size_t)N * rt_ldk(2L * N)) + 3L * N * 4 + 2L * N * 8;
+        else
+            b += planes * 2L * N * rt_ldk(2L * N) + 2L * N * 4 + 2L * N * 8;
     }
     p.nblk = ceil_div(p.n, bs);
     b += 2 * (size_t)p.n * 4;
@@ -335,6 +352,8 @@ extern "C" bm_status bm_enqueue_probe(bm_ctx* c, int which, int reps) {
         for (int r = 0; r < reps; ++r) {
             if (c->prec != BM_FP64 && c->resid_mode == BM_RESID_DF_UPDATE)
                 BM_TRY(residual_df(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
+            else if (c->prec != BM_FP64 && c->resid_mode == BM_RESID_TC_UPDATE)
+                BM_TRY(residual_tc(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
             else
                 BM_TRY(residual_fp64(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
         }
@@ -395,7 +414,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     int prec = opts ? opts->prec : BM_FP64;
     if (prec < BM_FP64 || prec > BM_CF32_3XTF32_IR) return BM_EINVAL;
     int nb = opts ? opts->nb : 0;
-    if (opts && (opts->refine_residual < BM_RESID_DF_UPDATE || opts->refine_residual > BM_RESID_FP64_ALL))
+    if (opts && (opts->refine_residual < BM_RESID_TC_UPDATE || opts->refine_residual > BM_RESID_DF_UPDATE))
         return BM_EINVAL;
     if (opts && opts->refine_tol > 0 && opts->refine_tol < 1e-12 && opts->refine_residual != BM_RESID_FP64_ALL &&
         prec != BM_FP64) {
@@ -496,7 +515,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     c->beta = beta;
     c->refine_tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : 1e-9;
     c->refine_maxit = (opts && opts->refine_maxit > 0) ? opts->refine_maxit : 30;
-    c->resid_mode = opts ? opts->refine_residual : BM_RESID_DF_UPDATE;
+    c->resid_mode = opts ? opts->refine_residual : BM_RESID_TC_UPDATE;
     c->ldtop = p.ldtop;
     c->ldbot = p.ldbot;
     c->ldA = p.ldA;
@@ -547,6 +566,19 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
         if (s == BM_OK) s = alloc_t(c, &c->d_Up_r, lb);
         if (s == BM_OK) s = alloc_t(c, &c->d_Up_i, lb);
     }
+    if (s == BM_OK && c32) {
+        // [0] Mtop (2N x N) or A (2N x 2N), [1] Mbot (N x 2N)
+        const int np = rt_digit_planes();
+        const long rows0 = 2L * N, k0 = (form == BM_MIXED) ? N : 2L * N;
+        c->dg_ldk[0] = rt_ldk(k0);
+        s = alloc_t(c, &c->d_dg[0], (size_t)np * rows0 * c->dg_ldk[0] * 2);
+        if (s == BM_OK) s = alloc_t(c, &c->d_dge[0], (size_t)rows0 * 4);
+        if (s == BM_OK && form == BM_MIXED) {
+            c->dg_ldk[1] = rt_ldk(2L * N);
+            s = alloc_t(c, &c->d_dg[1], (size_t)np * N * c->dg_ldk[1] * 2);
+            if (s == BM_OK) s = alloc_t(c, &c->d_dge[1], (size_t)N * 4);
+        }
+    }
     if (s == BM_OK) s = alloc_t(c, &c->d_ipiv, (size_t)p.n * 4);
     if (s == BM_OK) s = alloc_t(c, &c->d_perm, (size_t)p.n * 4);
     size_t dinv = (size_t)p.nblk * c->bs_solve * c->bs_solve * (c32 ? 8 : 16);
@@ -594,6 +626,23 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
             BM_CUDA_TRY(launch_split_planes(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_PA, c->d_QA, c->ldA));
             c->launches += 1;
         }
+        // digit planes of the operator for the tensor-core residual
+        void* rowmax = nullptr;
+        s = ctx_alloc(c, &rowmax, 2L * N * 8);
+        if (s != BM_OK) {
+            free_problem(c);
+            return s;
+        }
+        if (form == BM_MIXED) {
+            BM_CUDA_TRY(launch_digits_a(st, c->d_Mtop, c->ldtop, 2 * N, N, c->d_dge[0], c->d_dg[0], c->dg_ldk[0], rowmax));
+            BM_CUDA_TRY(launch_digits_a(st, c->d_Mbot, c->ldbot, N, 2 * N, c->d_dge[1], c->d_dg[1], c->dg_ldk[1], rowmax));
+            c->launches += 6;
+        } else {
+            BM_CUDA_TRY(launch_digits_a(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_dge[0], c->d_dg[0], c->dg_ldk[0], rowmax));
+            c->launches += 3;
+        }
+        BM_CUDA_TRY(cudaStreamSynchronize(st));
+        ctx_free(c, rowmax);
     }
     BM_CUDA_TRY(cudaStreamSynchronize(st));
     if (d_user) ctx_free(c, d_user);
@@ -613,6 +662,12 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
             BM_TRY(tc_make_map(c->tm_skinny[0], c->d_Cp_r, 2L * N, kext_c, p.ldk_c, TC_BM));
             BM_TRY(tc_make_map(c->tm_skinny[1], c->d_Cp_i, 2L * N, kext_c, p.ldk_c, TC_BM));
             c->tc_skinny = true;
+        }
+        {
+            const long rows0 = 2L * N, k0 = (form == BM_MIXED) ? N : 2L * N;
+            BM_TRY(rt_make_map(c->tm_dg[0], c->d_dg[0], rows0, k0, c->dg_ldk[0], rows0 * c->dg_ldk[0], 128));
+            if (form == BM_MIXED)
+                BM_TRY(rt_make_map(c->tm_dg[1], c->d_dg[1], N, 2L * N, c->dg_ldk[1], (long)N * c->dg_ldk[1], 128));
         }
         long klu = p.ldk_lu;
         BM_TRY(tc_make_map(c->tm_lu[0], c->d_Lp_r, p.n, klu, p.ldk_lu, TC_BM));
@@ -764,6 +819,28 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
         BM_TRY(alloc_t(c, &c->d_XQ, (size_t)c->nsys * w * 8));
         BM_TRY(alloc_t(c, &c->d_Wdf, (size_t)4 * c->N * w * 16));
     }
+    if (c->prec != BM_FP64) {
+        // x digit planes and split-K workspace of the tensor-core residual
+        const int N = c->N, np = rt_digit_planes();
+        const int npad = (int)round_up(w, rt_col_tile());
+        const int nprod = (c->form == BM_MIXED) ? 2 : 1;
+        size_t wsz = 0;
+        for (int q = 0; q < nprod; ++q) {
+            // mixed: [0] rows [2N, 3N) for Mtop (K = N), [1] rows [0, 2N) for Mbot (K = 2N);
+            // ordinary: [0] rows [0, 2N) for A (K = 2N)
+            const long K = (c->form == BM_MIXED && q == 0) ? N : 2L * N;
+            const long m = (c->form == BM_MIXED && q == 1) ? N : 2L * N;
+            c->dx_ldk[q] = rt_ldk(K);
+            BM_TRY(alloc_t(c, &c->d_dx[q], (size_t)np * npad * c->dx_ldk[q] * 2));
+            BM_TRY(alloc_t(c, &c->d_dxe[q], (size_t)npad * 4));
+            BM_TRY(rt_make_map(c->tm_dx[q], c->d_dx[q], npad, K, c->dx_ldk[q], (long)npad * c->dx_ldk[q],
+                               rt_col_tile()));
+            const int S = rt_splits((int)K);
+            if (S > 1) wsz += 2 * (size_t)S * m * w;
+        }
+        if (wsz) BM_TRY(alloc_t(c, &c->d_rtw, wsz * 8));
+        c->rtw_elems = wsz;
+    }
     if (c->tc_skinny) {
         const int N = c->N;
         const bool split = c->prec == BM_CF32_3XTF32_IR;
@@ -875,6 +952,8 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
                 cudaEventRecord(r0, s);
                 if (c->resid_mode == BM_RESID_DF_UPDATE)
                     st = residual_df(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
+                else if (c->resid_mode == BM_RESID_TC_UPDATE)
+                    st = residual_tc(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
                 else
                     st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
                 cudaEventRecord(r1, s);

@@ -176,7 +176,7 @@ struct bm_ctx {
     double2 k0{}, k1{}, eps0{}, eps1{}, beta{};
     double refine_tol = 1e-9;
     int refine_maxit = 30;
-    int resid_mode = BM_RESID_DF_UPDATE;
+    int resid_mode = BM_RESID_TC_UPDATE;
     int nb = 0;
     int zeta_p = 0;  // high-order zeta correction points (0: the one-point rule)
 
@@ -200,6 +200,21 @@ struct bm_ctx {
     float2* d_Qtop = nullptr;  // re + im of the same entries, split hi/lo (3-product complex multiply)
     float2* d_Qbot = nullptr;
     float2* d_QA = nullptr;
+    // the FP64 operator as base-128 digit planes for the tensor-core residual (CF32 precisions):
+    // [0] Mtop (mixed) or A (ordinary), [1] Mbot (mixed); 14 bf16 planes [rows][ldk] each, with the
+    // power-of-two exponent of every row
+    void* d_dg[2] = {nullptr, nullptr};
+    int* d_dge[2] = {nullptr, nullptr};
+    long dg_ldk[2] = {0, 0};
+    alignas(64) unsigned char tm_dg[2][128];
+    // x digit planes for the two products (K ranges [2N, 3N) and [0, 2N) mixed; [0, 2N) ordinary),
+    // their column exponents, and the split-K workspace of the tensor-core residual
+    void* d_dx[2] = {nullptr, nullptr};
+    int* d_dxe[2] = {nullptr, nullptr};
+    long dx_ldk[2] = {0, 0};
+    alignas(64) unsigned char tm_dx[2][128];
+    double* d_rtw = nullptr;
+    size_t rtw_elems = 0;
 
     // factorisation storage
     double2* d_F64 = nullptr;  // FP64 LU (n x n, ld ldF)

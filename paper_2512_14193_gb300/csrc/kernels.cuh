@@ -59,6 +59,7 @@ bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const do
 bm_status correction_c32(bm_ctx* c, const double2* R, double2* X, long ld, int nrhs);
 bm_status residual_update_c32(bm_ctx* c, double2* R, long ld, int nrhs);
 bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs);
+bm_status residual_tc(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs);
 
 // resid_df.cu: C += alpha A X in double-float arithmetic (A as split planes, X and C FP64)
 // one product C (m x n) += alpha A (m x k) X (k x n) of a double-float residual; S K splits (S > 1
@@ -81,3 +82,27 @@ cudaError_t launch_split_planes(cudaStream_t s, const double2* A, long lda, int 
 // gemm_simt.cu: C (FP64) += alpha A_hi B with A the hi parts of split planes, FP32 arithmetic
 cudaError_t gemm_update_f4hi_c32(cudaStream_t s, int m, int n, int k, float alpha, F4Hi A, C32 B, Z64 C);
 cudaError_t launch_copy_z64(cudaStream_t s, const double2* S, long lds, int m, int n, double2* D, long ldd);
+
+// resid_tc.cu: r += alpha A x to FP64-level accuracy from exact bf16 digit products on the tensor
+// cores (digit planes of A made once after assembly, of x per residual)
+struct RtArgs {
+    const void* tmA;   // host copies of the tensor maps (opaque 128-byte blobs)
+    const void* tmX;
+    const int* eA;     // row exponents of A (device)
+    const int* fX;     // column exponents of x (device)
+    double2* C;        // output, C += alpha A x
+    long ldc;
+    double* Wr;        // split-K workspace (S > 1): S m n doubles each
+    double* Wi;
+    int m, K, S;
+};
+long rt_ldk(long K);                 // leading dimension of a digit plane row (K rounded to 64)
+int rt_digit_planes();               // planes per operand (7 digits x Re, Im)
+int rt_col_tile();                   // right-hand sides per CTA
+int rt_splits(int K);                // K splits of a product
+bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk, long plane_elems, int box_rows);
+cudaError_t launch_digits_a(cudaStream_t s, const double2* A, long lda, int rows, int K, int* e, void* D, long ldk,
+                            void* rowmax);
+cudaError_t launch_digits_x(cudaStream_t s, const double2* X, long ldx, int r0, int K, int n, int npad, int* f,
+                            void* D, long ldk);
+cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, double alpha, int* d_err, int* launched);

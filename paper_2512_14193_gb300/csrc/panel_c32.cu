@@ -13,10 +13,11 @@ namespace {
 //   1. every lane tracks the best row of its own column (max |Re|+|Im|, then smallest row), so
 //      lane c of each warp holds the warp's candidate; the CTA's best is two warp reductions
 //      (redux.sync max of the value bits, then min of the row index among the maxima);
-//   2. the warp owning each CTA's candidate row writes it (lane k its column k entry), with its
-//      value and index, straight from registers into every CTA of the cluster with st.async; the
-//      owner of row c does the same with row c.  Each receiver's mbarrier for this column
-//      completes when all bytes have landed (no cluster barrier, no proxy fence);
+//   2. the warp owning each CTA's candidate row stages it (lane k its column k entry) with its
+//      value and index in shared memory, the owner of row c stages row c; after one CTA barrier
+//      warp d sends both to cluster CTA d with st.async (the CL destinations are served by CL warps
+//      at once instead of one warp in turn).  Each receiver's mbarrier for this column completes
+//      when all bytes have landed (no cluster barrier, no proxy fence);
 //   3. every CTA picks the pivot from the CL candidates (the same two reductions);
 //   4. rows c and pivot are interchanged in the registers of their owners;
 //   5. lane c stages its column (the rows' column-c entries) in shared memory and every lane
@@ -108,6 +109,8 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
     __shared__ alignas(16) float2 cand_buf[2][MAX_CLUSTER][CAND];  // received candidates
     __shared__ alignas(16) float2 diag_buf[2][32];                  // received row c
     __shared__ alignas(16) float2 colbuf[WARPS][RPW];               // column c of each warp's rows
+    __shared__ alignas(16) float2 stage_cand[CAND];                 // this CTA's candidate, to send
+    __shared__ alignas(16) float2 stage_diag[32];                   // row c if this CTA owns it
     __shared__ alignas(8) uint64_t bars[2];
     __shared__ uint2 red[2][WARPS];
     __shared__ int s_map[MAP_MAX / 2 * 3 + MAP_MAX];
@@ -160,21 +163,28 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         }
         warp_best(cvb, ciu);
         const int ci = (int)ciu;
-        // ---- (2) send the candidate row (its owner warp, else warp 0 sends zeros) and row c ----
+        // ---- (2) stage the candidate row (its owner warp, else warp 0 stages zeros) and row c,
+        //          then warp d sends them to cluster CTA d ----
         const bool has = ci != INT_MAX;
         if (warp == (has ? (ci - rb) / RPW : 0)) {
-            const float2 v = has ? row_get<RPW>(row, ci - wb) : zero;
-            const uint32_t la = smem_addr(&cand_buf[par][cta][lane]);
-            for (int d = 0; d < CL; ++d)
-                push8(remote_addr(la, d), __float_as_uint(v.x), __float_as_uint(v.y), remote_addr(bar, d));
-            if (lane < CL)
-                push8(remote_addr(smem_addr(&cand_buf[par][cta][32]), lane), cvb, ciu, remote_addr(bar, lane));
+            stage_cand[lane] = has ? row_get<RPW>(row, ci - wb) : zero;
+            if (lane == 0) stage_cand[32] = make_float2(__uint_as_float(cvb), __uint_as_float(ciu));
         }
-        if (c >= wb && c < wb + RPW) {
-            const float2 v = row_get<RPW>(row, c - wb);
-            const uint32_t la = smem_addr(&diag_buf[par][lane]);
-            for (int d = 0; d < CL; ++d)
-                push8(remote_addr(la, d), __float_as_uint(v.x), __float_as_uint(v.y), remote_addr(bar, d));
+        const bool own_diag = c >= rb && c < rb + R;  // row c lies in this CTA
+        if (c >= wb && c < wb + RPW) stage_diag[lane] = row_get<RPW>(row, c - wb);
+        __syncthreads();
+        if (warp < CL) {
+            const int d = warp;
+            const uint32_t rbar = remote_addr(bar, d);
+            const float2 v = stage_cand[lane];
+            push8(remote_addr(smem_addr(&cand_buf[par][cta][lane]), d), __float_as_uint(v.x), __float_as_uint(v.y),
+                  rbar);
+            if (lane == 0) push8(remote_addr(smem_addr(&cand_buf[par][cta][32]), d), cvb, ciu, rbar);
+            if (own_diag) {
+                const float2 g = stage_diag[lane];
+                push8(remote_addr(smem_addr(&diag_buf[par][lane]), d), __float_as_uint(g.x), __float_as_uint(g.y),
+                      rbar);
+            }
         }
         // ---- (3) wait for this column's data, pick the pivot ----
         if (!timed_out && !bar_wait(bar, (uint32_t)(c >> 1) & 1u)) {

@@ -264,6 +264,61 @@ bm_status residual_df(bm_ctx* c, const double2* B, const double2* X, double2* R,
     return BM_OK;
 }
 
+// R = B - A X with the FP64 operator, from exact digit products on the tensor cores (resid_tc.cu).
+// Not captured in a graph: counts its own launches.
+bm_status residual_tc(bm_ctx* c, const double2* B, const double2* X, double2* R, long ld, int nrhs) {
+    cudaStream_t s = c->stream;
+    const int N = c->N;
+    long t = (long)c->nsys * nrhs;
+    int nsub = (c->form == BM_MIXED) ? 2 * N : 0;
+    {
+        BM_PROF(c, "resid_init_kernel");
+        resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
+        SV_CUDA(cudaGetLastError());
+    }
+    const int npad = (int)((nrhs + rt_col_tile() - 1) / rt_col_tile() * rt_col_tile());
+    const int nprod = (c->form == BM_MIXED) ? 2 : 1;
+    {
+        BM_PROF(c, "digits_x (col_exponent/digits_x_kernel)");
+        for (int q = 0; q < nprod; ++q) {
+            const int r0 = (c->form == BM_MIXED && q == 0) ? 2 * N : 0;
+            const int K = (c->form == BM_MIXED && q == 0) ? N : 2 * N;
+            SV_CUDA(launch_digits_x(s, X, ld, r0, K, nrhs, npad, c->d_dxe[q], c->d_dx[q], c->dx_ldk[q]));
+        }
+    }
+    // mixed: Mbot (K = 2N, the longer units) first, then Mtop; ordinary: A
+    RtArgs P[2];
+    double* w = c->d_rtw;
+    int np = 0;
+    auto add = [&](int dg, int dx, double2* Cout, int m, int K) {
+        const int S = rt_splits(K);
+        RtArgs a{c->tm_dg[dg], c->tm_dx[dx], c->d_dge[dg], c->d_dxe[dx], Cout, ld, nullptr, nullptr, m, K, S};
+        if (S > 1) {
+            a.Wr = w;
+            a.Wi = w + (size_t)S * m * nrhs;
+            w += 2 * (size_t)S * m * nrhs;
+        }
+        P[np++] = a;
+    };
+    if (c->form == BM_MIXED) {
+        add(1, 1, R + 2 * N, N, 2 * N);
+        add(0, 0, R, 2 * N, N);
+    } else {
+        add(0, 0, R, 2 * N, 2 * N);
+    }
+    if ((size_t)(w - c->d_rtw) > c->rtw_elems) {
+        bm_set_error("residual_tc: split-K workspace too small");
+        return BM_EINVAL;
+    }
+    int nl = 0;
+    {
+        BM_PROF(c, "resid_tc_kernel (+ split-K reduction)");
+        SV_CUDA(gemm_rt(s, P, np, nrhs, -1.0, c->d_err, &nl));
+    }
+    c->launches += 1 + 2 * nprod + nl;
+    return BM_OK;
+}
+
 // d_eta[0] = backward error (max over columns), d_eta[1] = non-finite flag of B
 bm_status backward_error(bm_ctx* c, const double2* R, const double2* X, const double2* B, long ld, int nrhs,
                          double* d_eta) {

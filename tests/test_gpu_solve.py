@@ -76,11 +76,12 @@ def test_fp64_ordinary_matches_oracle(bmlib, handle, N):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("resid", [0, 1, 2])
+@pytest.mark.parametrize("resid", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("form", [0, 1])
 def test_mixed_precision_refinement(bmlib, handle, prec, form, resid):
-    # resid 0: first residual double-float, later ones r -= A d in FP32; 1: first in FP64; 2: all FP64
+    # first residual from tensor-core digit products (0), FP64 (1) or double-float (3), later ones
+    # r -= A d in FP32; 2: every residual in FP64
     curve, N, k0, k1 = W.star(1.0, 0.3, 5), 200, 6.0, 9.0
     bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, k0, k1, form,
                       bmlib.make_opts(prec, residual=resid))
@@ -133,13 +134,15 @@ def test_panel_variants_match_oracle(bmlib, prec, clmax, N, kernel):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("resid", [0, 3])
 @pytest.mark.parametrize("form", [0, 1])
-def test_double_float_residual_reaches_tight_tolerance(bmlib, handle, form):
+def test_first_residual_reaches_tight_tolerance(bmlib, handle, form, resid):
     # Refinement can only certify what its residual resolves: reaching 2e-12 through the
-    # double-float residual (and FP32 updates) pins that residual far below the 1e-9 target.
+    # tensor-core digit residual (0) or the double-float one (3), and FP32 updates, pins that
+    # residual far below the 1e-9 target.
     curve, N, k0, k1 = W.kite(), 300, 9.0 - 0.2j, 13.5 - 0.3j
     bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, k0, k1, form,
-                      bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=2e-12, residual=0))
+                      bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=2e-12, residual=resid))
     assert bmlib.bm_factor(handle) == 0
     g, P = O.nodes(curve, N), O.default_params(k0, k1)
     B = _rhs(g, P, N, form, 4, full=(form == 0), seed=3)
@@ -230,3 +233,26 @@ def test_profile_reports_every_kernel_and_the_same_solution(bmlib, handle):
         assert k in names, k
     assert all(l >= 1 and ms > 0 for _, l, ms in prof)
     assert [ms for _, _, ms in prof] == sorted([ms for _, _, ms in prof], reverse=True)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("nrhs", [1, 33, 70])
+def test_tensor_core_residual_ragged_shapes(bmlib, handle, form, nrhs):
+    # N = 150: K = 150 and 300 end inside a 64-wide K block and a 256-wide exact chunk; 1, 33 and 70
+    # right-hand sides end inside a 32-wide column tile (a 16-wide last product).  The refined
+    # solution is certified to 2e-12 through the digit residual, and the oracle's FP64 backward
+    # error agrees.
+    curve, N, k0, k1 = W.ellipse(1.0, 0.6), 150, 5.0 - 0.1j, 7.5 - 0.15j
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, k0, k1, form,
+                      bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=2e-12, residual=0))
+    assert bmlib.bm_factor(handle) == 0
+    g, P = O.nodes(curve, N), O.default_params(k0, k1)
+    nsys = 3 * N if form == 0 else 2 * N
+    B = np.asfortranarray(W.gaussian_full(nsys, nrhs, 7))
+    X = np.zeros_like(B, order="F")
+    info = bmlib.bm_solve(handle, B, X)
+    assert info.backward_error <= 2e-12
+    eta = (O.backward_error_mixed(O.mixed_blocks(g, P), X, B) if form == 0
+           else O.backward_error_dense(O.ordinary_matrix(g, P), X, B))
+    assert eta <= 5e-12
