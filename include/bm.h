@@ -100,10 +100,12 @@ typedef struct {
  *     BM_RESID_FP64_ALL (2): every residual in FP64;
  *     BM_RESID_DF_UPDATE (3): the first residual in double-float arithmetic on the FP32 cores (each
  *        FP64 operand split into two FP32 parts, exact products, compensated sums: ~1e-12 of
- *        |A||x|), later ones updated as in mode 0.
+ *        |A||x|), later ones updated as in mode 0;
+ *     BM_RESID_TC_ALL (4): every residual from exact tensor-core digit products as in mode 0, with
+ *        eight digits per operand (~2^-57 of the row and column scales).
  *  The updated residuals of modes 0, 1 and 3 carry the FP32 product error of each update, so the
  *  backward error they track is reliable down to about 1e-12; refine_tol below 1e-12 needs
- *  BM_RESID_FP64_ALL (bm_assemble returns BM_EINVAL otherwise).
+ *  BM_RESID_FP64_ALL or BM_RESID_TC_ALL (bm_assemble returns BM_EINVAL otherwise).
  * zeta_p: quadrature.  0 (default) is the one-point zeta-corrected rule of section 4.  1..20 adds
  *  the high-order zeta corrections of section 5.3 ("order 31" is zeta_p = 14): weights derived
  *  from the Euler-Maclaurin expansion of the punctured trapezoid sum (zeta'(-2k) for the log
@@ -144,7 +146,8 @@ typedef struct {
 } bm_opts;
 
 typedef enum {
-    BM_RESID_TC_UPDATE = 0, BM_RESID_FP64_UPDATE = 1, BM_RESID_FP64_ALL = 2, BM_RESID_DF_UPDATE = 3
+    BM_RESID_TC_UPDATE = 0, BM_RESID_FP64_UPDATE = 1, BM_RESID_FP64_ALL = 2, BM_RESID_DF_UPDATE = 3,
+    BM_RESID_TC_ALL = 4
 } bm_refine_residual;
 
 /* Per-solve report.  Times are device times (CUDA events) of the solve's phases. */

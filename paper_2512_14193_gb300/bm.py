@@ -24,7 +24,7 @@ BM_MIXED, BM_ORDINARY = 0, 1
 BM_FP64, BM_CF32_TF32_IR, BM_CF32_3XTF32_IR = 0, 1, 2
 BM_CURVE_CIRCLE, BM_CURVE_ELLIPSE, BM_CURVE_STAR, BM_CURVE_KITE, BM_CURVE_USER = range(5)
 BM_PROBE_SCHUR, BM_PROBE_RESIDUAL = 0, 1
-BM_RESID_TC_UPDATE, BM_RESID_FP64_UPDATE, BM_RESID_FP64_ALL, BM_RESID_DF_UPDATE = 0, 1, 2, 3
+BM_RESID_TC_UPDATE, BM_RESID_FP64_UPDATE, BM_RESID_FP64_ALL, BM_RESID_DF_UPDATE, BM_RESID_TC_ALL = 0, 1, 2, 3, 4
 BM_FAR_FIELD_STATIC_MAX_ANGLES = 8192
 
 

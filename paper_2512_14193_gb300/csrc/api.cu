@@ -184,7 +184,7 @@ struct Plan {
     size_t bytes = 0;
 };
 
-Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
+Plan make_plan(int N, int form, int prec, int nb_user, int bs, int nd) {
     Plan p;
     const bool c32 = prec != BM_FP64;
     const bool split = prec == BM_CF32_3XTF32_IR;
@@ -222,7 +222,7 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
         b += 2 * (size_t)p.n * p.ldk_lu * 8;
         // digit planes of the operator for the tensor-core residual, their row exponents, and the
         // row-maximum scratch of their construction
-        const size_t planes = (size_t)rt_digit_planes() * 2;
+        const size_t planes = (size_t)rt_digit_planes(nd) * 2;
         if (form == BM_MIXED)
             b += planes * (2L * N * rt_ldk(N) + (size_t)N * rt_ldk(2L * N)) + 3L * N * 4 + 2L * N * 8;
         else
@@ -241,7 +241,7 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs) {
 // workspace for nrhs right-hand sides (an estimate from the same sizes ensure_ws uses, with a
 // margin for the split-K partial sums).
 size_t request_bytes(int N, int form, int prec, int nb, int nrhs) {
-    Plan p = make_plan(N, form, prec, nb, 64);
+    Plan p = make_plan(N, form, prec, nb, 64, 8);
     const size_t w = (size_t)std::max(nrhs, 8);
     size_t b = p.bytes + 7 * (size_t)N * 8 + (size_t)p.nsys * w * 16 * 3 + (size_t)p.n * w * 16 * 2;
     if (prec == BM_FP64) {
@@ -352,7 +352,7 @@ extern "C" bm_status bm_enqueue_probe(bm_ctx* c, int which, int reps) {
         for (int r = 0; r < reps; ++r) {
             if (c->prec != BM_FP64 && c->resid_mode == BM_RESID_DF_UPDATE)
                 BM_TRY(residual_df(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
-            else if (c->prec != BM_FP64 && c->resid_mode == BM_RESID_TC_UPDATE)
+            else if (c->prec != BM_FP64 && (c->resid_mode == BM_RESID_TC_UPDATE || c->resid_mode == BM_RESID_TC_ALL))
                 BM_TRY(residual_tc(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
             else
                 BM_TRY(residual_fp64(c, c->d_Bw, c->d_X, c->d_R, c->nsys, c->last_nrhs));
@@ -414,12 +414,12 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     int prec = opts ? opts->prec : BM_FP64;
     if (prec < BM_FP64 || prec > BM_CF32_3XTF32_IR) return BM_EINVAL;
     int nb = opts ? opts->nb : 0;
-    if (opts && (opts->refine_residual < BM_RESID_TC_UPDATE || opts->refine_residual > BM_RESID_DF_UPDATE))
+    if (opts && (opts->refine_residual < BM_RESID_TC_UPDATE || opts->refine_residual > BM_RESID_TC_ALL))
         return BM_EINVAL;
     if (opts && opts->refine_tol > 0 && opts->refine_tol < 1e-12 && opts->refine_residual != BM_RESID_FP64_ALL &&
-        prec != BM_FP64) {
-        bm_set_error("refine_tol below 1e-12 needs refine_residual = BM_RESID_FP64_ALL (updated residuals are "
-                     "reliable to about 1e-12)");
+        opts->refine_residual != BM_RESID_TC_ALL && prec != BM_FP64) {
+        bm_set_error("refine_tol below 1e-12 needs refine_residual = BM_RESID_FP64_ALL or BM_RESID_TC_ALL (updated "
+                     "residuals are reliable to about 1e-12)");
         return BM_EINVAL;
     }
     if (nb != 0 && (nb % 32 != 0 || nb < 32 || nb > 256)) {
@@ -482,12 +482,14 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
 
     BM_CUDA_TRY(cudaSetDevice(c->device));
     cudaStreamSynchronize(c->stream);
-    Plan p = make_plan(N, form, prec, nb, 64);
+    const int rmode = opts ? opts->refine_residual : BM_RESID_TC_UPDATE;
+    const int nd = rmode == BM_RESID_TC_ALL ? 8 : 7;
+    Plan p = make_plan(N, form, prec, nb, 64, nd);
     // Same shape as the assembled system: assemble again into the same buffers (no device
     // allocation or release - cudaFree would wait for every stream of the device - and the cached
     // graphs and tensor maps stay valid, as they depend only on these pointers and sizes).
     const bool reuse = c->assembled && c->N == N && c->form == form && c->prec == prec && c->nb == p.nb &&
-                       curve->kind != BM_CURVE_USER;
+                       c->rt_nd == nd && curve->kind != BM_CURVE_USER;
     if (!reuse) free_problem(c);
     // the captured factorisation depends on the launch settings: capture again when they change
     if (reuse && (eager != c->eager || cl_cap != c->opt_cluster_cap || pkern != c->opt_panel_kernel))
@@ -515,7 +517,8 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     c->beta = beta;
     c->refine_tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : 1e-9;
     c->refine_maxit = (opts && opts->refine_maxit > 0) ? opts->refine_maxit : 30;
-    c->resid_mode = opts ? opts->refine_residual : BM_RESID_TC_UPDATE;
+    c->resid_mode = rmode;
+    c->rt_nd = nd;
     c->ldtop = p.ldtop;
     c->ldbot = p.ldbot;
     c->ldA = p.ldA;
@@ -568,7 +571,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     }
     if (s == BM_OK && c32) {
         // [0] Mtop (2N x N) or A (2N x 2N), [1] Mbot (N x 2N)
-        const int np = rt_digit_planes();
+        const int np = rt_digit_planes(nd);
         const long rows0 = 2L * N, k0 = (form == BM_MIXED) ? N : 2L * N;
         c->dg_ldk[0] = rt_ldk(k0);
         s = alloc_t(c, &c->d_dg[0], (size_t)np * rows0 * c->dg_ldk[0] * 2);
@@ -634,11 +637,14 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
             return s;
         }
         if (form == BM_MIXED) {
-            BM_CUDA_TRY(launch_digits_a(st, c->d_Mtop, c->ldtop, 2 * N, N, c->d_dge[0], c->d_dg[0], c->dg_ldk[0], rowmax));
-            BM_CUDA_TRY(launch_digits_a(st, c->d_Mbot, c->ldbot, N, 2 * N, c->d_dge[1], c->d_dg[1], c->dg_ldk[1], rowmax));
+            BM_CUDA_TRY(launch_digits_a(st, c->d_Mtop, c->ldtop, 2 * N, N, c->d_dge[0], c->d_dg[0], c->dg_ldk[0], rowmax,
+                                        nd));
+            BM_CUDA_TRY(launch_digits_a(st, c->d_Mbot, c->ldbot, N, 2 * N, c->d_dge[1], c->d_dg[1], c->dg_ldk[1], rowmax,
+                                        nd));
             c->launches += 6;
         } else {
-            BM_CUDA_TRY(launch_digits_a(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_dge[0], c->d_dg[0], c->dg_ldk[0], rowmax));
+            BM_CUDA_TRY(launch_digits_a(st, c->d_A, c->ldA, 2 * N, 2 * N, c->d_dge[0], c->d_dg[0], c->dg_ldk[0], rowmax,
+                                        nd));
             c->launches += 3;
         }
         BM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -665,9 +671,9 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
         }
         {
             const long rows0 = 2L * N, k0 = (form == BM_MIXED) ? N : 2L * N;
-            BM_TRY(rt_make_map(c->tm_dg[0], c->d_dg[0], rows0, k0, c->dg_ldk[0], rows0 * c->dg_ldk[0], 128));
+            BM_TRY(rt_make_map(c->tm_dg[0], c->d_dg[0], rows0, k0, c->dg_ldk[0], rows0 * c->dg_ldk[0], 128, nd));
             if (form == BM_MIXED)
-                BM_TRY(rt_make_map(c->tm_dg[1], c->d_dg[1], N, 2L * N, c->dg_ldk[1], (long)N * c->dg_ldk[1], 128));
+                BM_TRY(rt_make_map(c->tm_dg[1], c->d_dg[1], N, 2L * N, c->dg_ldk[1], (long)N * c->dg_ldk[1], 128, nd));
         }
         long klu = p.ldk_lu;
         BM_TRY(tc_make_map(c->tm_lu[0], c->d_Lp_r, p.n, klu, p.ldk_lu, TC_BM));
@@ -821,7 +827,7 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
     }
     if (c->prec != BM_FP64) {
         // x digit planes and split-K workspace of the tensor-core residual
-        const int N = c->N, np = rt_digit_planes();
+        const int N = c->N, np = rt_digit_planes(c->rt_nd);
         const int npad = (int)round_up(w, rt_col_tile());
         const int nprod = (c->form == BM_MIXED) ? 2 : 1;
         size_t wsz = 0;
@@ -834,7 +840,7 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
             BM_TRY(alloc_t(c, &c->d_dx[q], (size_t)np * npad * c->dx_ldk[q] * 2));
             BM_TRY(alloc_t(c, &c->d_dxe[q], (size_t)npad * 4));
             BM_TRY(rt_make_map(c->tm_dx[q], c->d_dx[q], npad, K, c->dx_ldk[q], (long)npad * c->dx_ldk[q],
-                               rt_col_tile()));
+                               rt_col_tile(), c->rt_nd));
             const int S = rt_splits((int)K);
             if (S > 1) wsz += 2 * (size_t)S * m * w;
         }
@@ -946,13 +952,14 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
         cudaMemsetAsync(c->d_X, 0, (size_t)ld * nrhs * 16, s);
         cudaMemcpyAsync(c->d_R, c->d_Bw, (size_t)ld * nrhs * 16, cudaMemcpyDeviceToDevice, s);
         for (int it = 0;; ++it) {
-            if (it == 1 || (it > 1 && c->resid_mode == BM_RESID_FP64_ALL)) {
+            const bool fresh_all = c->resid_mode == BM_RESID_FP64_ALL || c->resid_mode == BM_RESID_TC_ALL;
+            if (it == 1 || (it > 1 && fresh_all)) {
                 // r = b - A x in FP64 or double-float (after the first correction x is the plain
                 // FP32 solve)
                 cudaEventRecord(r0, s);
                 if (c->resid_mode == BM_RESID_DF_UPDATE)
                     st = residual_df(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
-                else if (c->resid_mode == BM_RESID_TC_UPDATE)
+                else if (c->resid_mode == BM_RESID_TC_UPDATE || c->resid_mode == BM_RESID_TC_ALL)
                     st = residual_tc(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);
                 else
                     st = residual_fp64(c, c->d_Bw, c->d_X, c->d_R, ld, nrhs);

@@ -206,6 +206,7 @@ struct bm_ctx {
     void* d_dg[2] = {nullptr, nullptr};
     int* d_dge[2] = {nullptr, nullptr};
     long dg_ldk[2] = {0, 0};
+    int rt_nd = 7;            // digits per operand (8 for BM_RESID_TC_ALL)
     alignas(64) unsigned char tm_dg[2][128];
     // x digit planes for the two products (K ranges [2N, 3N) and [0, 2N) mixed; [0, 2N) ordinary),
     // their column exponents, and the split-K workspace of the tensor-core residual

@@ -97,12 +97,14 @@ struct RtArgs {
     int m, K, S;
 };
 long rt_ldk(long K);                 // leading dimension of a digit plane row (K rounded to 64)
-int rt_digit_planes();               // planes per operand (7 digits x Re, Im)
+int rt_digit_planes(int nd);         // planes per operand (nd digits x Re, Im)
 int rt_col_tile();                   // right-hand sides per CTA
 int rt_splits(int K);                // K splits of a product
-bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk, long plane_elems, int box_rows);
+bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk, long plane_elems, int box_rows,
+                      int nd);
 cudaError_t launch_digits_a(cudaStream_t s, const double2* A, long lda, int rows, int K, int* e, void* D, long ldk,
-                            void* rowmax);
+                            void* rowmax, int nd);
 cudaError_t launch_digits_x(cudaStream_t s, const double2* X, long ldx, int r0, int K, int n, int npad, int* f,
-                            void* D, long ldk);
-cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, double alpha, int* d_err, int* launched);
+                            void* D, long ldk, int nd);
+cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, double alpha, int* d_err, int* launched,
+                    int nd);

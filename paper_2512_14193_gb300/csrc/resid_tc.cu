@@ -44,19 +44,25 @@ namespace {
 constexpr int RT_BM = 128;   // output rows per CTA
 constexpr int RT_NT = 32;    // right-hand sides per CTA (the last column tile may use 16)
 constexpr int RT_BK = 64;    // K elements per stage: bf16 rows of 128 bytes (one swizzle span)
-constexpr int RT_KB_CHUNK = 4;  // K blocks per exactly accumulated chunk (K = 256)
-constexpr int RT_D = 7;      // digits per operand
 constexpr int RT_AST = 3;    // stages of A digit pairs
 constexpr int RT_TILE_A = RT_BM * RT_BK * 2;  // one digit plane of A: 16 KB
 constexpr int RT_TILE_X = RT_NT * RT_BK * 2;  // one digit plane of x: 4 KB
 constexpr int RT_A_STAGE = 2 * RT_TILE_A;     // Re and Im of one digit
-constexpr int RT_X_BUF = 2 * RT_D * RT_TILE_X;  // all digits of x, Re and Im
-constexpr int RT_SMEM = RT_AST * RT_A_STAGE + 2 * RT_X_BUF + 1024 + 256;
 constexpr int RT_THREADS = 320;
 constexpr uint64_t RT_WAIT_NS = 2000000000ull;
-// tensor memory: real parts of levels 0..6 at columns 32 l, imaginary parts at 224 + 32 l
-static_assert(2 * RT_D * RT_NT <= 512, "seven level accumulators fit tensor memory");
-static_assert(RT_D * RT_NT <= 256, "the widest MMA (A digit 0 against all x digits) has N <= 256");
+// D digits per operand (7: pairs to level 6, 2^-50; 8: to level 7, 2^-57).  Level sums over a chunk
+// stay below 2^24: D pairs x 2 products x 4096 x chunk K, so the chunk is 256 for D = 7 and 128 for
+// D = 8.  Tensor memory: real parts of levels 0..D-1 at columns 32 l, imaginary parts at 32 (D + l).
+template <int D>
+struct RtCfg {
+    static constexpr int KB_CHUNK = D <= 7 ? 4 : 2;     // K blocks of 64 per exact chunk
+    static constexpr int X_BUF = 2 * D * RT_TILE_X;     // all digits of x, Re and Im
+    static constexpr int SMEM = RT_AST * RT_A_STAGE + 2 * X_BUF + 1024 + 256;
+    static_assert(2 * D * RT_NT <= 512, "the level accumulators fit tensor memory");
+    static_assert(D * RT_NT <= 256, "the widest MMA (A digit 0 against all x digits) has N <= 256");
+    static_assert(D * 2 * 4096L * 64 * KB_CHUNK <= (1L << 24), "chunk sums stay exact in FP32");
+    static_assert(SMEM <= 232448, "shared memory");
+};
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -162,7 +168,9 @@ struct RtJob {
     int first_unit[3];
 };
 
+template <int D>
 __global__ void __launch_bounds__(RT_THREADS, 1) resid_tc_kernel(const __grid_constant__ RtJob J, int* __restrict__ err) {
+    constexpr int RT_D = D, RT_KB_CHUNK = RtCfg<D>::KB_CHUNK, RT_X_BUF = RtCfg<D>::X_BUF;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;                               // RT_AST stages of (Re, Im) digit tiles of A
@@ -417,10 +425,9 @@ __global__ void row_exponent_kernel(const unsigned long long* __restrict__ mx, i
     e[i] = m > 0.0 ? ex + 1 : 0;
 }
 
-__device__ __forceinline__ void digits7(double v, __nv_bfloat16* out, long stride) {
-    // v in (-1/2, 1/2): seven base-128 digits, each an integer in [-64, 64] (exact in bf16)
-#pragma unroll
-    for (int d = 0; d < RT_D; ++d) {
+__device__ __forceinline__ void digits_of(double v, int nd, __nv_bfloat16* out, long stride) {
+    // v in (-1/2, 1/2): nd base-128 digits, each an integer in [-64, 64] (exact in bf16)
+    for (int d = 0; d < nd; ++d) {
         v *= 128.0;
         const double a = rint(v);
         v -= a;
@@ -431,7 +438,7 @@ __device__ __forceinline__ void digits7(double v, __nv_bfloat16* out, long strid
 // Digit planes of A: plane 2d + part holds digit d of the real (part 0) or imaginary (1) parts, K-major
 // ([row][ldk]); written through a 32 x 32 shared tile so both sides are coalesced.
 __global__ void digits_a_kernel(const double2* __restrict__ A, long lda, int rows, int K, const int* __restrict__ e,
-                                __nv_bfloat16* __restrict__ D, long ldk, long plane) {
+                                __nv_bfloat16* __restrict__ D, long ldk, long plane, int nd) {
     __shared__ double2 t[32][33];
     const int k0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -446,8 +453,8 @@ __global__ void digits_a_kernel(const double2* __restrict__ A, long lda, int row
         const double2 v = t[tx][q];
         const int ex = e[r];
         __nv_bfloat16* o = D + (long)r * ldk + k;
-        digits7(ldexp(v.x, -ex), o, 2 * plane);
-        digits7(ldexp(v.y, -ex), o + plane, 2 * plane);
+        digits_of(ldexp(v.x, -ex), nd, o, 2 * plane);
+        digits_of(ldexp(v.y, -ex), nd, o + plane, 2 * plane);
     }
 }
 
@@ -474,19 +481,20 @@ __global__ void col_exponent_kernel(const double2* __restrict__ X, long ldx, int
 // Digit planes of x rows [r0, r0 + K) (columns c < n; columns up to npad are zero): plane 2d + part,
 // layout [col][ldk].
 __global__ void digits_x_kernel(const double2* __restrict__ X, long ldx, int r0, int K, int n, int npad,
-                                const int* __restrict__ f, __nv_bfloat16* __restrict__ D, long ldk, long plane) {
+                                const int* __restrict__ f, __nv_bfloat16* __restrict__ D, long ldk, long plane,
+                                int nd) {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)npad * K) return;
     const int c = (int)(idx / K), k = (int)(idx % K);
     __nv_bfloat16* o = D + (long)c * ldk + k;
     if (c >= n) {
-        for (int p = 0; p < 2 * RT_D; ++p) o[p * plane] = __float2bfloat16_rn(0.f);
+        for (int p = 0; p < 2 * nd; ++p) o[p * plane] = __float2bfloat16_rn(0.f);
         return;
     }
     const double2 v = X[r0 + k + (long)c * ldx];
     const int ex = f[c];
-    digits7(ldexp(v.x, -ex), o, 2 * plane);
-    digits7(ldexp(v.y, -ex), o + plane, 2 * plane);
+    digits_of(ldexp(v.x, -ex), nd, o, 2 * plane);
+    digits_of(ldexp(v.y, -ex), nd, o + plane, 2 * plane);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 rt_encode() {
@@ -506,7 +514,8 @@ PFN_cuTensorMapEncodeTiled_v12000 rt_encode() {
 
 // 3-D tensor map over 14 bf16 digit planes, each [rows][ldk] (K-major): dims {K, rows, 14},
 // box {64, box_rows, 1}, 128-byte swizzle; reads outside {K, rows} return zeros.
-bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk, long plane_elems, int box_rows) {
+bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk, long plane_elems, int box_rows,
+                      int nd) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = rt_encode();
     if (enc == nullptr) {
         bm_set_error("cuTensorMapEncodeTiled is unavailable from the driver");
@@ -516,7 +525,7 @@ bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk,
         bm_set_error("digit-plane tensor map: base or stride not 16-byte aligned");
         return BM_EINVAL;
     }
-    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)(2 * RT_D)};
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)(2 * nd)};
     cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)plane_elems * 2};
     cuuint32_t box[3] = {(cuuint32_t)RT_BK, (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -531,12 +540,12 @@ bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk,
 }
 
 long rt_ldk(long K) { return (K + RT_BK - 1) / RT_BK * RT_BK; }
-int rt_digit_planes() { return 2 * RT_D; }
+int rt_digit_planes(int nd) { return 2 * nd; }
 int rt_col_tile() { return RT_NT; }
 
 // Row exponents and digit planes of A; rowmax is scratch of `rows` 8-byte words.
 cudaError_t launch_digits_a(cudaStream_t s, const double2* A, long lda, int rows, int K, int* e, void* D, long ldk,
-                            void* rowmax) {
+                            void* rowmax, int nd) {
     if (rows <= 0 || K <= 0) return cudaSuccess;
     unsigned long long* mx = reinterpret_cast<unsigned long long*>(rowmax);
     cudaError_t err = cudaMemsetAsync(mx, 0, (size_t)rows * 8, s);
@@ -545,35 +554,43 @@ cudaError_t launch_digits_a(cudaStream_t s, const double2* A, long lda, int rows
     row_exponent_kernel<<<ceil_div(rows, 128), 128, 0, s>>>(mx, rows, e);
     dim3 blk(32, 8), grid(ceil_div(K, 32), ceil_div(rows, 32));
     digits_a_kernel<<<grid, blk, 0, s>>>(A, lda, rows, K, e, reinterpret_cast<__nv_bfloat16*>(D), ldk,
-                                         (long)rows * ldk);
+                                         (long)rows * ldk, nd);
     return cudaGetLastError();
 }
 
 cudaError_t launch_digits_x(cudaStream_t s, const double2* X, long ldx, int r0, int K, int n, int npad, int* f,
-                            void* D, long ldk) {
+                            void* D, long ldk, int nd) {
     if (n <= 0 || K <= 0) return cudaSuccess;
     col_exponent_kernel<<<n, 256, 0, s>>>(X, ldx, r0, K, f);
     const long t = (long)npad * K;
     digits_x_kernel<<<ceil_div(t, 256L), 256, 0, s>>>(X, ldx, r0, K, n, npad, f, reinterpret_cast<__nv_bfloat16*>(D),
-                                                      ldk, (long)npad * ldk);
+                                                      ldk, (long)npad * ldk, nd);
     return cudaGetLastError();
 }
 
-// Split count of one product so that every CTA covers about eight 256-wide K chunks.
+// Split count of one product so that every CTA covers about 32 K blocks of 64.
 int rt_splits(int K) {
-    const int chunks = ceil_div(K, RT_BK * RT_KB_CHUNK);
-    return std::max(1, std::min(16, chunks / 8));
+    const int kblocks = ceil_div(K, RT_BK);
+    return std::max(1, std::min(16, kblocks / 32));
 }
 
 // The products of one residual (at most two, sharing n and alpha): C += alpha A x each.  A product
 // with S > 1 K splits writes S m n doubles (Re and Im) to its workspace, reduced in order afterwards.
-cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, double alpha, int* d_err, int* launched) {
-    if (nprod < 1 || nprod > 2 || n <= 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(resid_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, RT_SMEM);
+cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, double alpha, int* d_err, int* launched,
+                    int nd) {
+    if (nprod < 1 || nprod > 2 || n <= 0 || (nd != 7 && nd != 8)) return cudaSuccess;
+    static bool attr7 = false, attr8 = false;
+    if (nd == 7 && !attr7) {
+        cudaError_t e = cudaFuncSetAttribute(resid_tc_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             RtCfg<7>::SMEM);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr7 = true;
+    }
+    if (nd == 8 && !attr8) {
+        cudaError_t e = cudaFuncSetAttribute(resid_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             RtCfg<8>::SMEM);
+        if (e != cudaSuccess) return e;
+        attr8 = true;
     }
     RtJob J{};
     J.nprod = nprod;
@@ -603,7 +620,10 @@ cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, doubl
     J.first_unit[2] = u;
     if (nprod == 1) J.first_unit[1] = u;
     if (u == 0) return cudaSuccess;
-    resid_tc_kernel<<<u, RT_THREADS, RT_SMEM, s>>>(J, d_err);
+    if (nd == 7)
+        resid_tc_kernel<7><<<u, RT_THREADS, RtCfg<7>::SMEM, s>>>(J, d_err);
+    else
+        resid_tc_kernel<8><<<u, RT_THREADS, RtCfg<8>::SMEM, s>>>(J, d_err);
     *launched += 1;
     for (int q = 0; q < nprod; ++q) {
         const RtArgs& a = prods[q];

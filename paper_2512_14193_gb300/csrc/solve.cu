@@ -283,7 +283,7 @@ bm_status residual_tc(bm_ctx* c, const double2* B, const double2* X, double2* R,
         for (int q = 0; q < nprod; ++q) {
             const int r0 = (c->form == BM_MIXED && q == 0) ? 2 * N : 0;
             const int K = (c->form == BM_MIXED && q == 0) ? N : 2 * N;
-            SV_CUDA(launch_digits_x(s, X, ld, r0, K, nrhs, npad, c->d_dxe[q], c->d_dx[q], c->dx_ldk[q]));
+            SV_CUDA(launch_digits_x(s, X, ld, r0, K, nrhs, npad, c->d_dxe[q], c->d_dx[q], c->dx_ldk[q], c->rt_nd));
         }
     }
     // mixed: Mbot (K = 2N, the longer units) first, then Mtop; ordinary: A
@@ -313,7 +313,7 @@ bm_status residual_tc(bm_ctx* c, const double2* B, const double2* X, double2* R,
     int nl = 0;
     {
         BM_PROF(c, "resid_tc_kernel (+ split-K reduction)");
-        SV_CUDA(gemm_rt(s, P, np, nrhs, -1.0, c->d_err, &nl));
+        SV_CUDA(gemm_rt(s, P, np, nrhs, -1.0, c->d_err, &nl, c->rt_nd));
     }
     c->launches += 1 + 2 * nprod + nl;
     return BM_OK;

@@ -71,8 +71,9 @@ def test_tight_tolerance_needs_fp64_residuals(bmlib, handle):
         bmlib.bm_assemble(handle, curve.kind, curve.params4(), 64, 2.0, 3.0, bmlib.BM_MIXED,
                           bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=1e-14, residual=0))
     assert e.value.status == bmlib.BM_EINVAL
-    bmlib.bm_assemble(handle, curve.kind, curve.params4(), 64, 2.0, 3.0, bmlib.BM_MIXED,
-                      bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=1e-14, residual=2))
+    for resid in (bmlib.BM_RESID_FP64_ALL, bmlib.BM_RESID_TC_ALL):
+        bmlib.bm_assemble(handle, curve.kind, curve.params4(), 64, 2.0, 3.0, bmlib.BM_MIXED,
+                          bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, refine_tol=1e-14, residual=resid))
 
 
 @pytest.mark.gpu

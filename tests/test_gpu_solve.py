@@ -229,7 +229,7 @@ def test_profile_reports_every_kernel_and_the_same_solution(bmlib, handle):
     assert np.array_equal(X1, X2)
     names = {k for k, _, _ in prof}
     for k in ("cgemm_tc_kernel (Schur complement)", "panel_lc_kernel", "cgemm_tc_kernel (trailing update)",
-              "trsv_g_step_kernel", "resid_df_kernel (+ split-K reduction)", "eta_kernel"):
+              "trsv_g_step_kernel", "resid_tc_kernel (+ split-K reduction)", "eta_kernel"):
         assert k in names, k
     assert all(l >= 1 and ms > 0 for _, l, ms in prof)
     assert [ms for _, _, ms in prof] == sorted([ms for _, _, ms in prof], reverse=True)
@@ -256,3 +256,22 @@ def test_tensor_core_residual_ragged_shapes(bmlib, handle, form, nrhs):
     eta = (O.backward_error_mixed(O.mixed_blocks(g, P), X, B) if form == 0
            else O.backward_error_dense(O.ordinary_matrix(g, P), X, B))
     assert eta <= 5e-12
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", [0, 1])
+def test_eight_digit_residual_refines_to_fp64_accuracy(bmlib, handle, form):
+    # every residual afresh from eight-digit tensor-core products: TF32 factors refined to 1e-14
+    # (beyond what FP32-updated residuals can certify), confirmed by the oracle's FP64 residual
+    curve, N, k0, k1 = W.kite(), 300, 9.0 - 0.2j, 13.5 - 0.3j
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, k0, k1, form,
+                      bmlib.make_opts(bmlib.BM_CF32_TF32_IR, refine_tol=1e-14, residual=bmlib.BM_RESID_TC_ALL))
+    assert bmlib.bm_factor(handle) == 0
+    g, P = O.nodes(curve, N), O.default_params(k0, k1)
+    B = _rhs(g, P, N, form, 5, full=(form == 0), seed=4)
+    X = np.zeros_like(B, order="F")
+    info = bmlib.bm_solve(handle, B, X)
+    assert info.backward_error <= 1e-14
+    eta = (O.backward_error_mixed(O.mixed_blocks(g, P), X, B) if form == 0
+           else O.backward_error_dense(O.ordinary_matrix(g, P), X, B))
+    assert eta <= 3e-14
