@@ -102,7 +102,7 @@ typedef struct {
  *        FP64 operand split into two FP32 parts, exact products, compensated sums: ~1e-12 of
  *        |A||x|), later ones updated as in mode 0;
  *     BM_RESID_TC_ALL (4): every residual from exact tensor-core digit products as in mode 0, with
- *        eight digits per operand (~2^-57 of the row and column scales).
+ *        nine digits per operand (~2^-64 of the row and column scales).
  *  The updated residuals of modes 0, 1 and 3 carry the FP32 product error of each update, so the
  *  backward error they track is reliable down to about 1e-12; refine_tol below 1e-12 needs
  *  BM_RESID_FP64_ALL or BM_RESID_TC_ALL (bm_assemble returns BM_EINVAL otherwise).
@@ -267,10 +267,14 @@ bm_status bm_far_field_static(bm_ctx* ctx, const bm_c64* X, int ldx, int nrhs, c
  *   Hankel   H = [mu_{i+j}], Hs = [mu_{i+j+1}] (LM x LM block Hankel matrices);
  *   rank     H = W1 S W2^H, r = #{s_i > rank_tol s_1};
  *   pencil   the eigenvalues zeta of W1_r^H Hs W2_r S_r^{-1} give omega = center + radius zeta.
- * Every contour point is assembled, factored and solved on the device (as bm_assemble, bm_factor,
- * bm_solve, in the precision opts->prec selects), `workers` points at a time on their own streams;
- * the moments, Hankel matrices and the small pencil are formed on the device, the small SVD and
- * eigenvalue problem (size L M at most 256) use cuSOLVER. */
+ * The contour points run in batches of up to `batch` points (one handle each) and each phase covers
+ * a whole batch: one launch assembles every point's system (grid.z = point); for the CF32 precisions
+ * one launch forms every point's Schur complement on the tensor cores (a tensor map set per point);
+ * the points' LU factorisations replay their captured graphs on the points' streams at once, with the
+ * panel cluster size picked on the first batch by timing each candidate (the autotuner); `workers`
+ * host threads run the refined solves (bm_solve, precision opts->prec); one launch projects every
+ * point's solutions.  The moments, Hankel matrices and the small pencil are formed on the device,
+ * the small SVD and eigenvalue problem (size L M at most 256) use cuSOLVER. */
 typedef struct {
     bm_c64 center;    /* contour centre in the k_out plane */
     double radius;    /* circle radius, > 0 */
@@ -278,7 +282,9 @@ typedef struct {
     int nmoments;     /* M, 1 .. 16 */
     bm_c64 k_ratio;   /* k_in = k_ratio * k_out on the contour */
     double rank_tol;  /* relative singular-value cut; 0 selects 1e-8 */
-    int workers;      /* contour points in flight at once, 1 .. 16; 0 selects 4 */
+    int workers;      /* host threads running the points' refined solves, 1 .. 64; 0 selects 16 */
+    int batch;        /* contour points per batched launch, 1 .. 64; 0 selects min(npoints, 32) */
+    int panel_cluster;/* LU panel cluster size, 1 .. 16; 0 lets the autotuner pick it on the first batch */
 } bm_ssm_opts;
 
 typedef struct {
@@ -288,6 +294,11 @@ typedef struct {
     double max_backward_error;  /* largest backward error of the contour solves */
     double t_total_ms;   /* wall time of the call */
     double t_points_ms;  /* wall time of the contour points (assemble + factor + solve + projection) */
+    double t_assemble_ms, t_factor_ms, t_solve_ms;  /* wall time of each phase, summed over batches */
+    int batch;           /* points per batched launch */
+    int panel_cluster;   /* LU panel cluster size used */
+    double tune_ms[3];   /* autotuner: factor-phase wall time of the first batch with clusters of 16, 8, 4
+                            CTAs (0 when not tuned) */
 } bm_ssm_info;
 
 /* Eigenvalues of the discretised system `form` (curve, N as in bm_assemble) inside a circle.
@@ -300,6 +311,12 @@ typedef struct {
 bm_status bm_ssm(int device, const bm_curve* curve, int N, bm_formulation form, const bm_opts* opts,
                  const bm_ssm_opts* ssm, const bm_c64* V, int ldv, int L, bm_c64* omega, int cap,
                  double* sigma, bm_ssm_info* info);
+
+/* bm_ssm keeps the handles and device buffers of its last batch of contour points (and the panel
+ * cluster size its autotuner picked) for the next call with the same device, N, formulation,
+ * options, batch size and L: repeated contour solves then reuse them instead of allocating again.
+ * bm_ssm_release frees what is kept for `device` (every device when device < 0). */
+bm_status bm_ssm_release(int device);
 
 /* ---- Serving: continuous batching of independent solves ----
  * A library service around the solver (the paper has no counterpart; its solves arrive as a

@@ -50,12 +50,15 @@ class bm_solve_info(C.Structure):
 
 class bm_ssm_opts(C.Structure):
     _fields_ = [("center", bm_c64), ("radius", C.c_double), ("npoints", C.c_int), ("nmoments", C.c_int),
-                ("k_ratio", bm_c64), ("rank_tol", C.c_double), ("workers", C.c_int)]
+                ("k_ratio", bm_c64), ("rank_tol", C.c_double), ("workers", C.c_int), ("batch", C.c_int),
+                ("panel_cluster", C.c_int)]
 
 
 class bm_ssm_info(C.Structure):
     _fields_ = [("rank", C.c_int), ("n_inside", C.c_int), ("max_iterations", C.c_int),
-                ("max_backward_error", C.c_double), ("t_total_ms", C.c_double), ("t_points_ms", C.c_double)]
+                ("max_backward_error", C.c_double), ("t_total_ms", C.c_double), ("t_points_ms", C.c_double),
+                ("t_assemble_ms", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("batch", C.c_int), ("panel_cluster", C.c_int), ("tune_ms", C.c_double * 3)]
 
 
 class bm_server_opts(C.Structure):
@@ -117,6 +120,7 @@ def lib():
     L.bm_ssm.argtypes = [I, C.POINTER(bm_curve), I, I, C.POINTER(bm_opts), C.POINTER(bm_ssm_opts), P, I, I, P, I,
                          C.POINTER(D), C.POINTER(bm_ssm_info)]
     L.bm_hankel01.argtypes = [P, P, I, P, P, I]
+    L.bm_ssm_release.argtypes = [I]
     L.bm_zeta_weights.argtypes = [I, C.POINTER(D), C.POINTER(D)]
     L.bm_hankel_anchor_table.argtypes = [C.POINTER(D), I, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(D),
                                          C.POINTER(D)]
@@ -135,7 +139,7 @@ def lib():
                  "bm_server_stats_get", "bm_server_destroy",
                  "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_zeta_weights", "bm_memory",
                  "bm_destroy",
-                 "bm_kernel_launches", "bm_enqueue_probe", "bm_profile"):
+                 "bm_kernel_launches", "bm_enqueue_probe", "bm_profile", "bm_ssm_release"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -337,7 +341,8 @@ def bm_far_field_static(h, X, angles, U) -> None:
 
 
 def bm_ssm(device: int, kind: int, params, N: int, formulation: int, opts: bm_opts | None, center, radius: float,
-           npoints: int, nmoments: int, k_ratio, V, rank_tol: float = 0.0, workers: int = 0):
+           npoints: int, nmoments: int, k_ratio, V, rank_tol: float = 0.0, workers: int = 0, batch: int = 0,
+           panel_cluster: int = 0):
     """Eigenvalues inside a circle (block Sakurai-Sugiura).  V: host (nsys x L) probe columns.
     Returns (omega[r] with the n_inside interior ones first, sigma[L M], bm_ssm_info)."""
     cv = bm_curve()
@@ -353,6 +358,8 @@ def bm_ssm(device: int, kind: int, params, N: int, formulation: int, opts: bm_op
     so.k_ratio = _c64(k_ratio)
     so.rank_tol = float(rank_tol)
     so.workers = int(workers)
+    so.batch = int(batch)
+    so.panel_cluster = int(panel_cluster)
     pv, ldv, L, dev, _kv = _colmajor(V, 0, writable=False)
     if dev:
         raise ValueError("bm_ssm takes host probe vectors")
@@ -364,6 +371,11 @@ def bm_ssm(device: int, kind: int, params, N: int, formulation: int, opts: bm_op
                         C.byref(so), pv, ldv, L, C.c_void_p(om.ctypes.data), cap,
                         sig.ctypes.data_as(C.POINTER(C.c_double)), C.byref(info)), "bm_ssm")
     return om[:info.rank].copy(), sig, info
+
+
+def bm_ssm_release(device: int = -1) -> None:
+    """Free the contour solver's kept batch of handles and buffers (every device when device < 0)."""
+    _check(lib().bm_ssm_release(int(device)), "bm_ssm_release")
 
 
 def bm_server_create(device: int = 0, slots: int = 4, budget_bytes: int = 0, opts: bm_opts | None = None):

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 namespace {
@@ -34,6 +35,36 @@ extern "C" const char* bm_strerror(bm_status s) {
 // ------------------------------------------------------------------------------------------------
 // allocation with budget accounting
 // ------------------------------------------------------------------------------------------------
+namespace {
+// One stream-ordered memory pool per device for all handles of the process.  Freed blocks stay
+// mapped in the pool (release threshold: unlimited), so handles that come and go - contour batches,
+// serving requests - reuse memory instead of mapping it again on every allocation.  The handles'
+// HBM budgets still bound what each holds.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaMemPool_t device_pool(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pool[dev] == nullptr) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+}  // namespace
+
 bm_status ctx_alloc(bm_ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return BM_OK;
@@ -44,7 +75,8 @@ bm_status ctx_alloc(bm_ctx* c, void** p, size_t bytes) {
     // stream-ordered allocation on the handle's stream: unlike cudaMalloc / cudaFree it never
     // waits for the rest of the device, so handles that come and go (a serving loop, contour
     // workers) do not stall each other's streams
-    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+    cudaMemPool_t pool = device_pool(c->device);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, c->stream) : cudaMallocAsync(p, bytes, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -97,6 +129,7 @@ void drop_solve_graphs(bm_ctx* c) {
 
 void drop_graphs(bm_ctx* c) {
     drop_slot(c->g_factor);
+    drop_slot(c->g_lu);
     drop_solve_graphs(c);
 }
 
@@ -178,12 +211,6 @@ double2 d2(bm_c64 z) { return make_double2(z.re, z.im); }
 
 long round_up(long a, long b) { return (a + b - 1) / b * b; }
 
-struct Plan {
-    long ldtop = 0, ldbot = 0, ldA = 0, ldF = 0, ldk_schur = 0, ldk_lu = 0, ldk_c = 0;
-    int n = 0, nsys = 0, nb = 0, kseg = 0, nblk = 0;
-    size_t bytes = 0;
-};
-
 Plan make_plan(int N, int form, int prec, int nb_user, int bs, int nd) {
     Plan p;
     const bool c32 = prec != BM_FP64;
@@ -241,7 +268,7 @@ Plan make_plan(int N, int form, int prec, int nb_user, int bs, int nd) {
 // workspace for nrhs right-hand sides (an estimate from the same sizes ensure_ws uses, with a
 // margin for the split-K partial sums).
 size_t request_bytes(int N, int form, int prec, int nb, int nrhs) {
-    Plan p = make_plan(N, form, prec, nb, 64, 8);
+    Plan p = make_plan(N, form, prec, nb, 64, 9);
     const size_t w = (size_t)std::max(nrhs, 8);
     size_t b = p.bytes + 7 * (size_t)N * 8 + (size_t)p.nsys * w * 16 * 3 + (size_t)p.n * w * 16 * 2;
     if (prec == BM_FP64) {
@@ -376,8 +403,11 @@ extern "C" bm_status bm_memory(bm_ctx* c, size_t* held, size_t* budget) {
 }
 
 // ------------------------------------------------------------------------------------------------
-extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64 k_out, bm_c64 k_in,
-                                 bm_formulation form, const bm_opts* opts) {
+// Everything bm_assemble does; with defer_kernels the assembly kernel and what follows it (the
+// zeta band, the norm, the derived packs and planes, the tensor maps) wait for assemble_post, so that
+// a caller can assemble several handles' systems in one batched launch in between.
+bm_status assemble_impl(bm_ctx* c, const bm_curve* curve, int N, bm_c64 k_out, bm_c64 k_in, bm_formulation form,
+                        const bm_opts* opts, bool defer_kernels) {
     if (c == nullptr || curve == nullptr) return BM_EINVAL;
     if (N < 8 || N > 65536) {
         bm_set_error("N must be in [8, 65536]");
@@ -483,7 +513,7 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
     BM_CUDA_TRY(cudaSetDevice(c->device));
     cudaStreamSynchronize(c->stream);
     const int rmode = opts ? opts->refine_residual : BM_RESID_TC_UPDATE;
-    const int nd = rmode == BM_RESID_TC_ALL ? 8 : 7;
+    const int nd = rmode == BM_RESID_TC_ALL ? 9 : 7;
     Plan p = make_plan(N, form, prec, nb, 64, nd);
     // Same shape as the assembled system: assemble again into the same buffers (no device
     // allocation or release - cudaFree would wait for every stream of the device - and the cached
@@ -615,10 +645,41 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
         BM_CUDA_TRY(cudaMemcpyAsync(d_user, curve->user, 6 * (size_t)N * 8, cudaMemcpyHostToDevice, st));
     }
     BM_CUDA_TRY(launch_geometry(st, curve->kind, curve->p, N, d_user, c->d_geom));
-    BM_CUDA_TRY(launch_assemble(st, c));
+    c->opt_test_wait = test_wait;
+    c->nd_plan = p;
+    if (defer_kernels) {
+        BM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (d_user) ctx_free(c, d_user);
+        c->post_pending = true;
+        return BM_OK;
+    }
+    bm_status sp = assemble_post(c, true, true);
+    if (d_user) ctx_free(c, d_user);
+    return sp;
+}
+
+extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64 k_out, bm_c64 k_in,
+                                 bm_formulation form, const bm_opts* opts) {
+    return assemble_impl(c, curve, N, k_out, k_in, form, opts, false);
+}
+
+// The second half of assembly: the assembly kernel (unless a batched launch already wrote the
+// blocks), the zeta band, ||A||, the packs and planes the CF32 solves use, the panel set-up and the
+// tensor maps.
+bm_status assemble_post(bm_ctx* c, bool run_assembly_kernel, bool wait) {
+    cudaStream_t st = c->stream;
+    const int N = c->N, form = c->form, prec = c->prec, nd = c->rt_nd;
+    const bool c32 = prec != BM_FP64;
+    const Plan& p = c->nd_plan;
+    bm_status s = BM_OK;
+    c->post_pending = false;
+    if (run_assembly_kernel) {
+        BM_CUDA_TRY(launch_assemble(st, c));
+        c->launches += 1;
+    }
     BM_CUDA_TRY(launch_zeta_band(st, c));
     BM_CUDA_TRY(launch_normA(st, c));
-    c->launches += ((form == BM_MIXED) ? 4 : 3) + (c->zeta_p > 0 ? 1 : 0);
+    c->launches += ((form == BM_MIXED) ? 2 : 1) + (c->zeta_p > 0 ? 1 : 0);
     if (c32) {
         if (form == BM_MIXED) {
             BM_CUDA_TRY(launch_pack_solve(st, c, prec == BM_CF32_3XTF32_IR));
@@ -647,15 +708,13 @@ extern "C" bm_status bm_assemble(bm_ctx* c, const bm_curve* curve, int N, bm_c64
                                         nd));
             c->launches += 3;
         }
-        BM_CUDA_TRY(cudaStreamSynchronize(st));
-        ctx_free(c, rowmax);
+        ctx_free(c, rowmax);  // stream-ordered: released once the digit kernels are done with it
     }
-    BM_CUDA_TRY(cudaStreamSynchronize(st));
-    if (d_user) ctx_free(c, d_user);
-    BM_TRY(lu_setup(c, cl_cap, pkern));
-    // test hook read by the tensor-core products (d_err[1])
-    BM_CUDA_TRY(cudaMemcpyAsync(c->d_info + 2, &test_wait, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    BM_TRY(lu_setup(c, c->opt_cluster_cap, c->opt_panel_kernel));
+    // test hook read by the tensor-core products (d_err[1], any nonzero value sets it); a memset keeps
+    // the stream asynchronous (a copy from pageable memory would wait for the kernels above)
+    BM_CUDA_TRY(cudaMemsetAsync(c->d_info + 2, c->opt_test_wait ? 1 : 0, sizeof(int), c->stream));
+    if (wait) BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c32) {
         const bool split = prec == BM_CF32_3XTF32_IR;
         if (form == BM_MIXED) {
@@ -769,6 +828,39 @@ bm_status run_captured(bm_ctx* c, bm_ctx::GraphSlot* slot, Fn fn) {
 
 }  // namespace
 
+// The LU part of bm_factor alone (the Schur complement already in place, d_info cleared before it),
+// replayed from its own graph; stream-ordered, no synchronisation.  factor_result reads the outcome.
+bm_status factor_lu_enqueue(bm_ctx* c) {
+    return run_captured(c, &c->g_lu, [&]() -> bm_status { return lu_factor_enqueue(c); });
+}
+
+bm_status factor_result(bm_ctx* c, int* info) {
+    int h[2] = {0, 0};
+    BM_CUDA_TRY(cudaMemcpyAsync(h, c->d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (info) *info = h[0];
+    if (h[1] != 0) {
+        bm_set_error("factorisation: a bounded device-side wait timed out");
+        c->factored = false;
+        return BM_ETIMEOUT;
+    }
+    c->factored = true;
+    c->singular = h[0] != 0;
+    if (c->singular) {
+        bm_set_error("zero pivot in column " + std::to_string(h[0]));
+        return BM_ESINGULAR;
+    }
+    return BM_OK;
+}
+
+// Panel cluster size of an assembled handle (drops the captured factorisations).
+bm_status set_panel_cluster(bm_ctx* c, int cap) {
+    c->opt_cluster_cap = cap;
+    drop_slot(c->g_factor);
+    drop_slot(c->g_lu);
+    return lu_setup(c, cap, c->opt_panel_kernel);
+}
+
 extern "C" bm_status bm_factor(bm_ctx* c, int* info) {
     if (c == nullptr) return BM_EINVAL;
     if (info) *info = 0;
@@ -828,7 +920,7 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
     if (c->prec != BM_FP64) {
         // x digit planes and split-K workspace of the tensor-core residual
         const int N = c->N, np = rt_digit_planes(c->rt_nd);
-        const int npad = (int)round_up(w, rt_col_tile());
+        const int npad = (int)round_up(w, rt_col_tile(c->rt_nd));
         const int nprod = (c->form == BM_MIXED) ? 2 : 1;
         size_t wsz = 0;
         for (int q = 0; q < nprod; ++q) {
@@ -840,7 +932,7 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
             BM_TRY(alloc_t(c, &c->d_dx[q], (size_t)np * npad * c->dx_ldk[q] * 2));
             BM_TRY(alloc_t(c, &c->d_dxe[q], (size_t)npad * 4));
             BM_TRY(rt_make_map(c->tm_dx[q], c->d_dx[q], npad, K, c->dx_ldk[q], (long)npad * c->dx_ldk[q],
-                               rt_col_tile(), c->rt_nd));
+                               rt_col_tile(c->rt_nd), c->rt_nd));
             const int S = rt_splits((int)K);
             if (S > 1) wsz += 2 * (size_t)S * m * w;
         }

@@ -186,8 +186,9 @@ __device__ __forceinline__ void diag_outputs(const AsmArgs& a, int i, double2 ou
 constexpr int AT = 32;  // assembly tile
 constexpr int AY = 8;   // threads in y
 
+// One 32 x 32 tile pair (I <= J) of the assembled blocks, chosen by blockIdx.x.
 template <int FORM>
-__global__ void __launch_bounds__(AT* AY) assemble_kernel(AsmArgs a) {
+__device__ __forceinline__ void assemble_tile(const AsmArgs& a) {
     extern __shared__ double2 st[];  // [4][AT][AT+1] staging of the transposed tile
     // decode the upper-triangular tile pair (I <= J) from the linear block index
     long idx = blockIdx.x;
@@ -251,6 +252,18 @@ __global__ void __launch_bounds__(AT* AY) assemble_kernel(AsmArgs a) {
             for (int b = 0; b < 4; ++b) a.o[b][(long)jj + (long)ii * a.ld[b]] = st[(b * AT + tx) * (AT + 1) + il];
         }
     }
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(AT* AY) assemble_kernel(AsmArgs a) {
+    assemble_tile<FORM>(a);
+}
+
+// Several systems of the same size at once (contour points of one curve): system blockIdx.z takes
+// its wavenumbers, material constants and output blocks from args[blockIdx.z].
+template <int FORM>
+__global__ void __launch_bounds__(AT* AY) assemble_batch_kernel(const AsmArgs* __restrict__ args) {
+    assemble_tile<FORM>(args[blockIdx.z]);
 }
 
 // row sums of |A| for ||A||_inf; rows of an m x ncols column-major block, plus `add` per row
@@ -627,7 +640,7 @@ cudaError_t launch_geometry(cudaStream_t s, int kind, const double p[4], int N, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c) {
+static AsmArgs asm_args(const bm_ctx* c) {
     AsmArgs a{};
     a.N = c->N;
     a.h = 2.0 * PI / c->N;
@@ -653,7 +666,12 @@ cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c) {
         a.o[3] = c->d_A + N + N * c->ldA;
         a.ld[0] = a.ld[1] = a.ld[2] = a.ld[3] = c->ldA;
     }
-    long T = ceil_div(N, AT);
+    return a;
+}
+
+cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c) {
+    const AsmArgs a = asm_args(c);
+    long T = ceil_div(c->N, AT);
     long nblk = T * (T + 1) / 2;
     size_t smem = 4 * AT * (AT + 1) * sizeof(double2);
     dim3 blk(AT, AY);
@@ -666,6 +684,35 @@ cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c) {
         e = cudaFuncSetAttribute(assemble_kernel<BM_ORDINARY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         assemble_kernel<BM_ORDINARY><<<(unsigned)nblk, blk, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+// One launch assembling the systems of B handles of equal N and formulation (grid.z = handle);
+// d_args: device scratch of B * asm_args_bytes() bytes, filled here.
+size_t asm_args_bytes() { return sizeof(AsmArgs); }
+cudaError_t launch_assemble_batch(cudaStream_t s, bm_ctx* const* cs, int B, void* d_args) {
+    if (B < 1) return cudaSuccess;
+    std::vector<AsmArgs> h(B);
+    for (int b = 0; b < B; ++b) h[b] = asm_args(cs[b]);
+    cudaError_t e = cudaMemcpyAsync(d_args, h.data(), sizeof(AsmArgs) * B, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    const int N = cs[0]->N;
+    long T = ceil_div(N, AT);
+    long nblk = T * (T + 1) / 2;
+    size_t smem = 4 * AT * (AT + 1) * sizeof(double2);
+    dim3 blk(AT, AY), grid((unsigned)nblk, 1, (unsigned)B);
+    const AsmArgs* args = reinterpret_cast<const AsmArgs*>(d_args);
+    if (cs[0]->form == BM_MIXED) {
+        e = cudaFuncSetAttribute(assemble_batch_kernel<BM_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        assemble_batch_kernel<BM_MIXED><<<grid, blk, smem, s>>>(args);
+    } else {
+        e = cudaFuncSetAttribute(assemble_batch_kernel<BM_ORDINARY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        assemble_batch_kernel<BM_ORDINARY><<<grid, blk, smem, s>>>(args);
     }
     return cudaGetLastError();
 }

@@ -153,6 +153,13 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Sizes and leading dimensions of one assembled system (api.cu make_plan).
+struct Plan {
+    long ldtop = 0, ldbot = 0, ldA = 0, ldF = 0, ldk_schur = 0, ldk_lu = 0, ldk_c = 0;
+    int n = 0, nsys = 0, nb = 0, kseg = 0, nblk = 0;
+    size_t bytes = 0;
+};
+
 struct bm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -284,6 +291,7 @@ struct bm_ctx {
         int kernels = 0;
     };
     GraphSlot g_factor;
+    GraphSlot g_lu;                     // the LU of U33 alone (batched contour points)
     std::map<int, GraphSlot> g_solve;   // correction solve, keyed by nrhs
     std::map<int, GraphSlot> g_fp64;    // FP64 direct solve, keyed by nrhs
     unsigned long long launches = 0;    // kernels launched by this handle
@@ -305,6 +313,9 @@ struct bm_ctx {
     bool eager = false;          // bm_opts.eager: no CUDA graphs
     int opt_cluster_cap = 0;     // bm_opts.panel_cluster_max / panel_kernel of the assembled system
     int opt_panel_kernel = 0;
+    int opt_test_wait = 0;       // bm_opts.test_wait_timeout
+    Plan nd_plan;                // plan of the assembled system
+    bool post_pending = false;   // assembled with its kernels deferred (assemble_post not yet run)
 
     // per-kernel timing (bm_profile): while set, every launch is bracketed by two events on the
     // handle's stream and recorded here (graphs are bypassed)

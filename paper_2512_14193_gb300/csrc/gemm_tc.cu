@@ -25,6 +25,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
+#include <vector>
+
 namespace {
 
 constexpr int BM = TC_BM, BN = TC_BN;
@@ -164,12 +167,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// The body of one CTA: tile (tm, tn) of C, K split z of S.  The four tensor maps are param-space
+// copies (single product) or global-memory entries of a batch.
 template <int OUT>
-__global__ void __launch_bounds__(192, 1)
-    cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmAr, const __grid_constant__ CUtensorMap tmAi,
-                    const __grid_constant__ CUtensorMap tmBr, const __grid_constant__ CUtensorMap tmBi,
-                    float* __restrict__ Cr, float* __restrict__ Ci, double2* __restrict__ C64, long ldc, long zstride,
-                    int m, int n, int kext, int S, float alpha, float beta, int* __restrict__ err) {
+__device__ __forceinline__ void cgemm_tc_body(const CUtensorMap& tmAr, const CUtensorMap& tmAi, const CUtensorMap& tmBr,
+                                              const CUtensorMap& tmBi, float* __restrict__ Cr, float* __restrict__ Ci,
+                                              double2* __restrict__ C64, long ldc, long zstride, int m, int n, int kext,
+                                              int S, int zsplit, float alpha, float beta, int* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     // full[S], empty[S], done, never (the test hook's barrier: initialised, never arrived on)
@@ -180,8 +184,8 @@ __global__ void __launch_bounds__(192, 1)
     const int tm = blockIdx.x, tn = blockIdx.y;
     // this CTA's K split: k-blocks [kb_begin, kb_begin + nkb)
     const int nkb_all = (kext + BKE - 1) / BKE;
-    const int kb_begin = (int)((long)blockIdx.z * nkb_all / S);
-    const int nkb = (int)((long)(blockIdx.z + 1) * nkb_all / S) - kb_begin;
+    const int kb_begin = (int)((long)zsplit * nkb_all / S);
+    const int nkb = (int)((long)(zsplit + 1) * nkb_all / S) - kb_begin;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
     const uint32_t never = smem_u32(bars + 2 * STAGES + 1);
 
@@ -318,8 +322,8 @@ __global__ void __launch_bounds__(192, 1)
                 }
             } else if (OUT == OUT_PART && row < m) {
                 // slice z of the workspace: m x n column-major, leading dimension ldc (= m)
-                float* Pr = Cr + (long)blockIdx.z * zstride;
-                float* Pi = Ci + (long)blockIdx.z * zstride;
+                float* Pr = Cr + (long)zsplit * zstride;
+                float* Pi = Ci + (long)zsplit * zstride;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const long col = col0 + c0 + q;
@@ -385,6 +389,31 @@ __global__ void __launch_bounds__(192, 1)
         tmem_dealloc(tmem, tc_tmem_cols<OUT>());
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(192, 1)
+    cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmAr, const __grid_constant__ CUtensorMap tmAi,
+                    const __grid_constant__ CUtensorMap tmBr, const __grid_constant__ CUtensorMap tmBi,
+                    float* __restrict__ Cr, float* __restrict__ Ci, double2* __restrict__ C64, long ldc, long zstride,
+                    int m, int n, int kext, int S, float alpha, float beta, int* __restrict__ err) {
+    cgemm_tc_body<OUT>(tmAr, tmAi, tmBr, tmBi, Cr, Ci, C64, ldc, zstride, m, n, kext, S, (int)blockIdx.z, alpha, beta,
+                       err);
+}
+
+// One product per blockIdx.z: C_z = beta C_z + alpha A_z B_z^T for a batch of equal-shape products
+// (the contour points' Schur complements), maps and outputs read from global memory.
+struct alignas(64) TcBatchEntry {
+    CUtensorMap map[4];  // A re, A im, B re, B im
+    float* Cr;
+    float* Ci;
+    long ldc;
+};
+__global__ void __launch_bounds__(128, 1)
+    cgemm_tc_batch_kernel(const TcBatchEntry* __restrict__ E, int m, int n, int kext, float alpha, int* __restrict__ err) {
+    const TcBatchEntry& e = E[blockIdx.z];
+    cgemm_tc_body<OUT_C32>(e.map[0], e.map[1], e.map[2], e.map[3], e.Cr, e.Ci, nullptr, e.ldc, 0, m, n, kext, 1, 0,
+                           alpha, 0.f, err);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -582,5 +611,35 @@ cudaError_t launch_pack_b(cudaStream_t s, const float* Vr, const float* Vi, long
     const long t = (long)K * nrhs;
     if (t == 0) return cudaSuccess;
     pack_b_kernel<<<ceil_div(t, 256L), 256, 0, s>>>(Vr, Vi, ldv, K, nrhs, split, Br, Bi, ldk);
+    return cudaGetLastError();
+}
+
+// Batched Schur-type product: for each of B entries (maps: 4 opaque 128-byte tensor maps, outputs)
+// C = alpha A B^T (beta = 0), one launch with grid.z = B.  d_entries: device scratch of
+// B * tc_batch_entry_bytes() bytes, filled here.
+size_t tc_batch_entry_bytes() { return sizeof(TcBatchEntry); }
+cudaError_t gemm_tc_batch(cudaStream_t s, int B, const void* const* maps, float* const* Cr, float* const* Ci,
+                          const long* ldc, int m, int n, int kext, float alpha, void* d_entries, int* d_err) {
+    if (B < 1 || m <= 0 || n <= 0 || kext <= 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(cgemm_tc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    std::vector<TcBatchEntry> h(B);
+    for (int b = 0; b < B; ++b) {
+        for (int q = 0; q < 4; ++q)
+            std::memcpy(&h[b].map[q], static_cast<const unsigned char*>(maps[b]) + 128 * q, sizeof(CUtensorMap));
+        h[b].Cr = Cr[b];
+        h[b].Ci = Ci[b];
+        h[b].ldc = ldc[b];
+    }
+    cudaError_t e = cudaMemcpyAsync(d_entries, h.data(), sizeof(TcBatchEntry) * B, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(m, BM), ceil_div(n, BN), B);
+    cgemm_tc_batch_kernel<<<grid, 128, SMEM_BYTES, s>>>(reinterpret_cast<const TcBatchEntry*>(d_entries), m, n, kext,
+                                                        alpha, d_err);
     return cudaGetLastError();
 }

@@ -5,6 +5,8 @@
 // assemble.cu
 cudaError_t launch_geometry(cudaStream_t s, int kind, const double p[4], int N, const double* d_user, double* d_geom);
 cudaError_t launch_assemble(cudaStream_t s, const bm_ctx* c);
+size_t asm_args_bytes();
+cudaError_t launch_assemble_batch(cudaStream_t s, bm_ctx* const* cs, int B, void* d_args);
 cudaError_t launch_zeta_band(cudaStream_t s, const bm_ctx* c);  // high-order zeta corrections (zeta_p > 0)
 cudaError_t launch_normA(cudaStream_t s, const bm_ctx* c);
 cudaError_t launch_plane_wave(cudaStream_t s, const bm_ctx* c, const double* d_ang, int nrhs, double2* B, long ldb);
@@ -39,6 +41,9 @@ cudaError_t gemm_tc_split(cudaStream_t s, const void* tAr, const void* tAi, cons
                           int* d_err, int* launched);
 cudaError_t launch_pack_b(cudaStream_t s, const float* Vr, const float* Vi, long ldv, int K, int nrhs, int split,
                           float* Br, float* Bi, long ldk);
+size_t tc_batch_entry_bytes();
+cudaError_t gemm_tc_batch(cudaStream_t s, int B, const void* const* maps, float* const* Cr, float* const* Ci,
+                          const long* ldc, int m, int n, int kext, float alpha, void* d_entries, int* d_err);
 
 // lu.cu
 bm_status lu_setup(bm_ctx* c, int cluster_cap, int panel_kernel);
@@ -98,7 +103,7 @@ struct RtArgs {
 };
 long rt_ldk(long K);                 // leading dimension of a digit plane row (K rounded to 64)
 int rt_digit_planes(int nd);         // planes per operand (nd digits x Re, Im)
-int rt_col_tile();                   // right-hand sides per CTA
+int rt_col_tile(int nd);             // right-hand sides per CTA
 int rt_splits(int K);                // K splits of a product
 bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk, long plane_elems, int box_rows,
                       int nd);
@@ -108,3 +113,11 @@ cudaError_t launch_digits_x(cudaStream_t s, const double2* X, long ldx, int r0, 
                             void* D, long ldk, int nd);
 cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, double alpha, int* d_err, int* launched,
                     int nd);
+
+// api.cu: assembly in two halves (the batched contour solver assembles many handles at once)
+bm_status assemble_impl(bm_ctx* c, const bm_curve* curve, int N, bm_c64 k_out, bm_c64 k_in, bm_formulation form,
+                        const bm_opts* opts, bool defer_kernels);
+bm_status assemble_post(bm_ctx* c, bool run_assembly_kernel, bool wait);  // wait: synchronise the stream
+bm_status factor_lu_enqueue(bm_ctx* c);              // LU of the Schur complement in place (graph)
+bm_status factor_result(bm_ctx* c, int* info);       // waits, reads info / timeout, sets the state
+bm_status set_panel_cluster(bm_ctx* c, int cap);     // panel cluster cap of an assembled handle

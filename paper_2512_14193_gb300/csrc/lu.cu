@@ -31,6 +31,9 @@
 // (the same sums as L_bb^{-1} Y_b formed inside every step, without recomputing it in each CTA).
 #include "lu_internal.cuh"
 
+#include <map>
+#include <mutex>
+
 using namespace lu_detail;
 
 namespace {
@@ -910,8 +913,18 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* din
 // once), capped by bm_opts.panel_cluster_max (fewer CTAs put more rows on each thread, which selects
 // the narrower sub-panel variants), and the panel kernel bm_opts.panel_kernel selects.
 bm_status lu_setup(bm_ctx* c, int cluster_cap, int panel_kernel) {
+    // the occupancy query is a property of the device and kernel: asked once per process and device
+    static std::mutex mu;
+    static std::map<int, int> cache[2];
     int& dev_max = (c->prec == BM_FP64) ? c->panel_cluster_z64 : c->panel_cluster_c32;
-    if (dev_max == 0) dev_max = (c->prec == BM_FP64) ? query_cluster_max_z64() : query_cluster_max_c32();
+    if (dev_max == 0) {
+        const int kind = (c->prec == BM_FP64) ? 1 : 0;
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache[kind].find(c->device);
+        if (it == cache[kind].end())
+            it = cache[kind].emplace(c->device, kind ? query_cluster_max_z64() : query_cluster_max_c32()).first;
+        dev_max = it->second;
+    }
     c->panel_cluster = dev_max;
     if (cluster_cap >= 1 && cluster_cap <= MAX_CLUSTER) c->panel_cluster = std::min(c->panel_cluster, cluster_cap);
     c->panel_lane_col = panel_kernel == 0;

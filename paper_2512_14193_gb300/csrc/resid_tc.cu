@@ -42,24 +42,25 @@
 namespace {
 
 constexpr int RT_BM = 128;   // output rows per CTA
-constexpr int RT_NT = 32;    // right-hand sides per CTA (the last column tile may use 16)
 constexpr int RT_BK = 64;    // K elements per stage: bf16 rows of 128 bytes (one swizzle span)
 constexpr int RT_AST = 3;    // stages of A digit pairs
 constexpr int RT_TILE_A = RT_BM * RT_BK * 2;  // one digit plane of A: 16 KB
-constexpr int RT_TILE_X = RT_NT * RT_BK * 2;  // one digit plane of x: 4 KB
 constexpr int RT_A_STAGE = 2 * RT_TILE_A;     // Re and Im of one digit
 constexpr int RT_THREADS = 320;
 constexpr uint64_t RT_WAIT_NS = 2000000000ull;
-// D digits per operand (7: pairs to level 6, 2^-50; 8: to level 7, 2^-57).  Level sums over a chunk
-// stay below 2^24: D pairs x 2 products x 4096 x chunk K, so the chunk is 256 for D = 7 and 128 for
-// D = 8.  Tensor memory: real parts of levels 0..D-1 at columns 32 l, imaginary parts at 32 (D + l).
+// D digits per operand (7: pairs to level 6, 2^-50; 9: to level 8, 2^-64) and NT right-hand sides
+// per CTA (32 for D = 7, 16 for D = 9).  Level sums over a chunk stay below 2^24: D pairs x 2
+// products x 4096 x chunk K, so the chunk is 256 for D = 7 and 128 for D = 9.  Tensor memory:
+// real parts of levels 0..D-1 at columns NT l, imaginary parts at NT (D + l).
 template <int D>
 struct RtCfg {
+    static constexpr int NT = D <= 7 ? 32 : 16;         // right-hand sides per CTA
+    static constexpr int TILE_X = NT * RT_BK * 2;       // one digit plane of x
     static constexpr int KB_CHUNK = D <= 7 ? 4 : 2;     // K blocks of 64 per exact chunk
-    static constexpr int X_BUF = 2 * D * RT_TILE_X;     // all digits of x, Re and Im
+    static constexpr int X_BUF = 2 * D * TILE_X;        // all digits of x, Re and Im
     static constexpr int SMEM = RT_AST * RT_A_STAGE + 2 * X_BUF + 1024 + 256;
-    static_assert(2 * D * RT_NT <= 512, "the level accumulators fit tensor memory");
-    static_assert(D * RT_NT <= 256, "the widest MMA (A digit 0 against all x digits) has N <= 256");
+    static_assert(2 * D * NT <= 512, "the level accumulators fit tensor memory");
+    static_assert(D * NT <= 256, "the widest MMA (A digit 0 against all x digits) has N <= 256");
     static_assert(D * 2 * 4096L * 64 * KB_CHUNK <= (1L << 24), "chunk sums stay exact in FP32");
     static_assert(SMEM <= 232448, "shared memory");
 };
@@ -171,6 +172,7 @@ struct RtJob {
 template <int D>
 __global__ void __launch_bounds__(RT_THREADS, 1) resid_tc_kernel(const __grid_constant__ RtJob J, int* __restrict__ err) {
     constexpr int RT_D = D, RT_KB_CHUNK = RtCfg<D>::KB_CHUNK, RT_X_BUF = RtCfg<D>::X_BUF;
+    constexpr int RT_NT = RtCfg<D>::NT, RT_TILE_X = RtCfg<D>::TILE_X;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;                               // RT_AST stages of (Re, Im) digit tiles of A
@@ -425,14 +427,44 @@ __global__ void row_exponent_kernel(const unsigned long long* __restrict__ mx, i
     e[i] = m > 0.0 ? ex + 1 : 0;
 }
 
-__device__ __forceinline__ void digits_of(double v, int nd, __nv_bfloat16* out, long stride) {
-    // v in (-1/2, 1/2): nd base-128 digits, each an integer in [-64, 64] (exact in bf16)
-    for (int d = 0; d < nd; ++d) {
-        v *= 128.0;
-        const double a = rint(v);
-        v -= a;
-        out[d * stride] = __float2bfloat16_rn((float)a);
+// bf16 bit pattern of a small integer r, |r| <= 128 (exact: at most 8 significant bits)
+__device__ __forceinline__ unsigned short bf16_of_int(int r) {
+    if (r == 0) return 0;
+    const unsigned a = (unsigned)abs(r);
+    const int e = 31 - __clz(a);  // position of the leading bit, 0..7
+    const unsigned mant = (a << (7 - e)) & 0x7Fu;
+    return (unsigned short)((r < 0 ? 0x8000u : 0u) | ((unsigned)(127 + e) << 7) | mant);
+}
+
+// The nd base-128 digits of v 2^-ex (|v 2^-ex| < 1/2), most significant first, each an integer in
+// [-64, 64]: v 2^(7 nd - ex) rounded to the nearest integer M (|M| <= 2^(7 nd - 1)), written as
+// M = sum_d a_d 128^(nd - 1 - d) with balanced digits in [-64, 63] peeled off from the least
+// significant end and the most significant digit the remainder (which may be +64).
+// Integer arithmetic on the FP64 bit pattern only (FP64 arithmetic and conversions are slow here).
+__device__ __forceinline__ void digits_of(double v, int ex, int nd, __nv_bfloat16* out, long stride) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int E = (int)((bits >> 52) & 0x7FF);
+    long long M = 0;
+    // zero and subnormals (below any row scale used here) give zero digits; so does a value that
+    // does not fit its scale (only possible for non-finite data, which the backward error reports)
+    if (E != 0 && E != 0x7FF) {
+        const long long mant = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+        const int sh = E - 1075 + 7 * nd - ex;  // v 2^(7 nd - ex) = mant 2^sh, mant in [2^52, 2^53)
+        if (sh > 7 * nd - 54)                   // |v 2^-ex| >= 1/2: does not fit the scale
+            M = 0;
+        else if (sh >= 0)
+            M = mant << sh;
+        else if (sh > -62)
+            M = (mant + (1ll << (-sh - 1))) >> (-sh);  // round half up
+        if (bits >> 63) M = -M;
     }
+    for (int d = nd - 1; d >= 1; --d) {
+        int r = (int)(M & 127);
+        if (r >= 64) r -= 128;
+        M = (M - r) >> 7;
+        reinterpret_cast<unsigned short*>(out)[d * stride] = bf16_of_int(r);
+    }
+    reinterpret_cast<unsigned short*>(out)[0] = bf16_of_int((int)M);
 }
 
 // Digit planes of A: plane 2d + part holds digit d of the real (part 0) or imaginary (1) parts, K-major
@@ -453,8 +485,8 @@ __global__ void digits_a_kernel(const double2* __restrict__ A, long lda, int row
         const double2 v = t[tx][q];
         const int ex = e[r];
         __nv_bfloat16* o = D + (long)r * ldk + k;
-        digits_of(ldexp(v.x, -ex), nd, o, 2 * plane);
-        digits_of(ldexp(v.y, -ex), nd, o + plane, 2 * plane);
+        digits_of(v.x, ex, nd, o, 2 * plane);
+        digits_of(v.y, ex, nd, o + plane, 2 * plane);
     }
 }
 
@@ -493,8 +525,8 @@ __global__ void digits_x_kernel(const double2* __restrict__ X, long ldx, int r0,
     }
     const double2 v = X[r0 + k + (long)c * ldx];
     const int ex = f[c];
-    digits_of(ldexp(v.x, -ex), nd, o, 2 * plane);
-    digits_of(ldexp(v.y, -ex), nd, o + plane, 2 * plane);
+    digits_of(v.x, ex, nd, o, 2 * plane);
+    digits_of(v.y, ex, nd, o + plane, 2 * plane);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 rt_encode() {
@@ -541,7 +573,7 @@ bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk,
 
 long rt_ldk(long K) { return (K + RT_BK - 1) / RT_BK * RT_BK; }
 int rt_digit_planes(int nd) { return 2 * nd; }
-int rt_col_tile() { return RT_NT; }
+int rt_col_tile(int nd) { return nd <= 7 ? RtCfg<7>::NT : RtCfg<9>::NT; }
 
 // Row exponents and digit planes of A; rowmax is scratch of `rows` 8-byte words.
 cudaError_t launch_digits_a(cudaStream_t s, const double2* A, long lda, int rows, int K, int* e, void* D, long ldk,
@@ -578,24 +610,24 @@ int rt_splits(int K) {
 // with S > 1 K splits writes S m n doubles (Re and Im) to its workspace, reduced in order afterwards.
 cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, double alpha, int* d_err, int* launched,
                     int nd) {
-    if (nprod < 1 || nprod > 2 || n <= 0 || (nd != 7 && nd != 8)) return cudaSuccess;
-    static bool attr7 = false, attr8 = false;
+    if (nprod < 1 || nprod > 2 || n <= 0 || (nd != 7 && nd != 9)) return cudaSuccess;
+    static bool attr7 = false, attr9 = false;
     if (nd == 7 && !attr7) {
         cudaError_t e = cudaFuncSetAttribute(resid_tc_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              RtCfg<7>::SMEM);
         if (e != cudaSuccess) return e;
         attr7 = true;
     }
-    if (nd == 8 && !attr8) {
-        cudaError_t e = cudaFuncSetAttribute(resid_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             RtCfg<8>::SMEM);
+    if (nd == 9 && !attr9) {
+        cudaError_t e = cudaFuncSetAttribute(resid_tc_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             RtCfg<9>::SMEM);
         if (e != cudaSuccess) return e;
-        attr8 = true;
+        attr9 = true;
     }
     RtJob J{};
     J.nprod = nprod;
     J.n = n;
-    J.ntile_n = ceil_div(n, RT_NT);
+    J.ntile_n = ceil_div(n, rt_col_tile(nd));
     J.alpha = alpha;
     int u = 0;
     for (int q = 0; q < 2; ++q) {
@@ -623,7 +655,7 @@ cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, doubl
     if (nd == 7)
         resid_tc_kernel<7><<<u, RT_THREADS, RtCfg<7>::SMEM, s>>>(J, d_err);
     else
-        resid_tc_kernel<8><<<u, RT_THREADS, RtCfg<8>::SMEM, s>>>(J, d_err);
+        resid_tc_kernel<9><<<u, RT_THREADS, RtCfg<9>::SMEM, s>>>(J, d_err);
     *launched += 1;
     for (int q = 0; q < nprod; ++q) {
         const RtArgs& a = prods[q];

@@ -276,7 +276,7 @@ bm_status residual_tc(bm_ctx* c, const double2* B, const double2* X, double2* R,
         resid_init_kernel<<<ceil_div(t, 256), 256, 0, s>>>(B, X, ld, c->nsys, nsub, nrhs, R);
         SV_CUDA(cudaGetLastError());
     }
-    const int npad = (int)((nrhs + rt_col_tile() - 1) / rt_col_tile() * rt_col_tile());
+    const int nt = rt_col_tile(c->rt_nd), npad = (nrhs + nt - 1) / nt * nt;
     const int nprod = (c->form == BM_MIXED) ? 2 : 1;
     {
         BM_PROF(c, "digits_x (col_exponent/digits_x_kernel)");

@@ -76,7 +76,8 @@ def test_contour_and_server_argument_checks_need_no_gpu(bmlib):
                                   ctypes.c_void_p(V.ctypes.data), ldv, L_, ctypes.c_void_p(om.ctypes.data), cap,
                                   None, ctypes.byref(info))
 
-    for field, bad in (("radius", 0.0), ("npoints", 2), ("nmoments", 0), ("nmoments", 17), ("workers", 17),
+    for field, bad in (("radius", 0.0), ("npoints", 2), ("nmoments", 0), ("nmoments", 17), ("workers", 65),
+                       ("batch", 65), ("panel_cluster", 17), ("batch", -1),
                        ("rank_tol", 1.5)):
         s2 = bmlib.bm_ssm_opts.from_buffer_copy(so)
         setattr(s2, field, bad)

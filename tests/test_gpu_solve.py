@@ -260,8 +260,8 @@ def test_tensor_core_residual_ragged_shapes(bmlib, handle, form, nrhs):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("form", [0, 1])
-def test_eight_digit_residual_refines_to_fp64_accuracy(bmlib, handle, form):
-    # every residual afresh from eight-digit tensor-core products: TF32 factors refined to 1e-14
+def test_nine_digit_residual_refines_to_fp64_accuracy(bmlib, handle, form):
+    # every residual afresh from nine-digit tensor-core products: TF32 factors refined to 1e-14
     # (beyond what FP32-updated residuals can certify), confirmed by the oracle's FP64 residual
     curve, N, k0, k1 = W.kite(), 300, 9.0 - 0.2j, 13.5 - 0.3j
     bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, k0, k1, form,

@@ -65,17 +65,16 @@ def _golden():
     return g
 
 
-@pytest.mark.parametrize("prec,resid", [(2, 2), (0, 2)])
+@pytest.mark.parametrize("prec,resid", [(2, 2), (2, 4), (0, 2)])
 def test_ssm_contour_batch_n1024(bmlib, prec, resid):
     g = _golden()
     N, L = 1024, 16
     V = np.asfortranarray(W.gaussian_full(3 * N, L, 0))
     curve = W.ellipse(1.0, 0.6)
     # The contour runs ~0.25 from resonances, where T(z) is ill-conditioned, and the moments' noise
-    # must stay below the 1e-6 rank cut: FP32 factors then need every residual in FP64, refined to
-    # about the FP64 solve's own backward error (equal accuracy with the FP64 path).  The eight-digit
-    # tensor-core residual (fixed point relative to each row's largest entry, here the hypersingular
-    # near-diagonal band) bottoms out near 1e-16 in this normalisation, short of that.
+    # must stay below the 1e-6 rank cut: FP32 factors then need every residual formed afresh to
+    # FP64 accuracy (in FP64, resid 2, or from nine-digit tensor-core products, resid 4), refined
+    # to about the FP64 solve's own backward error (equal accuracy with the FP64 path).
     opts = bmlib.make_opts(prec, refine_tol=1e-15, residual=resid)
     om, sig, info = bmlib.bm_ssm(0, curve.kind, curve.params4(), N, 0, opts, 5.0, 0.5, 32, 4, 1.5, V, rank_tol=1e-6)
     assert info.rank == g["rank"] and info.n_inside == g["n_inside"] == 0
@@ -87,3 +86,24 @@ def test_ssm_contour_batch_n1024(bmlib, prec, resid):
     # eigenvalue estimates outside the contour are only loosely determined by the moments
     ref = np.sort_complex(np.array(g["omega"]))
     assert np.abs(np.sort_complex(om) - ref).max() < 2e-3 * np.abs(ref).max()
+
+
+def test_ssm_batches_and_cluster_sizes_agree(bmlib):
+    # the same contour in batches of 5 points (the last one ragged) and of all 16, with a fixed and an
+    # autotuned panel cluster: every result agrees (each point's solve is deterministic and the
+    # moments sum the points in a fixed order)
+    N, target = 128, _zero(2)
+    V = np.asfortranarray(W.gaussian_full(3 * N, 4, 3))
+    curve = W.circle(0.5)
+    out = []
+    for batch, cl in ((16, 0), (5, 4), (16, 16)):
+        om, sig, info = bmlib.bm_ssm(0, curve.kind, curve.params4(), N, 0, bmlib.make_opts(2), target, 0.05, 16, 4,
+                                     2.0, V, rank_tol=1e-6, batch=batch, panel_cluster=cl)
+        assert info.batch == batch and info.n_inside == 2
+        assert info.panel_cluster in ((16, 8, 4) if cl == 0 else (cl,))
+        if cl == 0:
+            assert all(t > 0 for t in info.tune_ms)
+        out.append((np.sort_complex(om[:2]), sig[:2].copy()))
+    for om, sig in out[1:]:
+        assert np.abs(om - out[0][0]).max() < 1e-9
+        assert np.abs(sig - out[0][1]).max() < 1e-9 * out[0][1][0]
