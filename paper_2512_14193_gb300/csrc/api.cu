@@ -324,7 +324,7 @@ extern "C" bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size
     bm_status s = alloc_t(c, &c->d_htab, tab.size() * sizeof(double2));
     if (s == BM_OK) s = alloc_t(c, &c->d_normA, 4 * sizeof(double));
     if (s == BM_OK) s = alloc_t(c, &c->d_info, 64 * sizeof(int));
-    if (s == BM_OK) s = alloc_t(c, &c->d_maps, 2 * swap_map_bytes());
+    if (s == BM_OK) s = alloc_t(c, &c->d_maps, 3 * swap_map_bytes());
     if (s != BM_OK) {
         bm_destroy(c);
         return s;
@@ -345,6 +345,12 @@ extern "C" bm_status bm_destroy(bm_ctx* c) {
     FREE(c->d_normA);
     FREE(c->d_info);
     FREE(c->d_maps);
+    if (c->la_hi) cudaStreamSynchronize(c->la_hi);
+    if (c->la_lo) cudaStreamSynchronize(c->la_lo);
+    for (cudaEvent_t& e : c->la_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->la_hi) cudaStreamDestroy(c->la_hi);
+    if (c->la_lo) cudaStreamDestroy(c->la_lo);
     for (auto& kv : c->allocs) cudaFreeAsync(kv.first, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);  // the stream-ordered frees above complete
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -739,6 +745,10 @@ bm_status assemble_post(bm_ctx* c, bool run_assembly_kernel, bool wait) {
         BM_TRY(tc_make_map(c->tm_lu[1], c->d_Lp_i, p.n, klu, p.ldk_lu, TC_BM));
         BM_TRY(tc_make_map(c->tm_lu[2], c->d_Up_r, p.n, klu, p.ldk_lu, TC_BN));
         BM_TRY(tc_make_map(c->tm_lu[3], c->d_Up_i, p.n, klu, p.ldk_lu, TC_BN));
+        if (p.n > p.nb) {  // the U12 pack from its row nb on (the look-ahead's rest of a trailing update)
+            BM_TRY(tc_make_map(c->tm_lu[4], c->d_Up_r + (long)p.nb * p.ldk_lu, p.n - p.nb, klu, p.ldk_lu, TC_BN));
+            BM_TRY(tc_make_map(c->tm_lu[5], c->d_Up_i + (long)p.nb * p.ldk_lu, p.n - p.nb, klu, p.ldk_lu, TC_BN));
+        }
         c->tm_ok = true;
     }
     c->assembled = true;
@@ -813,7 +823,9 @@ bm_status run_captured(bm_ctx* c, bm_ctx::GraphSlot* slot, Fn fn) {
             return BM_ECUDA;
         }
         slot->kernels = count_kernel_nodes(g);
-        e = cudaGraphInstantiate(&slot->exec, g, 0);
+        // kernel nodes keep the priority of the stream they were captured from (the factorisation's
+        // panel chain runs ahead of the trailing updates it overlaps)
+        e = cudaGraphInstantiate(&slot->exec, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
             slot->exec = nullptr;

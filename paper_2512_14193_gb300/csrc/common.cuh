@@ -233,7 +233,12 @@ struct bm_ctx {
     int* d_perm = nullptr;
     int* d_info = nullptr;
     int* d_err = nullptr;
-    void* d_maps = nullptr;    // two row-interchange maps used by the factorisation
+    void* d_maps = nullptr;    // row-interchange maps used by the factorisation: big panel (even),
+                               // sub-panel, big panel (odd)
+    // look-ahead of the FP32 factorisation: the panel chain on la_hi (high priority), the rest of
+    // each trailing update on la_lo; events start, fork, join, done
+    cudaStream_t la_hi = nullptr, la_lo = nullptr;
+    cudaEvent_t la_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // inverted diagonal blocks of L and U (getrs), bs x bs each, n/bs blocks
     void* d_dinvL = nullptr;
     void* d_dinvU = nullptr;
@@ -298,7 +303,7 @@ struct bm_ctx {
 
     // tensor maps (opaque bytes, built on the host)
     alignas(64) unsigned char tm_schur[4][128];
-    alignas(64) unsigned char tm_lu[4][128];
+    alignas(64) unsigned char tm_lu[6][128];  // L21 pack, U12 pack, U12 pack from row NB
     // skinny products: [0,1] [M13; M23] pack, [2,3] B pack of [W1; W2], [4,5] B pack of z3
     alignas(64) unsigned char tm_skinny[6][128];
     bool tm_ok = false;

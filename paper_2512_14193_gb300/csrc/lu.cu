@@ -724,19 +724,32 @@ cudaError_t gemm_any(cudaStream_t s, int m, int n, int k, C32 A, C32 B, C32 C) {
 
 template <class V>
 bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
-    cudaStream_t s = c->stream;
     const int n = c->n;
     const int NB = c->nb;
     const int cl_max = c->panel_cluster;
-    SwapMap* d_map = reinterpret_cast<SwapMap*>(c->d_maps);  // big-panel map
-    SwapMap* d_map2 = d_map + 1;                              // sub-panel map
+    SwapMap* const maps = reinterpret_cast<SwapMap*>(c->d_maps);
+    SwapMap* const d_map2 = maps + 1;  // sub-panel map (register-row panels)
+    // Look-ahead (FP32 with tensor-core trailing updates): after big panel J, the interchanges,
+    // U12 solve and trailing update of the next big panel's columns run first on the high-priority
+    // stream, which then factors that panel while the low-priority stream finishes the rest of the
+    // trailing update; the next block step waits for it.  Profiling keeps the serial order.
+    const bool la = std::is_same<V, C32>::value && tc && !c->prof && n > 2 * NB && c->la_hi != nullptr;
+    cudaStream_t s = la ? c->la_hi : c->stream;
+    cudaStream_t s2 = c->la_lo;
+    cudaEvent_t ev_start = c->la_ev[0], ev_fork = c->la_ev[1], ev_join = c->la_ev[2], ev_done = c->la_ev[3];
+    if (la) {
+        LU_CUDA(cudaEventRecord(ev_start, c->stream));
+        LU_CUDA(cudaStreamWaitEvent(s, ev_start, 0));
+        LU_CUDA(cudaStreamWaitEvent(s2, ev_start, 0));
+    }
     {
         BM_PROF(c, "iota");
         iota_kernel<<<ceil_div(n, 256), 256, 0, s>>>(c->d_perm, n);
         LU_CUDA(cudaGetLastError());
     }
-    for (int J = 0; J < n; J += NB) {
+    for (int J = 0, blk = 0; J < n; J += NB, ++blk) {
         const int jb = std::min(NB, n - J);
+        SwapMap* const d_map = (blk & 1) ? maps + 2 : maps;  // this big panel's map (two in flight)
         for (int j = J; j < J + jb;) {
             PanelShape ps;
             if (!panel_shape<V>(n - j, cl_max, c->panel_lane_col, ps)) {
@@ -744,12 +757,23 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
                 return BM_EINVAL;
             }
             const int ib = std::min(ps.nbp, J + jb - j);
-            {
-                BM_PROF(c, ps.RPW ? "panel_lc_kernel" : "panel_kernel");
+            // the lane-per-column kernel (FP32) also applies the sub-panel's interchanges to the
+            // big panel's other columns and solves L11 against its columns on the right
+            bool fused = false;
+            if constexpr (std::is_same<V, C32>::value) {
+                if (ps.RPW > 0) {
+                    BM_PROF(c, "panel_lc_kernel");
+                    LcParams lp{F, j, n - j, ib, J, jb, c->d_ipiv, c->d_info, c->d_info + 1, d_map, c->d_perm};
+                    LU_CUDA(launch_panel_lc(s, ps, lp));
+                    fused = true;
+                }
+            }
+            if (!fused) {
+                BM_PROF(c, "panel_kernel");
                 LU_CUDA(launch_panel(s, F, ps, j, n - j, ib, c->d_ipiv, c->d_info, J, jb, d_map2, d_map, c->d_perm));
             }
             if (jb > ib) {
-                {
+                if (!fused) {
                     BM_PROF(c, "swap_trsm_kernel (sub-panel)");
                     LU_CUDA(launch_swap_trsm<V>(s, F, d_map2, J, j, j + ib, J + jb, j, ib, nullptr, nullptr, 0, 0));
                 }
@@ -762,27 +786,49 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
             j += ib;
         }
         const bool pack = tc && (J + jb < n);
+        const int mm = n - J - jb;          // trailing rows and columns
+        const int nnext = la ? std::min(NB, mm) : mm;  // trailing columns updated on s
+        // the rest of the previous trailing update (columns this block row touches) is done
+        if (la && blk > 0) LU_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
         {
             BM_PROF(c, "swap_trsm_kernel (block row)");
-            LU_CUDA(launch_swap_trsm<V>(s, F, d_map, 0, J, J + jb, n, J, jb, pack ? c->d_Up_r : nullptr,
-                                        pack ? c->d_Up_i : nullptr, c->ldk_lu, split));
+            // on s: the next big panel's columns (all trailing columns without look-ahead), and the
+            // columns left of this panel unless the rest stream takes them
+            LU_CUDA(launch_swap_trsm<V>(s, F, d_map, 0, la ? 0 : J, J + jb, J + jb + nnext, J, jb,
+                                        pack ? c->d_Up_r : nullptr, pack ? c->d_Up_i : nullptr, c->ldk_lu, split));
         }
-        if (J + jb < n) {
-            const int mm = n - J - jb;
+        if (mm > 0) {
             if (tc) {
                 if constexpr (std::is_same<V, C32>::value) {
-                    dim3 blk(32, 8), grid(ceil_div(jb, 32), ceil_div(mm, 32));
+                    dim3 blk2(32, 8), grid(ceil_div(jb, 32), ceil_div(mm, 32));
                     {
                         BM_PROF(c, "pack_L_kernel");
-                        pack_L_kernel<<<grid, blk, 0, s>>>(F, J + jb, J, mm, jb, split, c->d_Lp_r, c->d_Lp_i,
-                                                           c->ldk_lu);
+                        pack_L_kernel<<<grid, blk2, 0, s>>>(F, J + jb, J, mm, jb, split, c->d_Lp_r, c->d_Lp_i,
+                                                            c->ldk_lu);
                         LU_CUDA(cudaGetLastError());
                     }
-                    int kext = split ? 3 * jb : jb;
+                    const int kext = split ? 3 * jb : jb;
                     C32 Cv = F.sub(J + jb, J + jb);
-                    BM_PROF(c, "cgemm_tc_kernel (trailing update)");
-                    LU_CUDA(gemm_tc(s, c->tm_lu[0], c->tm_lu[1], c->tm_lu[2], c->tm_lu[3], Cv.re, Cv.im, Cv.ld, mm, mm,
-                                    kext, -1.0f, 1.0f, c->d_err));
+                    {
+                        BM_PROF(c, "cgemm_tc_kernel (trailing update)");
+                        LU_CUDA(gemm_tc(s, c->tm_lu[0], c->tm_lu[1], c->tm_lu[2], c->tm_lu[3], Cv.re, Cv.im, Cv.ld, mm,
+                                        nnext, kext, -1.0f, 1.0f, c->d_err));
+                    }
+                    if (la) {
+                        // the rest on s2: interchanges of the columns left of this panel and right of
+                        // the next one, their U12 rows (packed from pack row NB on) and their update
+                        LU_CUDA(cudaEventRecord(ev_fork, s));
+                        LU_CUDA(cudaStreamWaitEvent(s2, ev_fork, 0));
+                        LU_CUDA(launch_swap_trsm<V>(s2, F, d_map, 0, J, J + jb + nnext, n, J, jb,
+                                                    c->d_Up_r + (long)NB * c->ldk_lu, c->d_Up_i + (long)NB * c->ldk_lu,
+                                                    c->ldk_lu, split));
+                        if (mm > nnext) {
+                            C32 Cr = F.sub(J + jb, J + jb + nnext);
+                            LU_CUDA(gemm_tc(s2, c->tm_lu[0], c->tm_lu[1], c->tm_lu[4], c->tm_lu[5], Cr.re, Cr.im, Cr.ld,
+                                            mm, mm - nnext, kext, -1.0f, 1.0f, c->d_err));
+                        }
+                        LU_CUDA(cudaEventRecord(ev_join, s2));
+                    }
                 }
             } else {
                 BM_PROF(c, "cgemm_simt_kernel (trailing update)");
@@ -790,6 +836,7 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
             }
         }
     }
+    if (la) LU_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
     // inverted diagonal blocks for getrs
     const int bs = c->bs_solve;
     if (bs != TI_B || bs != TS_BM) {
@@ -816,6 +863,10 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
                                                                 reinterpret_cast<const CV*>(c->d_dinvU));
             LU_CUDA(cudaGetLastError());
         }
+    }
+    if (la) {  // join the handle's stream
+        LU_CUDA(cudaEventRecord(ev_done, s));
+        LU_CUDA(cudaStreamWaitEvent(c->stream, ev_done, 0));
     }
     return BM_OK;
 }
@@ -928,6 +979,22 @@ bm_status lu_setup(bm_ctx* c, int cluster_cap, int panel_kernel) {
     c->panel_cluster = dev_max;
     if (cluster_cap >= 1 && cluster_cap <= MAX_CLUSTER) c->panel_cluster = std::min(c->panel_cluster, cluster_cap);
     c->panel_lane_col = panel_kernel == 0;
+    // the look-ahead's streams (panel chain at the device's highest priority, the rest of the
+    // trailing updates at its lowest) and events, created once per handle
+    if (c->prec != BM_FP64 && c->la_hi == nullptr) {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->la_hi, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->la_lo, cudaStreamNonBlocking, least) != cudaSuccess) {
+            bm_set_error("lu: cannot create the factorisation's streams");
+            return BM_ECUDA;
+        }
+        for (cudaEvent_t& e : c->la_ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                bm_set_error("lu: cannot create the factorisation's events");
+                return BM_ECUDA;
+            }
+    }
     return BM_OK;
 }
 

@@ -103,6 +103,76 @@ __device__ inline void apply_map_int_warp(const SwapMap* map, int* v) {
 }
 
 // ------------------------------------------------------------------------------------------------
+// helpers of the cluster panel kernels: register-array access by a runtime index (a chain of
+// selects, no local memory), distributed shared memory, bounded mbarrier waits, warp argmax
+// ------------------------------------------------------------------------------------------------
+template <class T, int N>
+__device__ __forceinline__ T row_get(const T (&row)[N], int s) {
+    T v = row[0];
+#pragma unroll
+    for (int r = 1; r < N; ++r)
+        if (r == s) v = row[r];
+    return v;
+}
+template <class T, int N>
+__device__ __forceinline__ void row_set(T (&row)[N], int s, T v) {
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+        if (r == s) row[r] = v;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t remote_addr(uint32_t local, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+// 8 bytes from registers into another CTA's shared memory, completing on that CTA's mbarrier
+__device__ __forceinline__ void push8(uint32_t raddr, uint32_t x, uint32_t y, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "r"(x), "r"(y), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait (2 s by the global timer) for phase `parity` of a local mbarrier, with cluster-scope
+// acquire of the data that completed it; false on a timeout
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok = 0;
+    uint64_t t0 = 0;
+    for (int it = 0;; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it == 0) t0 = gtime();
+        else if (gtime() - t0 > 2000000000ull) return false;
+    }
+}
+// best (value, row) over the warp: the largest value, then the smallest row.  Values are
+// non-negative floats, whose bit patterns order like the values; "no candidate" is (0, INT_MAX).
+__device__ __forceinline__ void warp_best(uint32_t& vbits, uint32_t& idx) {
+    const uint32_t vm = __reduce_max_sync(0xffffffffu, vbits);
+    idx = __reduce_min_sync(0xffffffffu, vbits == vm ? idx : 0xffffffffu);
+    vbits = vm;
+}
+// 1 / a by Smith's scaling, with IEEE reciprocals instead of divisions
+__device__ __forceinline__ float2 cinv_rcp(float2 a) {
+    if (fabsf(a.x) >= fabsf(a.y)) {
+        const float r = a.y * __frcp_rn(a.x), id = __frcp_rn(fmaf(a.y, r, a.x));
+        return make_float2(id, -r * id);
+    }
+    const float r = a.x * __frcp_rn(a.y), id = __frcp_rn(fmaf(a.x, r, a.y));
+    return make_float2(r * id, -id);
+}
+
+// ------------------------------------------------------------------------------------------------
 // panel factorisation
 // ------------------------------------------------------------------------------------------------
 template <class CV, int NBP>
@@ -350,13 +420,15 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
 
 struct PanelShape {
     int CL, R, RPT, nbp;
-    int RPW;  // > 0: lane-per-column kernel with RPW rows per warp (C32), else the register-row kernel
+    int RPW;  // > 0: lane-per-column kernel with RPW register rows per warp (C32), else the register-row kernel
+    int SRW;  // lane-per-column kernel: rows per warp held in shared memory (after the register rows)
 };
 
 // cluster size, rows per CTA, rows per thread and sub-panel width for a panel of m rows.  The
 // lane-per-column kernel (lane_col, C32 only) spreads the rows over as many CTAs as give each about
 // 64 rows (4 per warp: the per-column update shrinks with the rows per warp), up to the cluster
-// limit, and takes up to 256 rows per CTA (16 per warp); taller panels use the register-row kernel.
+// limit; it holds up to 16 rows per warp in registers and, for panels taller than that, 16 more
+// per warp in shared memory (512 rows per CTA).  Taller panels use the register-row kernel.
 template <class V>
 bool panel_shape(int m, int cl_max, bool lane_col, PanelShape& ps) {
     if (std::is_same<V, C32>::value && lane_col) {
@@ -365,7 +437,11 @@ bool panel_shape(int m, int cl_max, bool lane_col, PanelShape& ps) {
         int rpw = 2;
         while (rpw < need) rpw *= 2;
         if (rpw <= 16) {
-            ps = PanelShape{CL, (PANEL_THREADS / 32) * rpw, 0, 32, rpw};
+            ps = PanelShape{CL, (PANEL_THREADS / 32) * rpw, 0, 32, rpw, 0};
+            return true;
+        }
+        if (need <= 32) {
+            ps = PanelShape{CL, (PANEL_THREADS / 32) * 32, 0, 32, 16, 16};
             return true;
         }
     }
@@ -375,9 +451,27 @@ bool panel_shape(int m, int cl_max, bool lane_col, PanelShape& ps) {
     int RPT = ceil_div(R, PANEL_THREADS);
     if (RPT > 4) return false;
     if (RPT == 3) RPT = 4;
-    ps = PanelShape{CL, R, RPT, W / RPT, 0};
+    ps = PanelShape{CL, R, RPT, W / RPT, 0, 0};
     return true;
 }
+
+// Lane-per-column panel of an FP32 sub-panel, rows [j0, j0 + m) x columns [j0, j0 + ib) of its big
+// panel [J, J + jb).  Besides the factorisation (pivots to ipiv) it applies the sub-panel's row
+// interchanges to the other columns of the big panel and solves the unit-lower block against the
+// big panel's columns right of the sub-panel (U12 = L11^{-1} A12), so no separate launch is needed
+// for either.  The last sub-panel of a big panel also writes the big panel's interchange map and
+// applies it to the row order perm.
+struct LcParams {
+    C32 A;
+    int j0, m, ib;
+    int J, jb;
+    int* ipiv;
+    int* info;  // first singular column (1-based) if still 0
+    int* err;   // raised by a timed-out wait
+    SwapMap* map_big;
+    int* perm;
+};
+cudaError_t launch_panel_lc(cudaStream_t s, const PanelShape& ps, const LcParams& p);
 
 cudaError_t launch_panel(cudaStream_t s, C32 A, const PanelShape& ps, int j0, int m, int ib, int* ipiv, int* info,
                          int J, int jb, SwapMap* mi, SwapMap* mb, int* perm);
