@@ -239,6 +239,10 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_lc_kernel(const __grid
     // the cluster barrier that guards the first remote copy is entered now and left after the
     // load, which hides the CTAs' different start times
     asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    // launched as a programmatic dependent: the previous kernel of the stream has finished and its
+    // writes are visible after this wait; the next kernel may start launching (it waits likewise)
+    pdl_wait();
+    pdl_trigger();
 
     // ---- load the CTA's rows: column segments of R rows, coalesced, through shared memory ----
     {
@@ -488,9 +492,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_lc_kernel(const __grid
 
     // ---- the sub-panel's interchanges on the big panel's other columns; L11^{-1} on the right ----
     if (nright > 0) {
-        for (int e = threadIdx.x; e < ib * ib; e += PANEL_THREADS) {
-            const int i = e % ib, k = e / ib;
-            L11s[i][k] = (i > k) ? A.get((long)j0 + i, (long)j0 + k) : zero;
+        for (int e = threadIdx.x; e < 32 * 32; e += PANEL_THREADS) {
+            const int i = e % 32, k = e / 32;
+            L11s[i][k] = (i > k && i < ib) ? A.get((long)j0 + i, (long)j0 + k) : zero;
         }
     }
     __syncthreads();
@@ -504,13 +508,13 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1) panel_lc_kernel(const __grid
         if (lane < cnt) x0 = A.get((long)j0 + ss0, col);
         if (lane + 32 < cnt) x1 = A.get((long)j0 + ss1, col);
         if (right) {  // entries 0 .. ib-1 are rows j0 + lane: x0 -= L11 x below the diagonal
-            for (int k = 0; k + 1 < ib; ++k) {
+            // (L11s is zero on and above the diagonal and beyond ib, so every lane takes every step)
+#pragma unroll
+            for (int k = 0; k < 31; ++k) {
+                const float2 l = L11s[lane][k];
                 const float2 xk = make_float2(__shfl_sync(0xffffffffu, x0.x, k), __shfl_sync(0xffffffffu, x0.y, k));
-                if (lane > k && lane < ib) {
-                    const float2 l = L11s[lane][k];
-                    x0.x -= l.x * xk.x - l.y * xk.y;
-                    x0.y -= l.x * xk.y + l.y * xk.x;
-                }
+                x0.x = fmaf(-l.x, xk.x, fmaf(l.y, xk.y, x0.x));
+                x0.y = fmaf(-l.x, xk.y, fmaf(-l.y, xk.x, x0.y));
             }
         }
         __syncwarp();  // every source is read before any destination is written
@@ -531,13 +535,15 @@ cudaError_t launch_lc_t(cudaStream_t s, const PanelShape& ps, const LcParams& p)
     cfg.blockDim = dim3(PANEL_THREADS, 1, 1);
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = ps.CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
