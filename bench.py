@@ -354,6 +354,8 @@ def roofline_from_profile(prof, N: int, nrhs: int, prec: int, iters: int, peaks:
                                          "8-byte complex read + written"),
         "trsv_g_step_kernel": ("hbm", float(iters) * N * N * 8, hbm, "GB/s",
                                "the FP32 factors (N^2 x 8 bytes) read once per triangular-solve pair"),
+        "trsv_flow_kernel": ("hbm", float(iters) * N * N * 8, hbm, "GB/s",
+                             "the FP32 factors (N^2 x 8 bytes) read once per triangular-solve pair"),
         "cgemm_tc_kernel (skinny, + split-K reduction)": ("hbm", float(iters) * 4 * N * N * 8, hbm, "GB/s",
                                                           "[M31 M32] and [M13; M23] in complex FP32 read once per "
                                                           "correction"),
@@ -391,7 +393,7 @@ def run_ours(args, ws, rank, local):
 
     hm = bm.bm_create(local, stream.cuda_stream)
     ho = bm.bm_create(local, stream.cuda_stream)
-    opts = bm.make_opts(prec)
+    opts = bm.make_opts(prec, eager=args.eager)
     p = w.curve.params4()
 
     def ev():
@@ -784,6 +786,8 @@ def main():
     ap.add_argument("--config5-fp64", action="store_true", help="also time the FP64 mixed path at N=16384")
     ap.add_argument("--quick", action="store_true", help="N=1024 instead of 4096 (smoke-sized)")
     ap.add_argument("--n", type=int, default=0, help="another N for the same star workload (profiling sizes)")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the factor and solve kernels one by one instead of as CUDA graphs (for ncu)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -155,6 +155,8 @@ void free_solve_ws(bm_ctx* c) {
     FREE(c->d_XP);
     FREE(c->d_XQ);
     FREE(c->d_Wdf);
+    FREE(c->d_flow);
+    c->flow_len = 0;
     for (int q = 0; q < 2; ++q) {
         FREE(c->d_dx[q]);
         FREE(c->d_dxe[q]);
@@ -928,6 +930,10 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
         BM_TRY(alloc_t(c, &c->d_XP, (size_t)c->nsys * w * 16));
         BM_TRY(alloc_t(c, &c->d_XQ, (size_t)c->nsys * w * 8));
         BM_TRY(alloc_t(c, &c->d_Wdf, (size_t)4 * c->N * w * 16));
+        // two triangles x (64-row tiles) x (8-column tiles)
+        c->flow_len = 2L * ceil_div(c->n, 64) * ceil_div(w, 8);
+        BM_TRY(alloc_t(c, &c->d_flow, (size_t)(c->flow_len + 1) * sizeof(int)));  // + the timeout word
+        BM_CUDA_TRY(cudaMemsetAsync(c->d_flow, 0, (size_t)(c->flow_len + 1) * sizeof(int), c->stream));
     }
     if (c->prec != BM_FP64) {
         // x digit planes and split-K workspace of the tensor-core residual
@@ -1118,6 +1124,13 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
     if (se != cudaSuccess) {
         bm_set_error(std::string("solve: ") + cudaGetErrorString(se));
         return BM_ECUDA;
+    }
+    if (c->d_flow != nullptr && st == BM_OK) {  // a wait of the persistent triangular solve gave up
+        int tw = 0;
+        if (cudaMemcpy(&tw, c->d_flow + c->flow_len, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && tw != 0) {
+            bm_set_error("solve: a wait of the triangular solve timed out");
+            st = BM_ETIMEOUT;
+        }
     }
     if (info) {
         info->iterations = iters;

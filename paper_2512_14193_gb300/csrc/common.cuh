@@ -274,6 +274,8 @@ struct bm_ctx {
     double2* d_Y64 = nullptr; // FP64 work for the FP64 solve
     double2* d_Y64b = nullptr;
     double2* d_Zw64 = nullptr;  // n x nrhs work buffers of the blocked triangular solves
+    int* d_flow = nullptr;  // readiness flags of the persistent triangular solve (FP32)
+    long flow_len = 0;      // their count
     float* d_Zwr = nullptr;
     float* d_Zwi = nullptr;
     double* d_colred = nullptr;  // per-column reductions (4 x nrhs)

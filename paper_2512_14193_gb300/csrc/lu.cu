@@ -666,6 +666,144 @@ __global__ void __launch_bounds__(256) trsv_diag_kernel(V Y, V Z, int n, int nrh
     }
 }
 
+// Persistent blocked triangular solve in G form (C32): the block steps and the diagonal blocks of
+// one triangle (forward: lower, backward: upper) in a single cooperative launch.  Work item (i, j)
+// is tile row i (64 rows) of column tile j (16 right-hand sides).  It accumulates
+// sum_b G[i, b] Y[b, j] over the tile rows b before i (lower) or after i (upper), each as soon as
+// item (b, j) has published its final rows through the flag ready[b, j]; then it writes
+// Y[i, j] -= that sum (the rows later items read), publishes ready[i, j], and writes
+// Z[i, j] = T_i Y[i, j] with T_i the inverted diagonal block.  CTA q takes items q, q + grid, ...
+// in dependency order, so the earliest unfinished item never waits; with every CTA resident
+// (cooperative launch) no wait can deadlock.  Waits are bounded (1 s by the global timer): a
+// timeout raises *err and the item goes on with what it has.
+constexpr int FL_BN = 8;
+__device__ __forceinline__ void flow_wait(const int* flag, int* err) {
+    if (*reinterpret_cast<volatile int*>(err) != 0) return;  // an earlier wait gave up: no more waiting
+    uint64_t t0 = 0;
+    for (int it = 0;; ++it) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v != 0) return;
+        if (it == 0) t0 = gtime();
+        else if (gtime() - t0 > 1000000000ull) {
+            atomicExch(err, 1);
+            return;
+        }
+    }
+}
+// acc[c] += sum_k M[r, k] V[k, c] for k < kn: M column-major B x B, V row-major [k][BN]
+__device__ __forceinline__ void flow_mac(float2 (&acc)[FL_BN], const float2* M, const float2* V, int r, int kn) {
+    for (int k = 0; k < kn; ++k) {
+        const float2 g = M[k * TS_BM + r];
+        const float4* v4 = reinterpret_cast<const float4*>(V + k * FL_BN);
+#pragma unroll
+        for (int c2 = 0; c2 < FL_BN / 2; ++c2) {
+            const float4 y = v4[c2];
+            cfma(acc[2 * c2], g, make_float2(y.x, y.y));
+            cfma(acc[2 * c2 + 1], g, make_float2(y.z, y.w));
+        }
+    }
+}
+template <bool UPPER>
+__global__ void __launch_bounds__(256) trsv_flow_kernel(C32 F, C32 Y, C32 Z, int n, int nrhs,
+                                                        const float2* __restrict__ Tinv, int* ready, int* err) {
+    constexpr int B = TS_BM, BN = FL_BN, RS = 256 / B;  // RS k-slices of the 64 rows
+    extern __shared__ __align__(16) unsigned char sm[];
+    float2* Gs = reinterpret_cast<float2*>(sm);     // [B][B] column-major: G[i, b], then T_i
+    float2* Yb = Gs + B * B;                        // [B][BN] row-major: Y[b, j], then Y[i, j]
+    float2* Red = Yb + B * BN;                      // [RS][B][BN] partial sums of the k-slices
+    const int t = threadIdx.x;
+    const int nblk = (n + B - 1) / B, ct = (nrhs + BN - 1) / BN;
+    const int items = nblk * ct;
+    const int r = t % B, ks = t / B;  // this thread: row r, k in [ks B / RS, (ks + 1) B / RS)
+    const int kb0 = ks * (B / RS);
+    pdl_wait();
+    pdl_trigger();
+    for (int q = blockIdx.x; q < items; q += gridDim.x) {
+        __syncthreads();  // the previous item is done with the shared buffers
+        const int i = UPPER ? nblk - 1 - q / ct : q / ct, j = q % ct;
+        const long r0 = (long)i * B;
+        const int tm = (int)min((long)B, n - r0);
+        const int j0 = j * BN, nc = min(BN, nrhs - j0);
+        // this item's own right-hand-side rows (written only by it)
+        float2 yown[BN];
+#pragma unroll
+        for (int c = 0; c < BN; ++c)
+            yown[c] = (ks == 0 && r < tm && c < nc) ? Y.get(r0 + r, (long)j0 + c) : make_float2(0.f, 0.f);
+        float2 acc[BN];
+#pragma unroll
+        for (int c = 0; c < BN; ++c) acc[c] = make_float2(0.f, 0.f);
+        const int nsteps = UPPER ? nblk - 1 - i : i;
+        for (int st = 0; st < nsteps; ++st) {
+            const int b = UPPER ? nblk - 1 - st : st;
+            const long c0 = (long)b * B;
+            const int rb = (int)min((long)B, n - c0);
+            __syncthreads();  // the buffers are free
+            load_tile<B, B>(Gs, F, r0, c0, tm, rb);
+            if (t == 0) flow_wait(ready + b * ct + j, err);
+            __syncthreads();  // item (b, j) is final
+#pragma unroll
+            for (int m = 0; m < B * BN / 256; ++m) {
+                const int e = t + 256 * m;
+                const int k = e / BN, c = e % BN;
+                float2 v = make_float2(0.f, 0.f);
+                if (k < rb && c < nc) {
+                    const long off = (c0 + k) + (long)(j0 + c) * Y.ld;
+                    v = make_float2(__ldcg(Y.re + off), __ldcg(Y.im + off));
+                }
+                Yb[e] = v;
+            }
+            __syncthreads();
+            flow_mac(acc, Gs + kb0 * B, Yb + kb0 * BN, r, min(B / RS, max(rb - kb0, 0)));
+        }
+        // combine the k-slices: the final rows of Y[i, j], published for the later items
+#pragma unroll
+        for (int c = 0; c < BN; ++c) Red[(ks * B + r) * BN + c] = acc[c];
+        __syncthreads();
+        if (ks == 0) {
+#pragma unroll
+            for (int c = 0; c < BN; ++c) {
+                float2 sum = acc[c];
+                for (int q2 = 1; q2 < RS; ++q2) {
+                    const float2 p2 = Red[(q2 * B + r) * BN + c];
+                    sum.x += p2.x;
+                    sum.y += p2.y;
+                }
+                yown[c] = make_float2(yown[c].x - sum.x, yown[c].y - sum.y);
+                if (r < tm && c < nc) Y.set(r0 + r, (long)j0 + c, yown[c]);
+                Yb[r * BN + c] = yown[c];
+            }
+        }
+        // the CTA barrier orders every thread's rows before thread 0's release (cumulative at gpu
+        // scope), so a reader that acquires the flag sees them
+        __syncthreads();
+        if (t == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(ready + i * ct + j), "r"(1) : "memory");
+        // Z[i, j] = T_i Y[i, j] (rows r, k-slice ks; the slices summed as above)
+        load_block<B>(Gs, Tinv + (long)i * B * B, tm);
+        __syncthreads();
+        float2 z[BN];
+#pragma unroll
+        for (int c = 0; c < BN; ++c) z[c] = make_float2(0.f, 0.f);
+        flow_mac(z, Gs + kb0 * B, Yb + kb0 * BN, r, min(B / RS, max(tm - kb0, 0)));
+        __syncthreads();  // every slice has read Yb and Red is free
+#pragma unroll
+        for (int c = 0; c < BN; ++c) Red[(ks * B + r) * BN + c] = z[c];
+        __syncthreads();
+        if (ks == 0 && r < tm) {
+#pragma unroll
+            for (int c = 0; c < BN; ++c) {
+                float2 sum = z[c];
+                for (int q2 = 1; q2 < RS; ++q2) {
+                    const float2 p2 = Red[(q2 * B + r) * BN + c];
+                    sum.x += p2.x;
+                    sum.y += p2.y;
+                }
+                if (c < nc) Z.set(r0 + r, (long)j0 + c, sum);
+            }
+        }
+    }
+}
+
 __global__ void gather_rows_z64_kernel(const int* __restrict__ perm, int n, int nrhs, const double2* __restrict__ B,
                                        long ldb, double2* __restrict__ Y, long ldy) {
     long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -903,6 +1041,45 @@ cudaError_t launch_trsv_diag(cudaStream_t s, V Y, V Z, int n, int nrhs, const ty
     return launch_pdl(kern, grid, dim3(256), smem, s, Y, Z, n, nrhs, Tinv);
 }
 
+// one cooperative launch of the persistent triangular solve: as many CTAs as the items, at most
+// the number the device keeps resident (queried once per process and device)
+template <bool UPPER>
+cudaError_t launch_trsv_flow(cudaStream_t s, C32 F, C32 Y, C32 Z, int n, int nrhs, const float2* T, int* ready,
+                             int* err, int items, int num_sms) {
+    auto kern = trsv_flow_kernel<UPPER>;
+    const int smem = (TS_BM * TS_BM + FL_BN * TS_BM + 4 * TS_BM * FL_BN) * (int)sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    static std::mutex mu;
+    static std::map<int, int> per_sm_cache;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = per_sm_cache.find(dev);
+        if (it == per_sm_cache.end()) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+            if (e != cudaSuccess) return e;
+            it = per_sm_cache.emplace(dev, per_sm).first;
+        }
+        per_sm = it->second;
+    }
+    const int grid = std::max(1, std::min(items, std::max(per_sm, 1) * std::max(num_sms, 1)));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, F, Y, Z, n, nrhs, T, ready, err);
+}
+
 // Solve L U X = Y in place (Y holds P B); Zw is an n x nrhs work buffer.
 template <class V>
 bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* dinvL, const typename V::cv* dinvU) {
@@ -915,6 +1092,17 @@ bm_status getrs_t(bm_ctx* c, V F, V Y, V Zw, int nrhs, const typename V::cv* din
     const long widest16 = (long)ceil_div(std::max(n - bs, 1), TS_BM) * ceil_div(nrhs, 16);
     const bool narrow = nrhs <= 16 || widest16 <= (long)(1.1 * 2 * std::max(c->num_sms, 1));
     if constexpr (std::is_same<V, C32>::value) {  // factors in G form
+        const int ct = ceil_div(nrhs, FL_BN), items = nblk * ct;
+        if (bs == TS_BM && c->d_flow != nullptr && 2L * items <= c->flow_len) {
+            // one persistent launch per triangle (block steps and diagonal blocks)
+            BM_PROF(c, "trsv_flow_kernel");
+            int* const ferr = c->d_flow + c->flow_len;  // the solve's timeout word
+            LU_CUDA(cudaMemsetAsync(c->d_flow, 0, (size_t)2 * items * sizeof(int), s));
+            LU_CUDA(cudaMemsetAsync(ferr, 0, sizeof(int), s));
+            LU_CUDA(launch_trsv_flow<false>(s, F, Y, Zw, n, nrhs, dinvL, c->d_flow, ferr, items, c->num_sms));
+            LU_CUDA(launch_trsv_flow<true>(s, F, Zw, Y, n, nrhs, dinvU, c->d_flow + items, ferr, items, c->num_sms));
+            return BM_OK;
+        }
         auto gstep = [&](V Yv, int r0, int rb, int rest0, int nrest) {
             return narrow ? launch_trsv_g_step<V, 16>(s, F, Yv, r0, rb, rest0, nrest, nrhs)
                           : launch_trsv_g_step<V, 32>(s, F, Yv, r0, rb, rest0, nrest, nrhs);

@@ -229,7 +229,7 @@ def test_profile_reports_every_kernel_and_the_same_solution(bmlib, handle):
     assert np.array_equal(X1, X2)
     names = {k for k, _, _ in prof}
     for k in ("cgemm_tc_kernel (Schur complement)", "panel_lc_kernel", "cgemm_tc_kernel (trailing update)",
-              "trsv_g_step_kernel", "resid_tc_kernel (+ split-K reduction)", "eta_kernel"):
+              "trsv_flow_kernel", "resid_tc_kernel (+ split-K reduction)", "eta_kernel"):
         assert k in names, k
     assert all(l >= 1 and ms > 0 for _, l, ms in prof)
     assert [ms for _, _, ms in prof] == sorted([ms for _, _, ms in prof], reverse=True)
