@@ -15,6 +15,11 @@
 //       H_nu(z) ~ sqrt(2/(pi z)) e^{i(z - nu pi/2 - pi/4)} sum_k i^k a_k(nu) / z^k,
 //       a_k(nu) = prod_{j=1..k} (4nu^2 - (2j-1)^2) / (k! 8^k),
 //    summed until the terms fall below 1e-17 (at most 40 terms; about 20 at |z| = 20).
+// GB300 runs FP64 at 1/64 of its FP32 rate, and the series terms fall fast: past the first six
+// terms of either series (asymptotic: |a_7 / z^7| < 1e-8 for |z| >= 20; Taylor: |delta| <= 0.177)
+// the rest of the sum is below 1e-8 of it, so those terms are formed and summed in FP32 (their
+// rounding errors stay near 1e-15 of the result) and added to the FP64 sum once.  The leading
+// terms, the recurrence's starting values, exp, sincos and the roots stay FP64.
 #pragma once
 #include "common.cuh"
 
@@ -25,6 +30,9 @@ constexpr double R_ASYM = 20.0;
 constexpr double EULER_GAMMA = 0.57721566490153286060651209008240243;
 constexpr double TWO_OVER_PI = 0.63661977236758134307553505349005745;
 constexpr double ONE_OVER_PI = 0.31830988618379067153776752674502872;
+
+__device__ __forceinline__ float2 f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 fscale(float2 v, float s) { return make_float2(v.x * s, v.y * s); }
 
 __device__ __forceinline__ double2 clog(double2 z) {
     return make_double2(log(hypot(z.x, z.y)), atan2(z.y, z.x));
@@ -87,7 +95,9 @@ __device__ __forceinline__ void taylor(double2 z, const HankelTable& T, double2&
     double2 s0 = cadd(a0, cmul(ak1, d));     // H0 partial sum
     double2 s1 = ak1;                         // H0' partial sum
     double2 dk = d;                           // d^(k+1)
-    for (int k = 0; k < 40; ++k) {
+    constexpr int K64 = 6;                    // terms a_2 .. a_7 in FP64, the rest in FP32
+    bool done = false;
+    for (int k = 0; k < K64; ++k) {
         double dk_ = (double)k;
         // bracket = z0 (k+1)(2k+1) a_{k+1} + (k^2 + z0^2) a_k + 2 z0 a_{k-1} + a_{k-2}
         double2 br = cscale(cmul(z0, ak1), (dk_ + 1.0) * (2.0 * dk_ + 1.0));
@@ -104,7 +114,37 @@ __device__ __forceinline__ void taylor(double2 z, const HankelTable& T, double2&
         am1 = ak;
         ak = ak1;
         ak1 = an;
-        if (cnorm1(t0) <= 1e-17 * cnorm1(s0) && cnorm1(t1) <= 1e-17 * cnorm1(s1)) break;
+        if (cnorm1(t0) <= 1e-17 * cnorm1(s0) && cnorm1(t1) <= 1e-17 * cnorm1(s1)) {
+            done = true;
+            break;
+        }
+    }
+    if (!done) {
+        // the same recurrence and sums in FP32 from a_8 on
+        const float2 fz0 = f2(z0), fd = f2(d), fiz2 = f2(iz2), fz0sq = f2(z0sq);
+        float2 fdk = f2(dk), fm2 = f2(am2), fm1 = f2(am1), fk = f2(ak), fk1 = f2(ak1);
+        float2 f0 = make_float2(0.f, 0.f), f1 = f0;
+        const float n0 = 1e-17f * (float)cnorm1(s0), n1 = 1e-17f * (float)cnorm1(s1);
+        for (int k = K64; k < 40; ++k) {
+            const float kf = (float)k;
+            float2 br = fscale(cmul(fz0, fk1), (kf + 1.f) * (2.f * kf + 1.f));
+            br = cadd(br, cmul(make_float2(fz0sq.x + kf * kf, fz0sq.y), fk));
+            br = cadd(br, fscale(cmul(fz0, fm1), 2.f));
+            br = cadd(br, fm2);
+            const float2 an = fscale(cmul(br, fiz2), -1.f / ((kf + 1.f) * (kf + 2.f)));
+            const float2 t1 = fscale(cmul(an, fdk), kf + 2.f);
+            fdk = cmul(fdk, fd);
+            const float2 t0 = cmul(an, fdk);
+            f0 = cadd(f0, t0);
+            f1 = cadd(f1, t1);
+            fm2 = fm1;
+            fm1 = fk;
+            fk = fk1;
+            fk1 = an;
+            if (cnorm1(t0) <= n0 && cnorm1(t1) <= n1) break;
+        }
+        s0 = cadd(s0, make_double2(f0.x, f0.y));
+        s1 = cadd(s1, make_double2(f1.x, f1.y));
     }
     h0 = s0;
     h1 = cneg(s1);
@@ -113,13 +153,33 @@ __device__ __forceinline__ void taylor(double2 z, const HankelTable& T, double2&
 __device__ __forceinline__ void asym(double2 z, double2& h0, double2& h1) {
     double2 w = cmuli(cinv(z));  // i/z
     double2 t0 = make_double2(1.0, 0.0), t1 = t0, s0 = t0, s1 = t0;
-    for (int k = 1; k < 40; ++k) {
+    constexpr int K64 = 6;  // terms 1 .. 6 in FP64, the rest in FP32
+    bool done = false;
+    for (int k = 1; k <= K64; ++k) {
         double o = (double)(2 * k - 1);
         t0 = cscale(cmul(t0, w), (0.0 - o * o) / (8.0 * k));
         t1 = cscale(cmul(t1, w), (4.0 - o * o) / (8.0 * k));
         s0 = cadd(s0, t0);
         s1 = cadd(s1, t1);
-        if (cnorm1(t0) <= 1e-17 * cnorm1(s0) && cnorm1(t1) <= 1e-17 * cnorm1(s1)) break;
+        if (cnorm1(t0) <= 1e-17 * cnorm1(s0) && cnorm1(t1) <= 1e-17 * cnorm1(s1)) {
+            done = true;
+            break;
+        }
+    }
+    if (!done) {
+        const float2 fw = f2(w);
+        float2 ft0 = f2(t0), ft1 = f2(t1), f0 = make_float2(0.f, 0.f), f1 = f0;
+        const float n0 = 1e-17f * (float)cnorm1(s0), n1 = 1e-17f * (float)cnorm1(s1);
+        for (int k = K64 + 1; k < 40; ++k) {
+            const float o = (float)(2 * k - 1);
+            ft0 = fscale(cmul(ft0, fw), (0.f - o * o) / (8.f * (float)k));
+            ft1 = fscale(cmul(ft1, fw), (4.f - o * o) / (8.f * (float)k));
+            f0 = cadd(f0, ft0);
+            f1 = cadd(f1, ft1);
+            if (cnorm1(ft0) <= n0 && cnorm1(ft1) <= n1) break;
+        }
+        s0 = cadd(s0, make_double2(f0.x, f0.y));
+        s1 = cadd(s1, make_double2(f1.x, f1.y));
     }
     // c = sqrt(2/(pi z)) * exp(i (z - pi/4)); the -pi/4 is applied as the exact rotation
     // (1 - i)/sqrt(2) after sincos(Re z): subtracting pi/4 from a large Re z in FP64 would lose
