@@ -705,13 +705,14 @@ __device__ __forceinline__ void flow_mac(float2 (&acc)[FL_BN], const float2* M, 
     }
 }
 template <bool UPPER>
-__global__ void __launch_bounds__(256) trsv_flow_kernel(C32 F, C32 Y, C32 Z, int n, int nrhs,
-                                                        const float2* __restrict__ Tinv, int* ready, int* err) {
+__global__ void __launch_bounds__(256, 4) trsv_flow_kernel(C32 F, C32 Y, C32 Z, int n, int nrhs,
+                                                           const float2* __restrict__ Tinv, int* ready, int* err) {
     constexpr int B = TS_BM, BN = FL_BN, RS = 256 / B;  // RS k-slices of the 64 rows
     extern __shared__ __align__(16) unsigned char sm[];
     float2* Gs = reinterpret_cast<float2*>(sm);     // [B][B] column-major: G[i, b], then T_i
+    float2* Red = Gs;                               // [RS][B][BN] partial sums of the k-slices (over Gs)
     float2* Yb = Gs + B * B;                        // [B][BN] row-major: Y[b, j], then Y[i, j]
-    float2* Red = Yb + B * BN;                      // [RS][B][BN] partial sums of the k-slices
+    float2* Yo = Yb + B * BN;                       // [B][BN] this item's own right-hand-side rows
     const int t = threadIdx.x;
     const int nblk = (n + B - 1) / B, ct = (nrhs + BN - 1) / BN;
     const int items = nblk * ct;
@@ -725,11 +726,13 @@ __global__ void __launch_bounds__(256) trsv_flow_kernel(C32 F, C32 Y, C32 Z, int
         const long r0 = (long)i * B;
         const int tm = (int)min((long)B, n - r0);
         const int j0 = j * BN, nc = min(BN, nrhs - j0);
-        // this item's own right-hand-side rows (written only by it)
-        float2 yown[BN];
+        // this item's own right-hand-side rows (written only by it), fetched early
 #pragma unroll
-        for (int c = 0; c < BN; ++c)
-            yown[c] = (ks == 0 && r < tm && c < nc) ? Y.get(r0 + r, (long)j0 + c) : make_float2(0.f, 0.f);
+        for (int m = 0; m < B * BN / 256; ++m) {
+            const int e = t + 256 * m;
+            const int k = e / BN, c = e % BN;
+            Yo[e] = (k < tm && c < nc) ? Y.get(r0 + k, (long)j0 + c) : make_float2(0.f, 0.f);
+        }
         float2 acc[BN];
 #pragma unroll
         for (int c = 0; c < BN; ++c) acc[c] = make_float2(0.f, 0.f);
@@ -757,21 +760,22 @@ __global__ void __launch_bounds__(256) trsv_flow_kernel(C32 F, C32 Y, C32 Z, int
             flow_mac(acc, Gs + kb0 * B, Yb + kb0 * BN, r, min(B / RS, max(rb - kb0, 0)));
         }
         // combine the k-slices: the final rows of Y[i, j], published for the later items
+        __syncthreads();  // Gs is free: Red lies over it
 #pragma unroll
         for (int c = 0; c < BN; ++c) Red[(ks * B + r) * BN + c] = acc[c];
         __syncthreads();
         if (ks == 0) {
 #pragma unroll
             for (int c = 0; c < BN; ++c) {
-                float2 sum = acc[c];
-                for (int q2 = 1; q2 < RS; ++q2) {
+                float2 y = Yo[r * BN + c];
+#pragma unroll
+                for (int q2 = 0; q2 < RS; ++q2) {
                     const float2 p2 = Red[(q2 * B + r) * BN + c];
-                    sum.x += p2.x;
-                    sum.y += p2.y;
+                    y.x -= p2.x;
+                    y.y -= p2.y;
                 }
-                yown[c] = make_float2(yown[c].x - sum.x, yown[c].y - sum.y);
-                if (r < tm && c < nc) Y.set(r0 + r, (long)j0 + c, yown[c]);
-                Yb[r * BN + c] = yown[c];
+                if (r < tm && c < nc) Y.set(r0 + r, (long)j0 + c, y);
+                Yb[r * BN + c] = y;
             }
         }
         // the CTA barrier orders every thread's rows before thread 0's release (cumulative at gpu
@@ -785,15 +789,16 @@ __global__ void __launch_bounds__(256) trsv_flow_kernel(C32 F, C32 Y, C32 Z, int
 #pragma unroll
         for (int c = 0; c < BN; ++c) z[c] = make_float2(0.f, 0.f);
         flow_mac(z, Gs + kb0 * B, Yb + kb0 * BN, r, min(B / RS, max(tm - kb0, 0)));
-        __syncthreads();  // every slice has read Yb and Red is free
+        __syncthreads();  // every slice has read Gs: Red may overwrite it
 #pragma unroll
         for (int c = 0; c < BN; ++c) Red[(ks * B + r) * BN + c] = z[c];
         __syncthreads();
         if (ks == 0 && r < tm) {
 #pragma unroll
             for (int c = 0; c < BN; ++c) {
-                float2 sum = z[c];
-                for (int q2 = 1; q2 < RS; ++q2) {
+                float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q2 = 0; q2 < RS; ++q2) {
                     const float2 p2 = Red[(q2 * B + r) * BN + c];
                     sum.x += p2.x;
                     sum.y += p2.y;
@@ -1047,7 +1052,7 @@ template <bool UPPER>
 cudaError_t launch_trsv_flow(cudaStream_t s, C32 F, C32 Y, C32 Z, int n, int nrhs, const float2* T, int* ready,
                              int* err, int items, int num_sms) {
     auto kern = trsv_flow_kernel<UPPER>;
-    const int smem = (TS_BM * TS_BM + FL_BN * TS_BM + 4 * TS_BM * FL_BN) * (int)sizeof(float2);
+    const int smem = (TS_BM * TS_BM + 2 * FL_BN * TS_BM) * (int)sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     static std::mutex mu;
