@@ -270,18 +270,34 @@ __global__ void __launch_bounds__(AT* AY) assemble_batch_kernel(const AsmArgs* _
 __device__ __forceinline__ void atomic_max_pos(double* p, double v) {
     atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(v));
 }
-__global__ void rownorm_kernel(const double2* __restrict__ A, long ld, int m, int ncols, double add, double* out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+// max over rows of (add + sum_j |A(i, j)|) into *out (an infinity-norm term of the backward error).
+// CTA: 32 consecutive rows (lane = row, so every load instruction reads 32 consecutive entries),
+// its 8 warps taking every 8th column; the modulus is sqrt in FP32 of the FP64 sum of squares (a
+// relative 1e-7, ample for a norm that only scales the backward error), the sums in FP64.
+__global__ void __launch_bounds__(256) rownorm_kernel(const double2* __restrict__ A, long ld, int m, int ncols,
+                                                      double add, double* out) {
+    __shared__ double part[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
     double s = 0.0;
     if (i < m) {
-        s = add;
-        for (int j = 0; j < ncols; ++j) {
-            double2 v = A[i + (long)j * ld];
-            s += hypot(v.x, v.y);
+        for (int j = warp; j < ncols; j += 8) {
+            const double2 v = A[i + (long)j * ld];
+            s += (double)sqrtf((float)fma(v.x, v.x, v.y * v.y));
         }
     }
-    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
-    if ((threadIdx.x & 31) == 0 && s > 0) atomic_max_pos(out, s);
+    part[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+        double t = 0.0;
+        if (i < m) {
+            t = add;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) t += part[w][lane];
+        }
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (lane == 0 && t > 0) atomic_max_pos(out, t);
+    }
 }
 
 __global__ void plane_wave_kernel(const double* __restrict__ g, int N, double2 k0, double2 beta,
@@ -768,10 +784,10 @@ cudaError_t launch_normA(cudaStream_t s, const bm_ctx* c) {
     cudaError_t e = cudaMemsetAsync(c->d_normA, 0, sizeof(double), s);
     if (e != cudaSuccess) return e;
     if (c->form == BM_MIXED) {
-        rownorm_kernel<<<ceil_div(2 * c->N, 256), 256, 0, s>>>(c->d_Mtop, c->ldtop, 2 * c->N, c->N, 1.0, c->d_normA);
-        rownorm_kernel<<<ceil_div(c->N, 256), 256, 0, s>>>(c->d_Mbot, c->ldbot, c->N, 2 * c->N, 0.0, c->d_normA);
+        rownorm_kernel<<<ceil_div(2 * c->N, 32), 256, 0, s>>>(c->d_Mtop, c->ldtop, 2 * c->N, c->N, 1.0, c->d_normA);
+        rownorm_kernel<<<ceil_div(c->N, 32), 256, 0, s>>>(c->d_Mbot, c->ldbot, c->N, 2 * c->N, 0.0, c->d_normA);
     } else {
-        rownorm_kernel<<<ceil_div(2 * c->N, 256), 256, 0, s>>>(c->d_A, c->ldA, 2 * c->N, 2 * c->N, 0.0, c->d_normA);
+        rownorm_kernel<<<ceil_div(2 * c->N, 32), 256, 0, s>>>(c->d_A, c->ldA, 2 * c->N, 2 * c->N, 0.0, c->d_normA);
     }
     return cudaGetLastError();
 }
