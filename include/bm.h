@@ -125,8 +125,11 @@ typedef struct {
  *  test_wait_timeout : test hook for the device-wait error path.  1 makes every tensor-core product
  *                      wait on a barrier that nothing completes; the wait gives up after about 1 ms,
  *                      the product skips its output and bm_factor returns BM_ETIMEOUT (the FP64
- *                      precision, which has no tensor-core product, is unaffected).  Nothing is left
- *                      running on the device, and the handle stays usable after a new bm_assemble. */
+ *                      precision, which has no tensor-core product, is unaffected).  2 makes one wait
+ *                      of the FP32 triangular solve wait on a flag that nothing sets; it gives up
+ *                      after about 1 s, the rest of that solve stops waiting, and bm_solve returns
+ *                      BM_ETIMEOUT.  Nothing is left running on the device, and the handle stays
+ *                      usable after a new bm_assemble.  Other values: BM_EINVAL. */
 typedef struct {
     double eps0;
     bm_c64 eps1;

@@ -217,13 +217,13 @@ def bm_destroy(h) -> None:
 
 def make_opts(prec: int = BM_FP64, eps0: float = 1.0, eps1=None, beta=None, refine_tol: float = 1e-9,
               refine_maxit: int = 30, nb: int = 0, residual: int = 0, zeta_p: int = 0, eager: bool = False,
-              panel_cluster_max: int = 0, panel_kernel: int = 0, test_wait_timeout: bool = False) -> bm_opts:
+              panel_cluster_max: int = 0, panel_kernel: int = 0, test_wait_timeout: int = 0) -> bm_opts:
     o = bm_opts()
     o.zeta_p = int(zeta_p)
     o.eager = int(bool(eager))
     o.panel_cluster_max = int(panel_cluster_max)
     o.panel_kernel = int(panel_kernel)
-    o.test_wait_timeout = int(bool(test_wait_timeout))
+    o.test_wait_timeout = int(test_wait_timeout)
     o.eps0 = float(eps0)
     o.prec = int(prec)
     o.refine_tol = float(refine_tol)

@@ -467,9 +467,9 @@ bm_status assemble_impl(bm_ctx* c, const bm_curve* curve, int N, bm_c64 k_out, b
     const int cl_cap = opts ? opts->panel_cluster_max : 0;
     const int pkern = opts ? opts->panel_kernel : 0;
     const bool eager = opts && opts->eager != 0;
-    const int test_wait = (opts && opts->test_wait_timeout) ? 1 : 0;
-    if (cl_cap < 0 || cl_cap > 16 || pkern < 0 || pkern > 1) {
-        bm_set_error("panel_cluster_max must be in [0, 16] and panel_kernel 0 or 1");
+    const int test_wait = opts ? opts->test_wait_timeout : 0;
+    if (cl_cap < 0 || cl_cap > 16 || pkern < 0 || pkern > 1 || test_wait < 0 || test_wait > 2) {
+        bm_set_error("panel_cluster_max must be in [0, 16], panel_kernel 0 or 1 and test_wait_timeout 0, 1 or 2");
         return BM_EINVAL;
     }
     const int zeta_p = opts ? opts->zeta_p : 0;
@@ -721,7 +721,8 @@ bm_status assemble_post(bm_ctx* c, bool run_assembly_kernel, bool wait) {
     BM_TRY(lu_setup(c, c->opt_cluster_cap, c->opt_panel_kernel));
     // test hook read by the tensor-core products (d_err[1], any nonzero value sets it); a memset keeps
     // the stream asynchronous (a copy from pageable memory would wait for the kernels above)
-    BM_CUDA_TRY(cudaMemsetAsync(c->d_info + 2, c->opt_test_wait ? 1 : 0, sizeof(int), c->stream));
+    BM_CUDA_TRY(cudaMemsetAsync(c->d_info + 2, c->opt_test_wait == 1 ? 1 : 0, sizeof(int), c->stream));
+    BM_CUDA_TRY(cudaMemsetAsync(c->d_info + 3, c->opt_test_wait == 2 ? 1 : 0, sizeof(int), c->stream));
     if (wait) BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (c32) {
         const bool split = prec == BM_CF32_3XTF32_IR;
@@ -932,7 +933,7 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
         BM_TRY(alloc_t(c, &c->d_Wdf, (size_t)4 * c->N * w * 16));
         // two triangles x (64-row tiles) x (8-column tiles)
         c->flow_len = 2L * ceil_div(c->n, 64) * ceil_div(w, 8);
-        BM_TRY(alloc_t(c, &c->d_flow, (size_t)(c->flow_len + 1) * sizeof(int)));  // + the timeout word
+        BM_TRY(alloc_t(c, &c->d_flow, (size_t)(c->flow_len + 1) * sizeof(int)));  // + a flag never set (test hook)
         BM_CUDA_TRY(cudaMemsetAsync(c->d_flow, 0, (size_t)(c->flow_len + 1) * sizeof(int), c->stream));
     }
     if (c->prec != BM_FP64) {
@@ -996,7 +997,7 @@ bm_status read_eta(bm_ctx* c, double* eta, bool* nonfinite) {
     BM_CUDA_TRY(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     BM_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (herr != 0) {
-        bm_set_error("tensor-core GEMM: a bounded wait timed out");
+        bm_set_error("a bounded device wait timed out (tensor-core product or triangular solve)");
         return BM_ETIMEOUT;
     }
     *eta = h[0];
@@ -1124,13 +1125,6 @@ extern "C" bm_status bm_solve(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_
     if (se != cudaSuccess) {
         bm_set_error(std::string("solve: ") + cudaGetErrorString(se));
         return BM_ECUDA;
-    }
-    if (c->d_flow != nullptr && st == BM_OK) {  // a wait of the persistent triangular solve gave up
-        int tw = 0;
-        if (cudaMemcpy(&tw, c->d_flow + c->flow_len, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && tw != 0) {
-            bm_set_error("solve: a wait of the triangular solve timed out");
-            st = BM_ETIMEOUT;
-        }
     }
     if (info) {
         info->iterations = iters;

@@ -1,6 +1,8 @@
 """GPU-side error behaviour of the C ABI: call order, invalid arguments, non-finite input and
 HBM-budget admission.  None of these faults the GPU: every failure is detected on the host or
 by a device reduction and returned as a status."""
+import time
+
 import numpy as np
 import pytest
 
@@ -130,6 +132,35 @@ def test_device_wait_timeout_is_reported_and_the_device_stays_usable(bmlib, form
             finally:
                 if hh is None:
                     bmlib.bm_destroy(g)
+    finally:
+        bmlib.bm_destroy(h)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("form", [0, 1])
+def test_triangular_solve_wait_timeout_is_reported(bmlib, form):
+    # Hook 2: one wait of the persistent triangular solve is on a flag nothing sets; it gives up
+    # after ~1 s, the rest of that launch stops waiting, and bm_solve reports BM_ETIMEOUT at its
+    # next read-back instead of iterating.  The handle then factors and solves correctly again.
+    curve, N = W.ellipse(1.0, 0.6), 300
+    nsys = 3 * N if form == 0 else 2 * N
+    h = bmlib.bm_create(0)
+    try:
+        bmlib.bm_assemble(h, curve.kind, curve.params4(), N, 5.0, 7.5, form,
+                          bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR, test_wait_timeout=2))
+        assert bmlib.bm_factor(h) == 0
+        B = np.zeros((nsys, 2), dtype=np.complex128, order="F")
+        bmlib.bm_rhs_plane_wave(h, [0.0, 1.0], B)
+        X = np.zeros_like(B, order="F")
+        t0 = time.time()
+        with pytest.raises(bmlib.BMError) as e:
+            bmlib.bm_solve(h, B, X)
+        assert e.value.status == bmlib.BM_ETIMEOUT
+        assert time.time() - t0 < 20.0
+        bmlib.bm_assemble(h, curve.kind, curve.params4(), N, 5.0, 7.5, form,
+                          bmlib.make_opts(bmlib.BM_CF32_3XTF32_IR))
+        assert bmlib.bm_factor(h) == 0
+        assert bmlib.bm_solve(h, B, X).backward_error <= 1e-9
     finally:
         bmlib.bm_destroy(h)
 
