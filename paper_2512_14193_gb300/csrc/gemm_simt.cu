@@ -14,6 +14,8 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+#include <type_traits>
+
 namespace {
 
 constexpr int BK = 16;
@@ -142,6 +144,21 @@ cudaError_t launch_impl(cudaStream_t s, int m, int n, int k, VA A, VB B, VC C, R
         if ((long)ceil_div(m, 64) >= 2 * 152)
             return go(cgemm_simt_kernel<VA, VB, VC, R, AT, 64, 80>, dim3(ceil_div(m, 64), 1));
         return go(cgemm_simt_kernel<VA, VB, VC, R, AT, 32, 80>, dim3(ceil_div(m, 32), 1));
+    }
+    // FP64 products too small to fill the GPU with 64-row tiles (the FP64 pipe gives each SM only
+    // ~8 GFLOP/s, so idle SMs cost directly): 32 x 16 tiles
+    if constexpr (std::is_same<R, double>::value) {
+        static int sms = 0;
+        if (sms == 0) {
+            int dev = 0, v = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess &&
+                cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+                sms = v;
+            else
+                sms = 1;
+        }
+        if ((long)ceil_div(m, 64) * ceil_div(n, 64) < sms)
+            return go(cgemm_simt_kernel<VA, VB, VC, R, AT, 32, 16>, dim3(ceil_div(m, 32), ceil_div(n, 16)));
     }
     // otherwise the column tile with the least padding (ties go to the wider tile)
     int bn = 64;

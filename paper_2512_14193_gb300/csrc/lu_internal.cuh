@@ -446,7 +446,9 @@ bool panel_shape(int m, int cl_max, bool lane_col, PanelShape& ps) {
         }
     }
     constexpr int W = std::is_same<V, C32>::value ? 32 : 16;  // widest sub-panel (1 row per thread)
-    int CL = std::min(cl_max, std::max(1, ceil_div(m, PANEL_THREADS)));
+    // about 64 rows per CTA while the cluster allows (FP64 issues slowly on each SM, so short panels
+    // are spread rather than kept on one CTA), one row per thread up to 512 rows per CTA
+    int CL = std::min(cl_max, std::max(1, ceil_div(m, 64)));
     int R = ceil_div(m, CL);
     int RPT = ceil_div(R, PANEL_THREADS);
     if (RPT > 4) return false;
