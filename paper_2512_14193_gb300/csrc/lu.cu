@@ -355,16 +355,19 @@ __device__ __forceinline__ void load_block(CV* dst, const CV* __restrict__ src, 
 // (the reciprocals 1 / U_kk are formed before the sweep).
 // Entries outside the rb x rb leading block are zero.
 constexpr int TI_B = 64;
-template <class V, bool UPPER>
+template <class V, bool UPPER, int CG>
 __global__ void __launch_bounds__(256) tri_inv_kernel(V F, int n, typename V::cv* __restrict__ out) {
     using CV = typename V::cv;
     using Rl = typename V::real;
-    constexpr int B = TI_B, M = B * B / 256;
+    // CG column groups (blockIdx.y): the columns of the inverse are independent, so the FP64
+    // factors, whose pipe is slow on each SM, spread one block over CG CTAs
+    constexpr int B = TI_B, M = B * B / 256 / CG;
     extern __shared__ __align__(16) unsigned char sm[];
     CV* T = reinterpret_cast<CV*>(sm);  // [B][B] column-major
     CV* buf = T + B * B;                // [2][B]
     CV* dg = buf + 2 * B;               // [B] 1 / U_kk
     const int t = threadIdx.x, i = t % B, c0 = t / B;
+    const int mg = (int)blockIdx.y * M;  // this CTA's columns: c0 + 4 (mg + m), m < M
     const long r0 = (long)blockIdx.x * B;
     const int rb = (int)min((long)B, n - r0);
     load_tile<B, B>(T, F, r0, r0, rb, rb);
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(256) tri_inv_kernel(V F, int n, typename V::cv
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         x[m] = czero<Rl>();
-        if (i == c0 + 4 * m && i < rb) x[m].x = (Rl)1;
+        if (i == c0 + 4 * (mg + m) && i < rb) x[m].x = (Rl)1;
     }
     __syncthreads();
     for (int s = 0; s < rb; ++s) {
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(256) tri_inv_kernel(V F, int n, typename V::cv
                 for (int m = 0; m < M; ++m) x[m] = cmul(x[m], d);
             }
 #pragma unroll
-            for (int m = 0; m < M; ++m) bk[c0 + 4 * m] = x[m];
+            for (int m = 0; m < M; ++m) bk[c0 + 4 * (mg + m)] = x[m];
         }
         __syncthreads();
         if (UPPER ? i < k : (i > k && i < rb)) {
@@ -394,12 +397,12 @@ __global__ void __launch_bounds__(256) tri_inv_kernel(V F, int n, typename V::cv
             tik.x = -tik.x;
             tik.y = -tik.y;
 #pragma unroll
-            for (int m = 0; m < M; ++m) cfma(x[m], tik, bk[c0 + 4 * m]);
+            for (int m = 0; m < M; ++m) cfma(x[m], tik, bk[c0 + 4 * (mg + m)]);
         }
     }
     CV* o = out + (long)blockIdx.x * B * B;
 #pragma unroll
-    for (int m = 0; m < M; ++m) o[i + (c0 + 4 * m) * B] = x[m];
+    for (int m = 0; m < M; ++m) o[i + (c0 + 4 * (mg + m)) * B] = x[m];
 }
 
 // One block step of a blocked triangular solve with inverted diagonal blocks (one launch per
@@ -993,12 +996,15 @@ bm_status factor_t(bm_ctx* c, V F, bool tc, int split) {
     const int nblk = ceil_div(n, bs);
     size_t smem = ((size_t)bs * bs + 3 * (size_t)bs) * sizeof(typename V::cv);
     using CV = typename V::cv;
-    LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    constexpr int CG = std::is_same<V, C32>::value ? 1 : 4;  // column groups per block (FP64: 4)
+    LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, false, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    LU_CUDA(cudaFuncSetAttribute(tri_inv_kernel<V, true, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
     {
         BM_PROF(c, "tri_inv_kernel");
-        tri_inv_kernel<V, false><<<nblk, 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvL));
-        tri_inv_kernel<V, true><<<nblk, 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvU));
+        tri_inv_kernel<V, false, CG><<<dim3(nblk, CG), 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvL));
+        tri_inv_kernel<V, true, CG><<<dim3(nblk, CG), 256, smem, s>>>(F, n, reinterpret_cast<CV*>(c->d_dinvU));
         LU_CUDA(cudaGetLastError());
     }
     if constexpr (std::is_same<V, C32>::value) {

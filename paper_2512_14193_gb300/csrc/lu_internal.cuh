@@ -26,6 +26,14 @@ template <class Rl>
 __device__ __forceinline__ bool better(Rl v1, int i1, Rl v2, int i2) {
     return v1 > v2 || (v1 == v2 && i1 < i2);
 }
+// FP64: the values are magnitudes (>= 0) or -1 for "no candidate", whose bit patterns as signed
+// 64-bit integers order like the values, so the comparison runs on the integer pipe instead of
+// the FP64 pipe (1/64 of the FP32 rate on this part)
+template <>
+__device__ __forceinline__ bool better<double>(double v1, int i1, double v2, int i2) {
+    const long long a = __double_as_longlong(v1), b = __double_as_longlong(v2);
+    return a > b || (a == b && i1 < i2);
+}
 
 // ------------------------------------------------------------------------------------------------
 // swap maps: the net effect of ib sequential interchanges (j0+k <-> ipiv[j0+k]) on the rows they
@@ -240,14 +248,17 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         if (c >= ib) break;
         const int par = c & 1;
         const CV* uprev = ucur[par ^ 1];  // pivot row of column c-1 (valid for c > 0)
-        // ---- (1) CTA-wide argmax of column c: max |Re|+|Im|, then the smallest row ----
+        // ---- (1) CTA-wide argmax of column c: max |Re|+|Im|, then the smallest row (warps that
+        //          hold no rows keep (-1, none)) ----
+        if (RPT > 1 || warp * 32 < nloc) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            Rl ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (better(ov, oi, bv, bi)) {
-                bv = ov;
-                bi = oi;
+            for (int o = 16; o > 0; o >>= 1) {
+                Rl ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (better(ov, oi, bv, bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
             }
         }
         if (lane == 0) {
