@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(ST_WARPS * 32) swap_trsm_kernel(V A, const Swa
             if (lane > l && lane + 32 * QK < tb) cfma(x[QK], lk(lane + 32 * QK, k), nx);
 #pragma unroll
             for (int q = QK + 1; q < QMAX; ++q) {
+                if (32 * q >= tb) break;  // warp-uniform: groups past tb issue nothing
                 const int i = lane + 32 * q;
                 if (i < tb) cfma(x[q], lk(i, k), nx);
             }
@@ -448,7 +449,10 @@ __global__ void __launch_bounds__(256) trsv_step_kernel(V F, V Y, V Z, int r0, i
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < TN; ++b) acc[a][b] = czero<Rl>();
-        for (int k = 0; k < rb; ++k) {
+        // threads whose columns all lie past the last right-hand side skip the products (with one
+        // right-hand side, 15 of 16 column slots: the FP64 pipe is the bound of these small steps)
+        const int kend = (ty < nc) ? rb : 0;
+        for (int k = 0; k < kend; ++k) {
             CV tv[4], yv[TN];
 #pragma unroll
             for (int a = 0; a < 4; ++a) tv[a] = (a < TMb) ? Ts[tx + 16 * a + k * bs] : czero<Rl>();
@@ -477,7 +481,8 @@ __global__ void __launch_bounds__(256) trsv_step_kernel(V F, V Y, V Z, int r0, i
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < TN; ++b) acc[a][b] = czero<Rl>();
-    for (int k = 0; k < rb; ++k) {
+    const int kend2 = (ty < nc) ? rb : 0;
+    for (int k = 0; k < kend2; ++k) {
         CV fv[4], zv[TN];
 #pragma unroll
         for (int a = 0; a < 4; ++a) fv[a] = Ft[k * TS_BM + tx + 16 * a];
