@@ -372,7 +372,9 @@ __global__ void __launch_bounds__(PANEL_THREADS, 1)
         }
         // ---- (7) scale column c, update column c+1, argmax of column c+1 ----
         const CV uc = u[0 + c];
-        const CV inv = sing ? zero : cinv(uc);
+        // only warps that hold rows use 1/u_c (FP64 division is long on the FP64 pipe)
+        CV inv = zero;
+        if (!sing && (RPT > 1 || warp * 32 < nloc)) inv = cinv(uc);
         const CV un = (c + 1 < NBP) ? u[c + 1] : zero;
         bv = (Rl)-1;
         bi = INT_MAX;
