@@ -3,7 +3,8 @@
 // G = (i/4) H0^(1)(k r) and its normal derivatives (H0' = -H1).
 //
 // Three zones by |z|, each accurate to about 1e-14 relative in |H|:
-//  * |z| < 3    : ascending series of J0, J1, Y0, Y1 (16 terms; (|z|^2/4)^m/(m!)^2 < 1e-18).
+//  * |z| < 3    : ascending series of J0, J1, Y0, Y1, summed while (|z|^2/4)^m/(m!)^2 > 1e-17
+//    (at most 14 terms).
 //  * 3 <= |z| < 20 : Taylor expansion about the nearest anchor z0 of a grid with spacing 1/4
 //    (|z - z0| <= 0.177).  The Taylor coefficients of H0 about z0 follow from Bessel's equation
 //    z^2 y'' + z y' + z^2 y = 0 written in delta = z - z0:
@@ -16,10 +17,11 @@
 //       a_k(nu) = prod_{j=1..k} (4nu^2 - (2j-1)^2) / (k! 8^k),
 //    summed until the terms fall below 1e-17 (at most 40 terms; about 20 at |z| = 20).
 // GB300 runs FP64 at 1/64 of its FP32 rate, and the series terms fall fast: past the first six
-// terms of either series (asymptotic: |a_7 / z^7| < 1e-8 for |z| >= 20; Taylor: |delta| <= 0.177)
+// terms of the Taylor and asymptotic series (asymptotic: |a_7 / z^7| < 1e-8 for |z| >= 20;
+// Taylor: |delta| <= 0.177) and the first nine of the ascending one (|w|^10/(10!)^2 < 2.5e-10)
 // the rest of the sum is below 1e-8 of it, so those terms are formed and summed in FP32 (their
 // rounding errors stay near 1e-15 of the result) and added to the FP64 sum once.  The leading
-// terms, the recurrence's starting values, exp, sincos and the roots stay FP64.
+// terms, the recurrence's starting values, log, exp, sincos and the roots stay FP64.
 #pragma once
 #include "common.cuh"
 
@@ -50,13 +52,23 @@ __device__ __forceinline__ double2 csqrt(double2 w) {
 __device__ __forceinline__ void series(double2 z, double2& h0, double2& h1) {
     // w = -z^2/4; t0_m = w^m/(m!)^2, t1_m = w^m/(m!(m+1)!)
     double2 w = cscale(cmul(z, z), -0.25);
+    // |w|^m/(m!)^2 <= 1e-17 for |w| <= THR[m-1] (and the later terms are smaller still): the sums
+    // stop at the first such m, taken from |w| in FP32 once rather than from FP64 tests of the
+    // terms.  |w| < 2.25 in this zone, so at most 14 terms are summed (at |z| = 3), 9 for |z| <= 1.
+    constexpr float THR[15] = {1e-17f,    6.32456e-9f, 7.11379e-6f, 2.75490e-4f, 2.70192e-3f,
+                               1.31556e-2f, 4.25859e-2f, 0.106263f,  0.222133f,  0.409216f,
+                               0.686394f, 1.07166f,    1.58169f,    2.23167f,    3.03529f};
+    const float2 zf = f2(z);
+    const float wa = 0.25f * (zf.x * zf.x + zf.y * zf.y);
     double2 t0 = make_double2(1.0, 0.0), t1 = make_double2(1.0, 0.0);
     double2 J0 = t0, J1 = t1;
     double2 S0 = make_double2(0.0, 0.0);                      // sum H_m t0_m
     double2 S1 = cscale(t1, -2.0 * EULER_GAMMA + 1.0);        // sum (psi(m+1)+psi(m+2)) t1_m, m = 0 term
     double Hm = 0.0;
+    constexpr int M64 = 10;  // terms 1 .. 9 in FP64; from term 10 on |t_m| < 2.5e-10 |t_0|, so FP32
 #pragma unroll
-    for (int m = 1; m < 16; ++m) {
+    for (int m = 1; m < M64; ++m) {
+        if (wa <= THR[m - 1]) break;
         double dm = (double)m;
         t0 = cscale(cmul(t0, w), 1.0 / (dm * dm));
         t1 = cscale(cmul(t1, w), 1.0 / (dm * (dm + 1.0)));
@@ -65,6 +77,29 @@ __device__ __forceinline__ void series(double2 z, double2& h0, double2& h1) {
         J1 = cadd(J1, t1);
         S0 = cadd(S0, cscale(t0, Hm));
         S1 = cadd(S1, cscale(t1, -2.0 * EULER_GAMMA + 2.0 * Hm + 1.0 / (dm + 1.0)));
+    }
+    if (wa > THR[M64 - 1]) {
+        // the same sums in FP32 from term 10 on, added to the FP64 sums once
+        const float2 fw = f2(w);
+        float2 ft0 = f2(t0), ft1 = f2(t1);
+        float2 fJ0 = make_float2(0.f, 0.f), fJ1 = fJ0, fS0 = fJ0, fS1 = fJ0;
+        float fH = (float)Hm;
+#pragma unroll
+        for (int m = M64; m < 16; ++m) {
+            if (wa <= THR[m - 1]) break;
+            const float dm = (float)m;
+            ft0 = fscale(cmul(ft0, fw), 1.0f / (dm * dm));
+            ft1 = fscale(cmul(ft1, fw), 1.0f / (dm * (dm + 1.0f)));
+            fH += 1.0f / dm;
+            fJ0 = cadd(fJ0, ft0);
+            fJ1 = cadd(fJ1, ft1);
+            fS0 = cadd(fS0, fscale(ft0, fH));
+            fS1 = cadd(fS1, fscale(ft1, (float)(-2.0 * EULER_GAMMA) + 2.0f * fH + 1.0f / (dm + 1.0f)));
+        }
+        J0 = cadd(J0, make_double2(fJ0.x, fJ0.y));
+        J1 = cadd(J1, make_double2(fJ1.x, fJ1.y));
+        S0 = cadd(S0, make_double2(fS0.x, fS0.y));
+        S1 = cadd(S1, make_double2(fS1.x, fS1.y));
     }
     double2 zh = cscale(z, 0.5);
     J1 = cmul(J1, zh);
