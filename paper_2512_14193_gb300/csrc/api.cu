@@ -941,19 +941,28 @@ bm_status ensure_ws(bm_ctx* c, int nrhs) {
         const int N = c->N, np = rt_digit_planes(c->rt_nd);
         const int npad = (int)round_up(w, rt_col_tile(c->rt_nd));
         const int nprod = (c->form == BM_MIXED) ? 2 : 1;
-        size_t wsz = 0;
+        long mq[2], Kq[2];
         for (int q = 0; q < nprod; ++q) {
             // mixed: [0] rows [2N, 3N) for Mtop (K = N), [1] rows [0, 2N) for Mbot (K = 2N);
             // ordinary: [0] rows [0, 2N) for A (K = 2N)
             const long K = (c->form == BM_MIXED && q == 0) ? N : 2L * N;
-            const long m = (c->form == BM_MIXED && q == 1) ? N : 2L * N;
+            mq[q] = (c->form == BM_MIXED && q == 1) ? N : 2L * N;
+            Kq[q] = K;
             c->dx_ldk[q] = rt_ldk(K);
             BM_TRY(alloc_t(c, &c->d_dx[q], (size_t)np * npad * c->dx_ldk[q] * 2));
             BM_TRY(alloc_t(c, &c->d_dxe[q], (size_t)npad * 4));
             BM_TRY(rt_make_map(c->tm_dx[q], c->d_dx[q], npad, K, c->dx_ldk[q], (long)npad * c->dx_ldk[q],
                                rt_col_tile(c->rt_nd), c->rt_nd));
-            const int S = rt_splits((int)K);
-            if (S > 1) wsz += 2 * (size_t)S * m * w;
+        }
+        // the split count depends on the number of right-hand sides: size for the largest need
+        size_t wsz = 0;
+        for (int r = 1; r <= w; ++r) {
+            int S[2];
+            rt_plan_splits(nprod, mq, Kq, r, c->rt_nd, c->num_sms, S);
+            size_t t = 0;
+            for (int q = 0; q < nprod; ++q)
+                if (S[q] > 1) t += 2 * (size_t)S[q] * mq[q] * r;
+            wsz = std::max(wsz, t);
         }
         if (wsz) BM_TRY(alloc_t(c, &c->d_rtw, wsz * 8));
         c->rtw_elems = wsz;

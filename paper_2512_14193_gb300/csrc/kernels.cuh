@@ -104,7 +104,8 @@ struct RtArgs {
 long rt_ldk(long K);                 // leading dimension of a digit plane row (K rounded to 64)
 int rt_digit_planes(int nd);         // planes per operand (nd digits x Re, Im)
 int rt_col_tile(int nd);             // right-hand sides per CTA
-int rt_splits(int K);                // K splits of a product
+// K splits S[q] of the nprod products (m[q] rows, K[q] columns) of one launch with n right-hand sides
+void rt_plan_splits(int nprod, const long* m, const long* K, int n, int nd, int num_sms, int* S);
 bm_status rt_make_map(void* tmap, const void* base, long rows, long K, long ldk, long plane_elems, int box_rows,
                       int nd);
 cudaError_t launch_digits_a(cudaStream_t s, const double2* A, long lda, int rows, int K, int* e, void* D, long ldk,

@@ -600,10 +600,23 @@ cudaError_t launch_digits_x(cudaStream_t s, const double2* X, long ldx, int r0, 
     return cudaGetLastError();
 }
 
-// Split count of one product so that every CTA covers about 32 K blocks of 64.
-int rt_splits(int K) {
-    const int kblocks = ceil_div(K, RT_BK);
-    return std::max(1, std::min(16, kblocks / 32));
+// K splits of the products of one residual launch.  A CTA holds a whole SM (its shared memory
+// and all 512 tensor-memory columns), so the launch aims at one CTA per SM: every CTA covers
+// ceil(work / SMs) K blocks of 64, at least 4 (the set-up and the x digit loads amortised) and at
+// most 32, where work counts the K blocks of every row and column tile of the launch.  Large
+// systems land on 32 (N = 4096: two and four splits); small ones split further, so that, e.g., a
+// 1024-point mixed system with 16 right-hand sides runs 128 CTAs instead of 24.  Every split keeps
+// at least one K block (S <= K blocks).
+void rt_plan_splits(int nprod, const long* m, const long* K, int n, int nd, int num_sms, int* S) {
+    auto cdiv = [](long a, long b) { return (a + b - 1) / b; };
+    const long ntn = cdiv(n, rt_col_tile(nd));
+    long work = 0;
+    for (int q = 0; q < nprod; ++q) work += cdiv(m[q], RT_BM) * ntn * cdiv(K[q], RT_BK);
+    const long per = std::min(32L, std::max(4L, cdiv(work, std::max(num_sms, 1))));
+    for (int q = 0; q < nprod; ++q) {
+        const long kb = cdiv(K[q], RT_BK);
+        S[q] = (int)std::max(1L, std::min(std::min(16L, kb), cdiv(kb, per)));
+    }
 }
 
 // The products of one residual (at most two, sharing n and alpha): C += alpha A x each.  A product

@@ -290,13 +290,19 @@ bm_status residual_tc(bm_ctx* c, const double2* B, const double2* X, double2* R,
     RtArgs P[2];
     double* w = c->d_rtw;
     int np = 0;
+    int S[2];
+    {
+        const long mq[2] = {c->form == BM_MIXED ? N : 2L * N, 2L * N};
+        const long Kq[2] = {2L * N, c->form == BM_MIXED ? N : 2L * N};
+        rt_plan_splits(nprod, mq, Kq, nrhs, c->rt_nd, c->num_sms, S);
+    }
     auto add = [&](int dg, int dx, double2* Cout, int m, int K) {
-        const int S = rt_splits(K);
-        RtArgs a{c->tm_dg[dg], c->tm_dx[dx], c->d_dge[dg], c->d_dxe[dx], Cout, ld, nullptr, nullptr, m, K, S};
-        if (S > 1) {
+        const int Sq = S[np];
+        RtArgs a{c->tm_dg[dg], c->tm_dx[dx], c->d_dge[dg], c->d_dxe[dx], Cout, ld, nullptr, nullptr, m, K, Sq};
+        if (Sq > 1) {
             a.Wr = w;
-            a.Wi = w + (size_t)S * m * nrhs;
-            w += 2 * (size_t)S * m * nrhs;
+            a.Wi = w + (size_t)Sq * m * nrhs;
+            w += 2 * (size_t)Sq * m * nrhs;
         }
         P[np++] = a;
     };
