@@ -167,7 +167,10 @@ typedef struct bm_ctx bm_ctx;
 /* Create a handle on CUDA device `device`.  cuda_stream (a cudaStream_t, may be NULL) is the
  * stream all work is enqueued on; NULL makes the handle create and own a non-blocking stream.
  * hbm_budget_bytes bounds the device memory the handle may hold (0 = 90 % of free memory at
- * creation).  The Hankel anchor table (about 0.4 MB) is built on first use and uploaded. */
+ * creation).  The Hankel Taylor table (about 3 MB, see bm_hankel_taylor_table) is built on the
+ * host on first use and uploaded once per device and CUDA context by the first bm_create there;
+ * every handle on the device shares that copy, which is not counted against any handle's budget
+ * and lives as long as the context. */
 bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size_t hbm_budget_bytes);
 
 /* Assemble the Nystrom system (section 4, Eq. dis_mixedBM or Eq. dis_BM) for N nodes on the
@@ -388,13 +391,22 @@ bm_status bm_copy_block(bm_ctx* ctx, int which, bm_c64* dst, int ldd, int on_dev
  * on_device, else host arrays. */
 bm_status bm_hankel01(bm_ctx* ctx, const bm_c64* z, int n, bm_c64* h0, bm_c64* h1, int on_device);
 
-/* Host copy of the anchor table the device Taylor zone of bm_hankel01 expands from:
+/* Host copy of the anchor table the device Taylor zone of bm_hankel01 expands about:
  * H0^(1)(z0), H1^(1)(z0) at z0 = re0 + ix*step + i (im0 + iy*step), stored as
  * out[4*(iy*nx + ix) + {0,1,2,3}] = {Re H0, Im H0, Re H1, Im H1}; anchors outside the annulus
  * 2.5 <= |z0| <= 21 are zero.  Built once per process on the host (no GPU needed); out may be
  * NULL to query the sizes, else it must hold cap_anchors >= nx*ny anchors. */
 bm_status bm_hankel_anchor_table(double* out, int cap_anchors, int* nx, int* ny, double* re0, double* im0,
                                  double* step);
+
+/* Host copy of the Taylor coefficients the device Taylor zone of bm_hankel01 evaluates: for every
+ * anchor of bm_hankel_anchor_table (same nx, ny, re0, im0, step), H0^(1)(z0 + d) = sum_k a_k d^k
+ * (a_0 = H0(z0), a_1 = -H1(z0), the rest from Bessel's equation; H1 = -dH0/dz), k = 0 .. nterms-1,
+ * stored as out[2*(nterms*(iy*nx + ix) + k) + {0,1}] = {Re a_k, Im a_k}.  The device holds a_0 .. a_8
+ * in FP64 and the rest in FP32; they are returned as the device holds them, widened to double.
+ * Zero outside the annulus 2.5 <= |z0| <= 21.  Built once per process on the host (no GPU
+ * needed); out may be NULL to query nterms, else it must hold cap_anchors >= nx*ny anchors. */
+bm_status bm_hankel_taylor_table(double* out, int cap_anchors, int* nterms);
 
 /* Timing probe: enqueue `reps` launches of one hot kernel on the handle's stream and return
  * without synchronising, so a caller can bracket them with its own events on that stream.

@@ -124,6 +124,7 @@ def lib():
     L.bm_zeta_weights.argtypes = [I, C.POINTER(D), C.POINTER(D)]
     L.bm_hankel_anchor_table.argtypes = [C.POINTER(D), I, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(D),
                                          C.POINTER(D)]
+    L.bm_hankel_taylor_table.argtypes = [C.POINTER(D), I, C.POINTER(I)]
     L.bm_memory.argtypes = [P, C.POINTER(S), C.POINTER(S)]
     L.bm_kernel_launches.argtypes = [P, C.POINTER(C.c_ulonglong)]
     L.bm_enqueue_probe.argtypes = [P, I, I]
@@ -137,7 +138,8 @@ def lib():
                  "bm_far_field",
                  "bm_far_field_static", "bm_ssm", "bm_server_create", "bm_server_submit", "bm_server_wait",
                  "bm_server_stats_get", "bm_server_destroy",
-                 "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_zeta_weights", "bm_memory",
+                 "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_hankel_taylor_table", "bm_zeta_weights",
+                 "bm_memory",
                  "bm_destroy",
                  "bm_kernel_launches", "bm_enqueue_probe", "bm_profile", "bm_ssm_release"):
         getattr(L, name).restype = C.c_int
@@ -466,6 +468,20 @@ def bm_hankel_anchor_table():
                                     None, None, None), "bm_hankel_anchor_table")
     t = out.view(np.complex128).reshape(ny.value, nx.value, 2)
     return t, re0.value, im0.value, step.value
+
+
+def bm_hankel_taylor_table():
+    """table[ny, nx, nterms] complex: the Taylor coefficients of H0 about every anchor of
+    bm_hankel_anchor_table (as the device holds them) - host-built, no GPU needed."""
+    T, _re0, _im0, _step = bm_hankel_anchor_table()
+    ny, nx = T.shape[0], T.shape[1]
+    L = lib()
+    K = C.c_int()
+    _check(L.bm_hankel_taylor_table(None, 0, C.byref(K)), "bm_hankel_taylor_table")
+    out = np.zeros(2 * K.value * nx * ny, dtype=np.float64)
+    _check(L.bm_hankel_taylor_table(out.ctypes.data_as(C.POINTER(C.c_double)), nx * ny, None),
+           "bm_hankel_taylor_table")
+    return out.view(np.complex128).reshape(ny, nx, K.value)
 
 
 def bm_memory(h):

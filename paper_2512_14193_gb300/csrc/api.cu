@@ -322,8 +322,9 @@ extern "C" bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size
     c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
     int nx, ny;
     double re0, im0, step;
-    const std::vector<double2>& tab = hankel_anchor_host(nx, ny, re0, im0, step);
-    bm_status s = alloc_t(c, &c->d_htab, tab.size() * sizeof(double2));
+    hankel_anchor_host(nx, ny, re0, im0, step);
+    const double2* tab = nullptr;
+    bm_status s = hankel_table_device(device, &tab);
     if (s == BM_OK) s = alloc_t(c, &c->d_normA, 4 * sizeof(double));
     if (s == BM_OK) s = alloc_t(c, &c->d_info, 64 * sizeof(int));
     if (s == BM_OK) s = alloc_t(c, &c->d_maps, 3 * swap_map_bytes());
@@ -332,8 +333,7 @@ extern "C" bm_status bm_create(bm_ctx** out, int device, void* cuda_stream, size
         return s;
     }
     c->d_err = c->d_info + 1;
-    cudaMemcpy(c->d_htab, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
-    c->htab = HankelTable{c->d_htab, nx, ny, re0, im0, step, 1.0 / step};
+    c->htab = HankelTable{tab, nx, ny, re0, im0, step, 1.0 / step};
     *out = c;
     return BM_OK;
 }
@@ -343,7 +343,6 @@ extern "C" bm_status bm_destroy(bm_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_problem(c);
-    FREE(c->d_htab);
     FREE(c->d_normA);
     FREE(c->d_info);
     FREE(c->d_maps);

@@ -137,13 +137,27 @@ static inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 // ---------------------------------------------------------------------------------------------
 // Hankel anchor table (built on the host in double-double, see hankel_table.cpp)
 // ---------------------------------------------------------------------------------------------
+// Taylor coefficients a_0 .. a_18 of H0^(1) about every anchor z0 (H0(z0 + d) = sum a_k d^k):
+// a_0 .. a_8 as FP64 complex, a_9 .. a_18 as FP32 complex (two per 16-byte slot), 14 slots
+// (224 bytes) per anchor at [(iy * nx + ix) * HT_SLOTS].
+constexpr int HT_K64 = 9, HT_K32 = 10, HT_SLOTS = HT_K64 + HT_K32 / 2;
 struct HankelTable {
-    const double2* h;  // [iy * nx + ix] -> {H0, H1} pairs (2 entries per anchor)
+    const double2* c;  // coefficient blocks, HT_SLOTS per anchor
     int nx, ny;
     double re0, im0, step, inv_step;
 };
-// Builds (once per process) the host copy of the anchor table.
+// Builds (once per process) the host copy of the anchor table: {H0(z0), H1(z0)} per anchor.
 const std::vector<double2>& hankel_anchor_host(int& nx, int& ny, double& re0, double& im0, double& step);
+// The coefficient blocks of the same anchors (built with the anchor table).
+const std::vector<double2>& hankel_coef_host();
+// The device copy of the coefficient blocks on `dev` (the current device): uploaded by the first
+// call in each CUDA context of the device and shared by every handle there; it lives as long as
+// the context (no handle owns it or counts it against its HBM budget).
+bm_status hankel_table_device(int dev, const double2** out);
+// Unique ID of the calling thread's current CUDA context (driver API through the runtime's
+// entry-point query); 0 if there is none or the query is unavailable.  IDs are never reused within
+// a process, so a context that replaced a reset one has a new ID.
+unsigned long long cuda_context_id();
 
 // ---------------------------------------------------------------------------------------------
 // The handle
@@ -169,7 +183,6 @@ struct bm_ctx {
     std::map<void*, size_t> allocs;
 
     HankelTable htab{};
-    double2* d_htab = nullptr;
 
     // problem
     bool assembled = false;

@@ -15,7 +15,8 @@
 //
 // Set-up: the first call on a device, with that device current, looks up the device address of
 // the array (cudaGetSymbolAddress) and keeps it for later calls on that device, together with the
-// CUDA context it belongs to.  The lookup can load the library's device code onto the device, so
+// unique ID of the CUDA context it belongs to (a context created after a reset gets a new ID, even
+// where the driver reuses the old context's handle).  The lookup can load the library's device code onto the device, so
 // make this first call before any stream capture starts on the device.  If the device's context
 // has been replaced since (cudaDeviceReset, then new work), the address is looked up again: an
 // address from the old context would no longer belong to the array.
@@ -37,26 +38,7 @@ namespace {
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mu;
 double* g_angles_ptr[MAX_DEVICES] = {};
-void* g_angles_ctx[MAX_DEVICES] = {};  // the context each address was looked up in
-
-// The calling thread's current CUDA context (driver API, reached through the runtime's entry-point
-// query so the library needs no link-time dependence on libcuda); nullptr if unavailable.
-void* current_context() {
-    using GetCurrent = int (*)(void**);
-    static GetCurrent fn = []() -> GetCurrent {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        return reinterpret_cast<GetCurrent>(p);
-    }();
-    void* ctx = nullptr;
-    if (fn == nullptr || fn(&ctx) != 0) return nullptr;
-    return ctx;
-}
+unsigned long long g_angles_ctx[MAX_DEVICES] = {};  // ID of the context each address was looked up in
 
 // Device address of g_ff_angles on `dev` (the current device), looked up once per device and
 // context.
@@ -65,9 +47,9 @@ bm_status angles_scratch(int dev, double** out) {
         bm_set_error("bm_far_field_static: device index " + std::to_string(dev) + " out of range");
         return BM_EINVAL;
     }
-    void* ctx = current_context();
+    const unsigned long long ctx = cuda_context_id();
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (g_angles_ptr[dev] == nullptr || ctx == nullptr || ctx != g_angles_ctx[dev]) {
+    if (g_angles_ptr[dev] == nullptr || ctx == 0 || ctx != g_angles_ctx[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_ff_angles);
         if (e != cudaSuccess || p == nullptr) {

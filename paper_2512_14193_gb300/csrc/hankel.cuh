@@ -10,18 +10,20 @@
 //    z^2 y'' + z y' + z^2 y = 0 written in delta = z - z0:
 //       z0^2 (k+1)(k+2) a_{k+2} = -[ z0 (k+1)(2k+1) a_{k+1} + (k^2 + z0^2) a_k
 //                                    + 2 z0 a_{k-1} + a_{k-2} ],
-//    a_0 = H0(z0), a_1 = -H1(z0); H1(z) = -H0'(z) is the differentiated series.  The anchors
-//    come from the table built on the host (ODE integration in double-double).
+//    a_0 = H0(z0), a_1 = -H1(z0); H1(z) = -H0'(z) is the differentiated series.  The host table
+//    (hankel_table.cu: ODE integration in double-double) holds a_0 .. a_18 for every anchor, so
+//    the device evaluates the polynomial and its derivative by Horner's scheme: 18 complex
+//    multiply-adds each, the nine of a_8 .. a_0 in FP64 (72 FP64 FMAs), the rest in FP32.
 //  * |z| >= 20  : Hankel's asymptotic expansion
 //       H_nu(z) ~ sqrt(2/(pi z)) e^{i(z - nu pi/2 - pi/4)} sum_k i^k a_k(nu) / z^k,
 //       a_k(nu) = prod_{j=1..k} (4nu^2 - (2j-1)^2) / (k! 8^k),
 //    summed until the terms fall below 1e-17 (at most 40 terms; about 20 at |z| = 20).
 // GB300 runs FP64 at 1/64 of its FP32 rate, and the series terms fall fast: past the first six
-// terms of the Taylor and asymptotic series (asymptotic: |a_7 / z^7| < 1e-8 for |z| >= 20;
-// Taylor: |delta| <= 0.177) and the first nine of the ascending one (|w|^10/(10!)^2 < 2.5e-10)
-// the rest of the sum is below 1e-8 of it, so those terms are formed and summed in FP32 (their
-// rounding errors stay near 1e-15 of the result) and added to the FP64 sum once.  The leading
-// terms, the recurrence's starting values, log, exp, sincos and the roots stay FP64.
+// terms of the asymptotic series (|a_7 / z^7| < 1e-8 for |z| >= 20), the first nine of the Taylor
+// one (relative 3e-11 for H0, 2e-9 for the differentiated H1) and the first nine of the ascending
+// one (|w|^10/(10!)^2 < 2.5e-10) the rest of the sum is below 1e-8 of it, so those terms are
+// formed and summed in FP32 (their rounding errors stay near 1e-15 of the result) and added to
+// the FP64 sum once.  The leading terms, log, exp, sincos and the roots stay FP64.
 #pragma once
 #include "common.cuh"
 
@@ -119,70 +121,35 @@ __device__ __forceinline__ void taylor(double2 z, const HankelTable& T, double2&
     int iy = __double2int_rn((z.y - T.im0) * T.inv_step);
     ix = min(max(ix, 0), T.nx - 1);
     iy = min(max(iy, 0), T.ny - 1);
-    double2 z0 = make_double2(T.re0 + ix * T.step, T.im0 + iy * T.step);
-    const double2* a = T.h + 2 * ((long)iy * T.nx + ix);
-    double2 a0 = __ldg(a), H1z0 = __ldg(a + 1);
-    double2 d = csub(z, z0);
-    double2 z0sq = cmul(z0, z0);
-    double2 iz2 = cinv(z0sq);
-    double2 am2 = make_double2(0.0, 0.0), am1 = make_double2(0.0, 0.0);
-    double2 ak = a0, ak1 = cneg(H1z0);
-    double2 s0 = cadd(a0, cmul(ak1, d));     // H0 partial sum
-    double2 s1 = ak1;                         // H0' partial sum
-    double2 dk = d;                           // d^(k+1)
-    constexpr int K64 = 6;                    // terms a_2 .. a_7 in FP64, the rest in FP32
-    bool done = false;
-    for (int k = 0; k < K64; ++k) {
-        double dk_ = (double)k;
-        // bracket = z0 (k+1)(2k+1) a_{k+1} + (k^2 + z0^2) a_k + 2 z0 a_{k-1} + a_{k-2}
-        double2 br = cscale(cmul(z0, ak1), (dk_ + 1.0) * (2.0 * dk_ + 1.0));
-        br = cadd(br, cmul(make_double2(z0sq.x + dk_ * dk_, z0sq.y), ak));
-        br = cadd(br, cscale(cmul(z0, am1), 2.0));
-        br = cadd(br, am2);
-        double2 an = cscale(cmul(br, iz2), -1.0 / ((dk_ + 1.0) * (dk_ + 2.0)));
-        double2 t1 = cscale(cmul(an, dk), dk_ + 2.0);   // (k+2) a_{k+2} d^(k+1)
-        dk = cmul(dk, d);                                // d^(k+2)
-        double2 t0 = cmul(an, dk);
-        s0 = cadd(s0, t0);
-        s1 = cadd(s1, t1);
-        am2 = am1;
-        am1 = ak;
-        ak = ak1;
-        ak1 = an;
-        if (cnorm1(t0) <= 1e-17 * cnorm1(s0) && cnorm1(t1) <= 1e-17 * cnorm1(s1)) {
-            done = true;
-            break;
-        }
+    const double2 z0 = make_double2(T.re0 + ix * T.step, T.im0 + iy * T.step);
+    const double2* C = T.c + (long)HT_SLOTS * ((long)iy * T.nx + ix);
+    const double2 d = csub(z, z0);
+    // Horner's scheme for P(d) = sum a_k d^k and its derivative together (Q <- Q d + P before
+    // P <- P d + a_k): a_18 .. a_9 in FP32, then a_8 .. a_0 in FP64.  H0 = P, H1 = -P'.
+    const float4* C32 = reinterpret_cast<const float4*>(C + HT_K64);
+    float2 c32[HT_K32];
+#pragma unroll
+    for (int j = 0; j < HT_K32 / 2; ++j) {
+        const float4 v = __ldg(C32 + j);
+        c32[2 * j] = make_float2(v.x, v.y);
+        c32[2 * j + 1] = make_float2(v.z, v.w);
     }
-    if (!done) {
-        // the same recurrence and sums in FP32 from a_8 on
-        const float2 fz0 = f2(z0), fd = f2(d), fiz2 = f2(iz2), fz0sq = f2(z0sq);
-        float2 fdk = f2(dk), fm2 = f2(am2), fm1 = f2(am1), fk = f2(ak), fk1 = f2(ak1);
-        float2 f0 = make_float2(0.f, 0.f), f1 = f0;
-        const float n0 = 1e-17f * (float)cnorm1(s0), n1 = 1e-17f * (float)cnorm1(s1);
-        for (int k = K64; k < 40; ++k) {
-            const float kf = (float)k;
-            float2 br = fscale(cmul(fz0, fk1), (kf + 1.f) * (2.f * kf + 1.f));
-            br = cadd(br, cmul(make_float2(fz0sq.x + kf * kf, fz0sq.y), fk));
-            br = cadd(br, fscale(cmul(fz0, fm1), 2.f));
-            br = cadd(br, fm2);
-            const float2 an = fscale(cmul(br, fiz2), -1.f / ((kf + 1.f) * (kf + 2.f)));
-            const float2 t1 = fscale(cmul(an, fdk), kf + 2.f);
-            fdk = cmul(fdk, fd);
-            const float2 t0 = cmul(an, fdk);
-            f0 = cadd(f0, t0);
-            f1 = cadd(f1, t1);
-            fm2 = fm1;
-            fm1 = fk;
-            fk = fk1;
-            fk1 = an;
-            if (cnorm1(t0) <= n0 && cnorm1(t1) <= n1) break;
-        }
-        s0 = cadd(s0, make_double2(f0.x, f0.y));
-        s1 = cadd(s1, make_double2(f1.x, f1.y));
+    const float2 fd = f2(d);
+    float2 fp = c32[HT_K32 - 1], fq = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = HT_K32 - 2; j >= 0; --j) {
+        fq = cadd(cmul(fq, fd), fp);
+        fp = cadd(cmul(fp, fd), c32[j]);
     }
-    h0 = s0;
-    h1 = cneg(s1);
+    double2 P = make_double2(fp.x, fp.y), Q = make_double2(fq.x, fq.y);
+#pragma unroll
+    for (int k = HT_K64 - 1; k >= 0; --k) {
+        const double2 ak = __ldg(C + k);
+        Q = make_double2(fma(Q.x, d.x, fma(-Q.y, d.y, P.x)), fma(Q.x, d.y, fma(Q.y, d.x, P.y)));
+        P = make_double2(fma(P.x, d.x, fma(-P.y, d.y, ak.x)), fma(P.x, d.y, fma(P.y, d.x, ak.y)));
+    }
+    h0 = P;
+    h1 = cneg(Q);
 }
 
 __device__ __forceinline__ void asym(double2 z, double2& h0, double2& h1) {

@@ -10,10 +10,21 @@
 // so the start error neither grows nor is amplified; every anchor is accurate to about 1e-16
 // relative.  Only anchors with 2.5 <= |z0| <= 21 are filled (the Taylor zone uses
 // 3 <= |z| < 20 and the nearest anchor is within 0.177).
+//
+// For the device, every filled anchor also gets the Taylor coefficients a_0 .. a_18 of H0 about it
+// (a_0 = H0(z0), a_1 = H0'(z0) = -H1(z0), the rest by the recurrence Bessel's equation gives in
+// d = z - z0), computed in double-double from the double-double values of the integration and
+// rounded once: the device then evaluates H0(z0 + d) and H1 = -H0' by Horner's scheme.  Relative to
+// a_0, |a_k| 0.177^k < 3e-11 from k = 9 on (at |z0| = 2.8, and smaller further out; the derivative
+// scales term k by k/0.177), so a_9 .. a_18 are kept in FP32, and at k = 19 the terms are below
+// 1e-19 of the sum.
 #include "common.cuh"
 
 #include <cmath>
+#include <cstring>
 #include <mutex>
+#include <string>
+#include <utility>
 
 namespace {
 
@@ -159,7 +170,29 @@ void taylor_step(cdd z0, double d, cdd& y, cdd& yp) {
     yp = s1;
 }
 
+// Taylor coefficients a_0 .. a_{n-1} of H0 about z0 from a_0 = y = H0(z0), a_1 = yp = H0'(z0), by the
+// recurrence taylor_step sums: z0^2 (k+1)(k+2) a_{k+2} = -[z0 (k+1)(2k+1) a_{k+1} + (k^2 + z0^2) a_k
+// + 2 z0 a_{k-1} + a_{k-2}].
+void taylor_coefs(cdd z0, cdd y, cdd yp, cdd* a, int n) {
+    const cdd z0sq = z0 * z0;
+    const cdd iz2 = cinv_dd(z0sq);
+    a[0] = y;
+    a[1] = yp;
+    for (int k = 0; k + 2 < n; ++k) {
+        const double kk = (double)k;
+        cdd br = (z0 * a[k + 1]) * ((kk + 1.0) * (2.0 * kk + 1.0));
+        const cdd c2 = {z0sq.re + mkdd(kk * kk), z0sq.im};
+        br = br + c2 * a[k];
+        if (k >= 1) br = br + (z0 * a[k - 1]) * 2.0;
+        if (k >= 2) br = br + a[k - 2];
+        const cdd t = br * iz2;
+        const dd den = mkdd((kk + 1.0) * (kk + 2.0));
+        a[k + 2] = {-ddiv(t.re, den), -ddiv(t.im, den)};
+    }
+}
+
 std::vector<double2> g_table;
+std::vector<double2> g_coef;
 int g_nx = 0, g_ny = 0;
 const double g_step = 0.25, g_re0 = 0.0, g_im0 = -20.5;
 std::once_flag g_once;
@@ -168,6 +201,7 @@ void build() {
     g_nx = 83;   // Re 0 .. 20.5
     g_ny = 165;  // Im -20.5 .. 20.5
     g_table.assign((size_t)g_nx * g_ny * 2, make_double2(0.0, 0.0));
+    g_coef.assign((size_t)g_nx * g_ny * HT_SLOTS, make_double2(0.0, 0.0));
     for (int iy = 0; iy < g_ny; ++iy) {
         double y = g_im0 + iy * g_step;
         double xs = std::ceil(std::sqrt(std::fmax(0.0, 21.0 * 21.0 - y * y)) / g_step) * g_step;
@@ -183,6 +217,18 @@ void build() {
                 size_t o = 2 * ((size_t)iy * g_nx + ix);
                 g_table[o] = make_double2(Y.re.hi + Y.re.lo, Y.im.hi + Y.im.lo);
                 g_table[o + 1] = make_double2(-(Yp.re.hi + Yp.re.lo), -(Yp.im.hi + Yp.im.lo));
+                cdd a[HT_K64 + HT_K32];
+                taylor_coefs(cdd{mkdd(x), mkdd(y)}, Y, Yp, a, HT_K64 + HT_K32);
+                double2* blk = &g_coef[(size_t)HT_SLOTS * ((size_t)iy * g_nx + ix)];
+                for (int k = 0; k < HT_K64; ++k)
+                    blk[k] = make_double2(a[k].re.hi + a[k].re.lo, a[k].im.hi + a[k].im.lo);
+                float f[2 * HT_K32];
+                for (int j = 0; j < HT_K32; ++j) {
+                    const cdd& v = a[HT_K64 + j];
+                    f[2 * j] = (float)(v.re.hi + v.re.lo);
+                    f[2 * j + 1] = (float)(v.im.hi + v.im.lo);
+                }
+                std::memcpy(blk + HT_K64, f, sizeof f);
             }
             if (x <= g_re0 + 1e-12 || r < 2.5) break;
             cdd z0{mkdd(x), mkdd(y)};
@@ -204,6 +250,70 @@ const std::vector<double2>& hankel_anchor_host(int& nx, int& ny, double& re0, do
     return g_table;
 }
 
+const std::vector<double2>& hankel_coef_host() {
+    std::call_once(g_once, build);
+    return g_coef;
+}
+
+unsigned long long cuda_context_id() {
+    using GetCurrent = int (*)(void**);
+    using GetId = int (*)(void*, unsigned long long*);
+    static const std::pair<GetCurrent, GetId> fns = []() {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        const bool ok =
+            cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return std::pair<GetCurrent, GetId>(nullptr, nullptr);
+        }
+        return std::pair<GetCurrent, GetId>(reinterpret_cast<GetCurrent>(a), reinterpret_cast<GetId>(b));
+    }();
+    if (fns.first == nullptr || fns.second == nullptr) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (fns.first(&ctx) != 0 || ctx == nullptr || fns.second(ctx, &id) != 0) return 0;
+    return id;
+}
+
+namespace {
+constexpr int TAB_MAX_DEVICES = 64;
+std::mutex g_dev_mu;
+double2* g_dev_tab[TAB_MAX_DEVICES] = {};
+unsigned long long g_dev_ctx[TAB_MAX_DEVICES] = {};  // the context each copy was uploaded in
+}  // namespace
+
+bm_status hankel_table_device(int dev, const double2** out) {
+    *out = nullptr;
+    if (dev < 0 || dev >= TAB_MAX_DEVICES) {
+        bm_set_error("Hankel table: device index " + std::to_string(dev) + " out of range");
+        return BM_EINVAL;
+    }
+    const std::vector<double2>& tab = hankel_coef_host();
+    const unsigned long long ctx = cuda_context_id();
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    if (g_dev_tab[dev] == nullptr || ctx == 0 || ctx != g_dev_ctx[dev]) {
+        // a copy from an earlier (reset) context is not freed: its memory went with that context
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, tab.size() * sizeof(double2));
+        if (e == cudaSuccess) e = cudaMemcpy(p, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (p) cudaFree(p);
+            cudaGetLastError();
+            bm_set_error(std::string("Hankel table upload: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? BM_ENOMEM : BM_ECUDA;
+        }
+        g_dev_tab[dev] = static_cast<double2*>(p);
+        g_dev_ctx[dev] = ctx;
+    }
+    *out = g_dev_tab[dev];
+    return BM_OK;
+}
+
 extern "C" bm_status bm_hankel_anchor_table(double* out, int cap_anchors, int* nx, int* ny, double* re0,
                                             double* im0, double* step) {
     int a, b;
@@ -219,6 +329,30 @@ extern "C" bm_status bm_hankel_anchor_table(double* out, int cap_anchors, int* n
         for (size_t i = 0; i < t.size(); ++i) {
             out[2 * i] = t[i].x;
             out[2 * i + 1] = t[i].y;
+        }
+    }
+    return BM_OK;
+}
+
+extern "C" bm_status bm_hankel_taylor_table(double* out, int cap_anchors, int* nterms) {
+    int a, b;
+    double r0, i0, st;
+    hankel_anchor_host(a, b, r0, i0, st);
+    const std::vector<double2>& t = hankel_coef_host();
+    const int K = HT_K64 + HT_K32;
+    if (nterms) *nterms = K;
+    if (out) {
+        if (cap_anchors < a * b) return BM_EINVAL;
+        for (long q = 0; q < (long)a * b; ++q) {
+            const double2* blk = t.data() + (size_t)HT_SLOTS * q;
+            double* o = out + 2L * K * q;
+            for (int k = 0; k < HT_K64; ++k) {
+                o[2 * k] = blk[k].x;
+                o[2 * k + 1] = blk[k].y;
+            }
+            float f[2 * HT_K32];
+            std::memcpy(f, blk + HT_K64, sizeof f);
+            for (int j = 0; j < 2 * HT_K32; ++j) o[2 * HT_K64 + j] = (double)f[j];
         }
     }
     return BM_OK;

@@ -1,5 +1,5 @@
 """CPU checks of the C-ABI library: it builds, loads, exports every symbol include/bm.h declares,
-its host-built Hankel anchor table matches scipy and its high-order zeta weights match the
+its host-built Hankel anchor and Taylor tables match scipy and its high-order zeta weights match the
 oracle's, and its argument checks run before any device work (no GPU needed for any of this)."""
 import os
 import re
@@ -41,6 +41,33 @@ def test_anchor_table_matches_scipy(bmlib):
     e = np.maximum(np.abs(T[..., 0][used] - H0) / np.abs(H0), np.abs(T[..., 1][used] - H1) / np.abs(H1))
     assert used.sum() > 9000
     assert e.max() < 1e-14
+
+
+def test_taylor_table_reproduces_scipy(bmlib):
+    # the coefficients the device Taylor zone evaluates, summed by Horner's scheme with the
+    # derivative (H1 = -H0') at the nearest anchor, over the zone 3 <= |z| < 20, arg -70..60 deg
+    T, re0, im0, step = bmlib.bm_hankel_anchor_table()
+    A = bmlib.bm_hankel_taylor_table()
+    assert A.shape[:2] == T.shape[:2] and A.shape[2] >= 12
+    np.testing.assert_array_equal(A[..., 0], T[..., 0])       # a_0 = H0(z0)
+    np.testing.assert_array_equal(A[..., 1], -T[..., 1])      # a_1 = -H1(z0)
+    rng = np.random.default_rng(7)
+    r = np.concatenate([3.0 + 17.0 * rng.random(3000), [3.0, 19.999999]])
+    th = np.radians(rng.uniform(-70.0, 60.0, r.size))
+    z = r * np.exp(1j * th)
+    ix = np.rint((z.real - re0) / step).astype(int)
+    iy = np.rint((z.imag - im0) / step).astype(int)
+    d = z - (re0 + ix * step + 1j * (im0 + iy * step))
+    assert np.abs(d).max() <= step / np.sqrt(2) + 1e-12
+    c = A[iy, ix]
+    p = c[:, -1].copy()
+    q = np.zeros_like(p)
+    for k in range(c.shape[1] - 2, -1, -1):
+        q = q * d + p
+        p = p * d + c[:, k]
+    H0, H1 = sp.hankel1(0, z), sp.hankel1(1, z)
+    assert np.max(np.abs(p - H0) / np.abs(H0)) < 1e-14
+    assert np.max(np.abs(-q - H1) / np.abs(H1)) < 1e-14
 
 
 def test_create_without_gpu_reports_cuda_error(bmlib):
