@@ -5,7 +5,7 @@
 // Three zones by |z|, each accurate to about 1e-14 relative in |H|:
 //  * |z| < 3    : ascending series of J0, J1, Y0, Y1, summed while (|z|^2/4)^m/(m!)^2 > 1e-17
 //    (at most 14 terms).
-//  * 3 <= |z| < 20 : Taylor expansion about the nearest anchor z0 of a grid with spacing 1/4
+//  * 3 <= |z| < 80 : Taylor expansion about the nearest anchor z0 of a grid with spacing 1/4
 //    (|z - z0| <= 0.177).  The Taylor coefficients of H0 about z0 follow from Bessel's equation
 //    z^2 y'' + z y' + z^2 y = 0 written in delta = z - z0:
 //       z0^2 (k+1)(k+2) a_{k+2} = -[ z0 (k+1)(2k+1) a_{k+1} + (k^2 + z0^2) a_k
@@ -14,10 +14,12 @@
 //    (hankel_table.cu: ODE integration in double-double) holds a_0 .. a_18 for every anchor, so
 //    the device evaluates the polynomial and its derivative by Horner's scheme: 18 complex
 //    multiply-adds each, the nine of a_8 .. a_0 in FP64 (72 FP64 FMAs), the rest in FP32.
-//  * |z| >= 20  : Hankel's asymptotic expansion
+//  * |z| >= 80  : Hankel's asymptotic expansion
 //       H_nu(z) ~ sqrt(2/(pi z)) e^{i(z - nu pi/2 - pi/4)} sum_k i^k a_k(nu) / z^k,
 //       a_k(nu) = prod_{j=1..k} (4nu^2 - (2j-1)^2) / (k! 8^k),
-//    summed until the terms fall below 1e-17 (at most 40 terms; about 20 at |z| = 20).
+//    summed until the terms fall below 1e-17 (at most 40 terms; about 9 at |z| = 80).  A Horner
+//    pass costs about a quarter of the FP64 work of this zone (two complex reciprocals, a complex
+//    root, FP64 sincos and exp), which is why the Taylor table reaches out to |z| = 80.
 // GB300 runs FP64 at 1/64 of its FP32 rate, and the series terms fall fast: past the first six
 // terms of the asymptotic series (|a_7 / z^7| < 1e-8 for |z| >= 20), the first nine of the Taylor
 // one (relative 3e-11 for H0, 2e-9 for the differentiated H1) and the first nine of the ascending
@@ -30,7 +32,7 @@
 namespace hk {
 
 constexpr double R_SERIES = 3.0;
-constexpr double R_ASYM = 20.0;
+constexpr double R_ASYM = 80.0;
 constexpr double EULER_GAMMA = 0.57721566490153286060651209008240243;
 constexpr double TWO_OVER_PI = 0.63661977236758134307553505349005745;
 constexpr double ONE_OVER_PI = 0.31830988618379067153776752674502872;
@@ -196,9 +198,9 @@ __device__ __forceinline__ void asym(double2 z, double2& h0, double2& h1) {
 }
 
 __device__ __forceinline__ void hankel01(double2 z, const HankelTable& T, double2& h0, double2& h1) {
-    double r = hypot(z.x, z.y);
-    if (r < R_SERIES) series(z, h0, h1);
-    else if (r < R_ASYM) taylor(z, T, h0, h1);
+    const double r2 = z.x * z.x + z.y * z.y;
+    if (r2 < R_SERIES * R_SERIES) series(z, h0, h1);
+    else if (r2 < R_ASYM * R_ASYM) taylor(z, T, h0, h1);
     else asym(z, h0, h1);
 }
 

@@ -1,15 +1,16 @@
 // Host construction of the Hankel anchor table used by the device Taylor zone (hankel.cuh).
 //
-// Anchors z0 = re0 + ix*step + i (im0 + iy*step), step = 1/4, cover Re z0 in [0, 20.5] and
-// Im z0 in [-20.5, 20.5]; each stores (H0^(1)(z0), H1^(1)(z0)).  Values are produced without
-// special-function libraries: along each grid row (fixed Im z0 = y) start at a point with
-// |z| >= 21, where Hankel's asymptotic expansion is accurate to a few units of FP64 rounding,
-// and integrate Bessel's equation z^2 y'' + z y' + z^2 y = 0 leftwards in steps of -1/4 with
-// Taylor series summed in double-double arithmetic (about 32 digits), down to |z| < 2.5 or
-// Re z = 0.  Along a row the second solution H^(2) keeps a fixed size ratio e^{2y} to H^(1),
-// so the start error neither grows nor is amplified; every anchor is accurate to about 1e-16
-// relative.  Only anchors with 2.5 <= |z0| <= 21 are filled (the Taylor zone uses
-// 3 <= |z| < 20 and the nearest anchor is within 0.177).
+// Anchors z0 = re0 + ix*step + i (im0 + iy*step), step = 1/4, cover Re z0 in [0, 81] and
+// Im z0 in [-81, 81]; each stores (H0^(1)(z0), H1^(1)(z0)).  Values are produced without
+// special-function libraries.  For 21 < |z0| <= 81, Hankel's asymptotic expansion is accurate to a
+// few units of FP64 rounding and gives them directly.  Inside, along each grid row (fixed
+// Im z0 = y) start at a point with |z| >= 21 and integrate Bessel's equation
+// z^2 y'' + z y' + z^2 y = 0 leftwards in steps of -1/4 with Taylor series summed in
+// double-double arithmetic (about 32 digits), down to |z| < 2.5 or Re z = 0.  Along a row the
+// second solution H^(2) keeps a fixed size ratio e^{2y} to H^(1), so the start error neither
+// grows nor is amplified; every anchor is accurate to about 1e-16 relative.  Only anchors with
+// 2.5 <= |z0| <= 81 are filled (the Taylor zone uses 3 <= |z| < 80 and the nearest anchor is
+// within 0.177).  Rows are built in parallel on the host's cores.
 //
 // For the device, every filled anchor also gets the Taylor coefficients a_0 .. a_18 of H0 about it
 // (a_0 = H0(z0), a_1 = H0'(z0) = -H1(z0), the rest by the recurrence Bessel's equation gives in
@@ -17,14 +18,18 @@
 // rounded once: the device then evaluates H0(z0 + d) and H1 = -H0' by Horner's scheme.  Relative to
 // a_0, |a_k| 0.177^k < 3e-11 from k = 9 on (at |z0| = 2.8, and smaller further out; the derivative
 // scales term k by k/0.177), so a_9 .. a_18 are kept in FP32, and at k = 19 the terms are below
-// 1e-19 of the sum.
+// 1e-19 of the sum.  In the device's domain (arg z in [-70, 60] degrees) |H0| stays within
+// [1e-31, 1e32], so the FP32 coefficients neither overflow nor lose more than terms below 1e-22.
 #include "common.cuh"
 
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <algorithm>
 #include <string>
+#include <thread>
 #include <utility>
+#include <vector>
 
 namespace {
 
@@ -194,48 +199,74 @@ void taylor_coefs(cdd z0, cdd y, cdd yp, cdd* a, int n) {
 std::vector<double2> g_table;
 std::vector<double2> g_coef;
 int g_nx = 0, g_ny = 0;
-const double g_step = 0.25, g_re0 = 0.0, g_im0 = -20.5;
+constexpr double R_ODE = 21.0;  // anchors inside come from the ODE integration
+constexpr double R_TAB = 81.0;  // table radius (the device Taylor zone ends at |z| = 80)
+const double g_step = 0.25, g_re0 = 0.0, g_im0 = -R_TAB;
 std::once_flag g_once;
 
+// Fills anchor (ix, iy) at z0 = x + i y from y = H0(z0), yp = H0'(z0): the anchor pair and the
+// Taylor coefficient block.
+void store(int iy, int ix, double x, double y, cdd Y, cdd Yp) {
+    size_t o = 2 * ((size_t)iy * g_nx + ix);
+    g_table[o] = make_double2(Y.re.hi + Y.re.lo, Y.im.hi + Y.im.lo);
+    g_table[o + 1] = make_double2(-(Yp.re.hi + Yp.re.lo), -(Yp.im.hi + Yp.im.lo));
+    cdd a[HT_K64 + HT_K32];
+    taylor_coefs(cdd{mkdd(x), mkdd(y)}, Y, Yp, a, HT_K64 + HT_K32);
+    double2* blk = &g_coef[(size_t)HT_SLOTS * ((size_t)iy * g_nx + ix)];
+    for (int k = 0; k < HT_K64; ++k) blk[k] = make_double2(a[k].re.hi + a[k].re.lo, a[k].im.hi + a[k].im.lo);
+    float f[2 * HT_K32];
+    for (int j = 0; j < HT_K32; ++j) {
+        const cdd& v = a[HT_K64 + j];
+        f[2 * j] = (float)(v.re.hi + v.re.lo);
+        f[2 * j + 1] = (float)(v.im.hi + v.im.lo);
+    }
+    std::memcpy(blk + HT_K64, f, sizeof f);
+}
+
+// One grid row (fixed Im z0 = y): the anchors with R_ODE < |z0| <= R_TAB straight from Hankel's
+// asymptotic expansion, then those with 2.5 <= |z0| <= R_ODE by integrating Bessel's equation
+// leftwards from the first grid point with |z| >= R_ODE.
+void build_row(int iy) {
+    const double y = g_im0 + iy * g_step;
+    for (int ix = 0; ix < g_nx; ++ix) {
+        const double x = g_re0 + ix * g_step;
+        const double r = std::hypot(x, y);
+        if (r <= R_ODE + 1e-12 || r > R_TAB + 1e-12) continue;
+        cd h0, h1;
+        asym_start(x, y, h0, h1);
+        store(iy, ix, x, y, cdd{mkdd(h0.re), mkdd(h0.im)}, cdd{mkdd(-h1.re), mkdd(-h1.im)});
+    }
+    double xs = std::ceil(std::sqrt(std::fmax(0.0, R_ODE * R_ODE - y * y)) / g_step) * g_step;
+    cd h0, h1;
+    asym_start(xs, y, h0, h1);
+    cdd Y{mkdd(h0.re), mkdd(h0.im)};
+    cdd Yp{mkdd(-h1.re), mkdd(-h1.im)};  // H0' = -H1
+    double x = xs;
+    while (true) {
+        int ix = (int)std::lround((x - g_re0) / g_step);
+        double r = std::hypot(x, y);
+        if (ix < g_nx && r <= R_ODE + 1e-12) store(iy, ix, x, y, Y, Yp);
+        if (x <= g_re0 + 1e-12 || r < 2.5) break;
+        cdd z0{mkdd(x), mkdd(y)};
+        taylor_step(z0, -g_step, Y, Yp);
+        x -= g_step;
+    }
+}
+
 void build() {
-    g_nx = 83;   // Re 0 .. 20.5
-    g_ny = 165;  // Im -20.5 .. 20.5
+    g_nx = (int)std::lround((R_TAB - g_re0) / g_step) + 1;   // Re 0 .. R_TAB
+    g_ny = (int)std::lround(-2.0 * g_im0 / g_step) + 1;      // Im -R_TAB .. R_TAB
     g_table.assign((size_t)g_nx * g_ny * 2, make_double2(0.0, 0.0));
     g_coef.assign((size_t)g_nx * g_ny * HT_SLOTS, make_double2(0.0, 0.0));
-    for (int iy = 0; iy < g_ny; ++iy) {
-        double y = g_im0 + iy * g_step;
-        double xs = std::ceil(std::sqrt(std::fmax(0.0, 21.0 * 21.0 - y * y)) / g_step) * g_step;
-        cd h0, h1;
-        asym_start(xs, y, h0, h1);
-        cdd Y{mkdd(h0.re), mkdd(h0.im)};
-        cdd Yp{mkdd(-h1.re), mkdd(-h1.im)};  // H0' = -H1
-        double x = xs;
-        while (true) {
-            int ix = (int)std::lround((x - g_re0) / g_step);
-            double r = std::hypot(x, y);
-            if (ix < g_nx && r <= 21.0 + 1e-12) {
-                size_t o = 2 * ((size_t)iy * g_nx + ix);
-                g_table[o] = make_double2(Y.re.hi + Y.re.lo, Y.im.hi + Y.im.lo);
-                g_table[o + 1] = make_double2(-(Yp.re.hi + Yp.re.lo), -(Yp.im.hi + Yp.im.lo));
-                cdd a[HT_K64 + HT_K32];
-                taylor_coefs(cdd{mkdd(x), mkdd(y)}, Y, Yp, a, HT_K64 + HT_K32);
-                double2* blk = &g_coef[(size_t)HT_SLOTS * ((size_t)iy * g_nx + ix)];
-                for (int k = 0; k < HT_K64; ++k)
-                    blk[k] = make_double2(a[k].re.hi + a[k].re.lo, a[k].im.hi + a[k].im.lo);
-                float f[2 * HT_K32];
-                for (int j = 0; j < HT_K32; ++j) {
-                    const cdd& v = a[HT_K64 + j];
-                    f[2 * j] = (float)(v.re.hi + v.re.lo);
-                    f[2 * j + 1] = (float)(v.im.hi + v.im.lo);
-                }
-                std::memcpy(blk + HT_K64, f, sizeof f);
-            }
-            if (x <= g_re0 + 1e-12 || r < 2.5) break;
-            cdd z0{mkdd(x), mkdd(y)};
-            taylor_step(z0, -g_step, Y, Yp);
-            x -= g_step;
-        }
-    }
+    // rows are independent and write disjoint parts of the tables
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nt = (int)std::max(1u, std::min(hw, 32u));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([t, nt]() {
+            for (int iy = t; iy < g_ny; iy += nt) build_row(iy);
+        });
+    for (auto& x : th) x.join();
 }
 
 }  // namespace
