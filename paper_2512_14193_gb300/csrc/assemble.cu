@@ -16,6 +16,7 @@
 // Blocks (Theorem thm:LU): M13 = -S1, M23 = -(D*1 + I/2)/eps1, M31 = D0 - I/2 + beta N0,
 // M32 = -eps0 (S0 + beta (D*0 + I/2)); ordinary (Eq. dis_BM, (2,2) block -eps1 S1):
 // [M31, M32; D1 + I/2, -eps1 S1].
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -324,50 +325,117 @@ __global__ void plane_wave_kernel(const double* __restrict__ g, int N, double2 k
     B[r + (long)c * ldb] = val;
 }
 
-// far field: one block per (angle m, column c)
-__global__ void far_field_kernel(const double* __restrict__ g, int N, double2 k0, double2 eps0,
-                                 const double2* __restrict__ X, long ldx, const double* __restrict__ ang, int M,
-                                 double2* U, long ldu) {
-    int m = blockIdx.x, c = blockIdx.y;
-    double sa, ca;
-    sincos(ang[m], &sa, &ca);
-    const double2* u = X + (long)c * ldx;
-    const double2* q = u + N;
-    double2 acc = make_double2(0, 0);
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        double s = ca * g[j] + sa * g[N + j];
-        double xn = ca * g[2 * N + j] + sa * g[3 * N + j];
-        double w = g[6 * N + j];
-        // e = exp(-i k0 s)
-        double e = exp(k0.y * s), sn, cs;
-        sincos(-k0.x * s, &sn, &cs);
-        double2 ph = make_double2(e * cs, e * sn);
-        double2 t = cscale(cmul(cmuli(k0), u[j]), -xn);      // -i k0 (xhat.nu) u
-        t = csub(t, cmul(eps0, q[j]));
-        acc = cadd(acc, cscale(cmul(t, ph), w));
+// Far field: U[m, c] = c0 sum_j w_j e^{-i k0 xhat_m . y_j} [(-i k0 xhat_m . nu_j) u_jc - eps0 q_jc],
+// c0 = e^{i pi/4} / sqrt(8 pi k0).  A contraction over the nodes: with the weighted phases
+// P_mj = w_j e^{-i k0 xhat_m . y_j}, U = c0 (Au X_u + Aq X_q), Au_mj = -i k0 (xhat_m . nu_j) P_mj,
+// Aq_mj = -eps0 P_mj.  CTA: FF_MT = 8 angles x up to FF_CT = 128 right-hand sides x one of S node
+// slices (S = the cluster size).  Per 32-node chunk the 8 x 32 phases (one FP64 exp and sincos
+// each) are formed once, one per thread, and serve every column; each thread keeps the sums of one
+// angle and columns oc, oc + 32, ...  The S slices' partial sums are added in rank order through
+// distributed shared memory (deterministic, no workspace).
+constexpr int FF_MT = 8, FF_JT = 32, FF_CT = 128, FF_THREADS = 256;
+constexpr int FF_OUT = FF_MT * FF_CT / FF_THREADS;  // sums per thread
+
+__device__ __forceinline__ double2 ld_cluster_d2(const double2* p, int rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    double2 v;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(r) : "memory");
+    return v;
+}
+__device__ __forceinline__ void ff_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(FF_THREADS) far_field_kernel(const double* __restrict__ g, int N, double2 k0,
+                                                               double2 eps0, const double2* __restrict__ X, long ldx,
+                                                               const double* __restrict__ ang, int M, int nrhs,
+                                                               double2* U, long ldu) {
+    extern __shared__ double2 ffs[];
+    const int S = (int)gridDim.x, z = (int)blockIdx.x;  // node slice = rank in the cluster
+    const int m0 = (int)blockIdx.y * FF_MT, c0 = (int)blockIdx.z * FF_CT;
+    const int nc = min(FF_CT, nrhs - c0), ncp = nc + 1;  // padded row of the X chunk
+    double2* sAu = ffs;                   // [FF_JT][FF_MT]
+    double2* sAq = sAu + FF_JT * FF_MT;   // [FF_JT][FF_MT]
+    double2* sXu = sAq + FF_JT * FF_MT;   // [FF_JT][ncp]
+    double2* sXq = sXu + FF_JT * ncp;     // [FF_JT][ncp]
+    const int t = (int)threadIdx.x;
+    const int om = t % FF_MT, oc = t / FF_MT;  // this thread's angle (phases and sums) and first column
+    const int pj = t / FF_MT;                  // this thread's node within a chunk (phases)
+    const bool mok = m0 + om < M;
+    double sa = 0.0, ca = 0.0;
+    if (mok) sincos(ang[m0 + om], &sa, &ca);
+    double2 acc[FF_OUT];
+#pragma unroll
+    for (int i = 0; i < FF_OUT; ++i) acc[i] = make_double2(0.0, 0.0);
+    const int jb = (int)((long)z * N / S), je = (int)((long)(z + 1) * N / S);
+    for (int jc = jb; jc < je; jc += FF_JT) {
+        const int nj = min(FF_JT, je - jc);
+        __syncthreads();  // the previous chunk has been read
+        {
+            double2 au = make_double2(0.0, 0.0), aq = au;
+            if (mok && pj < nj) {
+                const int j = jc + pj;
+                const double sx = ca * g[j] + sa * g[N + j];
+                const double xn = ca * g[2 * N + j] + sa * g[3 * N + j];
+                const double e = exp(k0.y * sx) * g[6 * N + j];
+                double sn, cs;
+                sincos(-k0.x * sx, &sn, &cs);
+                const double2 ph = make_double2(e * cs, e * sn);  // w_j e^{-i k0 s}
+                au = cscale(cmul(cmuli(k0), ph), -xn);            // -i k0 (xhat . nu) w_j e^{-i k0 s}
+                aq = cneg(cmul(eps0, ph));
+            }
+            sAu[pj * FF_MT + om] = au;
+            sAq[pj * FF_MT + om] = aq;
+        }
+        for (int q = t; q < FF_JT * nc; q += FF_THREADS) {
+            const int jj = q % FF_JT, cc = q / FF_JT;
+            double2 u = make_double2(0.0, 0.0), v = u;
+            if (jj < nj) {
+                const double2* col = X + (long)(c0 + cc) * ldx + jc + jj;
+                u = col[0];
+                v = col[N];
+            }
+            sXu[jj * ncp + cc] = u;
+            sXq[jj * ncp + cc] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int jj = 0; jj < FF_JT; ++jj) {
+            const double2 a = sAu[jj * FF_MT + om], b = sAq[jj * FF_MT + om];
+#pragma unroll
+            for (int i = 0; i < FF_OUT; ++i) {
+                const int cc = oc + 32 * i;
+                if (cc < nc) {
+                    const double2 u = sXu[jj * ncp + cc], v = sXq[jj * ncp + cc];
+                    acc[i].x = fma(a.x, u.x, fma(-a.y, u.y, fma(b.x, v.x, fma(-b.y, v.y, acc[i].x))));
+                    acc[i].y = fma(a.x, u.y, fma(a.y, u.x, fma(b.x, v.y, fma(b.y, v.x, acc[i].y))));
+                }
+            }
+        }
     }
-    __shared__ double2 red[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    }
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[warp] = acc;
+    // this slice's partial sums into shared memory (o = column * 8 + angle), then rank z adds the
+    // slices of its share of the outputs in rank order
     __syncthreads();
-    if (warp == 0) {
-        int nw = blockDim.x >> 5;
-        acc = lane < nw ? red[lane] : make_double2(0, 0);
-        for (int o = 16; o > 0; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-        }
-        if (lane == 0) {
-            // c0 = e^{i pi/4} / sqrt(8 pi k0)
-            double2 kk = hk::csqrt(cscale(k0, 8.0 * PI));
-            double2 c0 = cmul(make_double2(0.70710678118654752440, 0.70710678118654752440), cinv(kk));
-            U[m + (long)c * ldu] = cmul(c0, acc);
-        }
+    double2* sP = sXu;
+#pragma unroll
+    for (int i = 0; i < FF_OUT; ++i) {
+        const int cc = oc + 32 * i;
+        if (cc < nc) sP[cc * FF_MT + om] = acc[i];
     }
+    ff_cluster_sync();
+    const double2 kk = hk::csqrt(cscale(k0, 8.0 * PI));
+    const double2 cpre = cmul(make_double2(0.70710678118654752440, 0.70710678118654752440), cinv(kk));
+    const int nout = FF_MT * nc;
+    for (int o = z * FF_THREADS + t; o < nout; o += S * FF_THREADS) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int r = 0; r < S; ++r) sum = cadd(sum, ld_cluster_d2(sP + o, r));
+        const int m = m0 + o % FF_MT, cc = c0 + o / FF_MT;
+        if (m < M) U[m + (long)cc * ldu] = cmul(cpre, sum);
+    }
+    ff_cluster_sync();  // no CTA leaves while another still reads its shared memory
 }
 
 __global__ void hankel_probe_kernel(const double2* __restrict__ z, int n, HankelTable T, double2* h0, double2* h1) {
@@ -800,9 +868,38 @@ cudaError_t launch_plane_wave(cudaStream_t s, const bm_ctx* c, const double* d_a
 
 cudaError_t launch_far_field(cudaStream_t s, const bm_ctx* c, const double2* X, long ldx, int nrhs, const double* d_ang,
                              int M, double2* U, long ldu) {
-    dim3 grid(M, nrhs);
-    far_field_kernel<<<grid, 256, 0, s>>>(c->d_geom, c->N, c->k0, c->eps0, X, ldx, d_ang, M, U, ldu);
-    return cudaGetLastError();
+    const int at = ceil_div(M, FF_MT), ct = ceil_div(nrhs, FF_CT);
+    // node slices per cluster: enough CTAs for about two per SM, at most 8 (portable clusters), at
+    // least a chunk of nodes per slice
+    int S = 1;
+    while (S < 8 && (long)at * ct * S < 2L * c->num_sms && 2L * S * FF_JT <= c->N) S *= 2;
+    const int cmax = std::min(nrhs, FF_CT);
+    const size_t smem = (size_t)(2 * FF_JT * FF_MT + 2 * FF_JT * (cmax + 1)) * sizeof(double2);
+    if (at > 65535) return cudaErrorInvalidConfiguration;  // more than 524280 angles in one call
+    // the shared-memory limit is a per-device attribute of the kernel (idempotent, so a race between
+    // host threads only sets it twice)
+    static bool attr[64] = {};
+    const bool known = c->device >= 0 && c->device < 64;
+    if (!known || !attr[c->device]) {
+        cudaError_t e = cudaFuncSetAttribute(far_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)((2 * FF_JT * FF_MT + 2 * FF_JT * (FF_CT + 1)) * sizeof(double2)));
+        if (e != cudaSuccess) return e;
+        if (known) attr[c->device] = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(S, at, ct);
+    cfg.blockDim = dim3(FF_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeClusterDimension;
+    la[0].val.clusterDim.x = S;
+    la[0].val.clusterDim.y = 1;
+    la[0].val.clusterDim.z = 1;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, far_field_kernel, c->d_geom, c->N, c->k0, c->eps0, X, ldx, d_ang, M, nrhs, U,
+                              ldu);
 }
 
 cudaError_t launch_hankel_probe(cudaStream_t s, const bm_ctx* c, const double2* z, int n, double2* h0, double2* h1) {
