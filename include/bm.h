@@ -391,6 +391,12 @@ bm_status bm_copy_block(bm_ctx* ctx, int which, bm_c64* dst, int ldd, int on_dev
  * on_device, else host arrays. */
 bm_status bm_hankel01(bm_ctx* ctx, const bm_c64* z, int n, bm_c64* h0, bm_c64* h1, int on_device);
 
+/* Run the device's integer FP64 -> FP32 rounding (used where the operator's magnitudes are formed
+ * in FP32, e.g. its row norms) on n host values x: rn[i] = x[i] rounded to the nearest FP32, ties to
+ * even, formed from the bit pattern by integer operations.  This call exposes it so it can be
+ * compared with the IEEE conversion.  Both arrays are host arrays. */
+bm_status bm_f32_convert(bm_ctx* ctx, const double* x, int n, float* rn);
+
 /* Host copy of the anchor table the device Taylor zone of bm_hankel01 expands about:
  * H0^(1)(z0), H1^(1)(z0) at z0 = re0 + ix*step + i (im0 + iy*step), stored as
  * out[4*(iy*nx + ix) + {0,1,2,3}] = {Re H0, Im H0, Re H1, Im H1}; anchors outside the annulus

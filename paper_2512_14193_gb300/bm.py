@@ -125,6 +125,7 @@ def lib():
     L.bm_hankel_anchor_table.argtypes = [C.POINTER(D), I, C.POINTER(I), C.POINTER(I), C.POINTER(D), C.POINTER(D),
                                          C.POINTER(D)]
     L.bm_hankel_taylor_table.argtypes = [C.POINTER(D), I, C.POINTER(I)]
+    L.bm_f32_convert.argtypes = [P, P, I, P]
     L.bm_memory.argtypes = [P, C.POINTER(S), C.POINTER(S)]
     L.bm_kernel_launches.argtypes = [P, C.POINTER(C.c_ulonglong)]
     L.bm_enqueue_probe.argtypes = [P, I, I]
@@ -138,7 +139,8 @@ def lib():
                  "bm_far_field",
                  "bm_far_field_static", "bm_ssm", "bm_server_create", "bm_server_submit", "bm_server_wait",
                  "bm_server_stats_get", "bm_server_destroy",
-                 "bm_copy_block", "bm_hankel01", "bm_hankel_anchor_table", "bm_hankel_taylor_table", "bm_zeta_weights",
+                 "bm_copy_block", "bm_hankel01", "bm_f32_convert", "bm_hankel_anchor_table", "bm_hankel_taylor_table",
+                 "bm_zeta_weights",
                  "bm_memory",
                  "bm_destroy",
                  "bm_kernel_launches", "bm_enqueue_probe", "bm_profile", "bm_ssm_release"):
@@ -454,6 +456,15 @@ def bm_zeta_weights(p: int):
     _check(lib().bm_zeta_weights(int(p), tau.ctypes.data_as(C.POINTER(C.c_double)),
                                  c2.ctypes.data_as(C.POINTER(C.c_double))), "bm_zeta_weights")
     return tau, c2
+
+
+def bm_f32_convert(h, x):
+    """float32 array: the device's integer FP64 -> FP32 rounding (nearest, ties to even) of x."""
+    xs = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    _need(xs.size >= 1, "x must not be empty")
+    rn = np.zeros(xs.size, dtype=np.float32)
+    _check(lib().bm_f32_convert(h, xs.ctypes.data, int(xs.size), rn.ctypes.data), "bm_f32_convert")
+    return rn
 
 
 def bm_hankel_anchor_table():

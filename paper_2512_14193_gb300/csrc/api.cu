@@ -1353,6 +1353,32 @@ extern "C" bm_status bm_hankel01(bm_ctx* c, const bm_c64* z, int n, bm_c64* h0, 
     return BM_OK;
 }
 
+extern "C" bm_status bm_f32_convert(bm_ctx* c, const double* x, int n, float* rn) {
+    if (c == nullptr || x == nullptr || rn == nullptr || n < 1) return BM_EINVAL;
+    BM_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    double* dx = nullptr;
+    float* df = nullptr;
+    bm_status st = alloc_t(c, &dx, (size_t)n * 8);
+    if (st == BM_OK) st = alloc_t(c, &df, (size_t)n * 4);
+    if (st != BM_OK) {
+        ctx_free(c, dx);
+        return st;
+    }
+    cudaMemcpyAsync(dx, x, (size_t)n * 8, cudaMemcpyHostToDevice, s);
+    cudaError_t e = launch_f32_convert(s, dx, n, df);
+    c->launches += 1;
+    if (e == cudaSuccess) cudaMemcpyAsync(rn, df, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    ctx_free(c, dx);
+    ctx_free(c, df);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        bm_set_error(std::string("f32 convert probe: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return BM_ECUDA;
+    }
+    return BM_OK;
+}
+
 // ------------------------------------------------------------------------------------------------
 extern "C" bm_status bm_profile(bm_ctx* c, int nrhs, const bm_c64* B, int ldb, bm_c64* X, int ldx, int on_device,
                                 bm_kernel_time* out, int cap, int* count) {

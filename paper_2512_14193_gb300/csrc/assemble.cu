@@ -273,18 +273,42 @@ __device__ __forceinline__ void atomic_max_pos(double* p, double v) {
 }
 // max over rows of (add + sum_j |A(i, j)|) into *out (an infinity-norm term of the backward error).
 // CTA: 32 consecutive rows (lane = row, so every load instruction reads 32 consecutive entries),
-// its 8 warps taking every 8th column; the modulus is sqrt in FP32 of the FP64 sum of squares (a
-// relative 1e-7, ample for a norm that only scales the backward error), the sums in FP64.
+// its 8 warps taking every 8th column, eight loads in flight per thread.  The moduli are formed in
+// FP32 from the entries rounded to FP32 (by integer operations: the FP64 pipe is narrow) and each
+// thread sums its columns in FP32, the eight warps' sums added in FP64: a relative error of a few
+// 1e-6 at most, ample for a norm that only scales the backward error.
 __global__ void __launch_bounds__(256) rownorm_kernel(const double2* __restrict__ A, long ld, int m, int ncols,
                                                       double add, double* out) {
     __shared__ double part[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
-    double s = 0.0;
+    float sf = 0.f;
     if (i < m) {
+        const double2* a = A + i;
+        int j = warp;
+        for (; j + 56 < ncols; j += 64) {
+            double2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = a[(long)(j + 8 * u) * ld];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float x = f32_rn(v[u].x), y = f32_rn(v[u].y);
+                sf += sqrtf(fmaf(x, x, y * y));
+            }
+        }
+        for (; j < ncols; j += 8) {
+            const double2 v = a[(long)j * ld];
+            const float x = f32_rn(v.x), y = f32_rn(v.y);
+            sf += sqrtf(fmaf(x, x, y * y));
+        }
+    }
+    // FP32 overflow (entries above ~1e19) falls back to the FP64 modulus for this thread's row
+    double s = (double)sf;
+    if (!isfinite(sf) && i < m) {
+        s = 0.0;
         for (int j = warp; j < ncols; j += 8) {
             const double2 v = A[i + (long)j * ld];
-            s += (double)sqrtf((float)fma(v.x, v.x, v.y * v.y));
+            s += hypot(v.x, v.y);
         }
     }
     part[warp][lane] = s;
@@ -900,6 +924,16 @@ cudaError_t launch_far_field(cudaStream_t s, const bm_ctx* c, const double2* X, 
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, far_field_kernel, c->d_geom, c->N, c->k0, c->eps0, X, ldx, d_ang, M, nrhs, U,
                               ldu);
+}
+
+__global__ void f32_convert_kernel(const double* __restrict__ x, int n, float* rn) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rn[i] = f32_rn(x[i]);
+}
+
+cudaError_t launch_f32_convert(cudaStream_t s, const double* x, int n, float* rn) {
+    f32_convert_kernel<<<ceil_div(n, 256), 256, 0, s>>>(x, n, rn);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hankel_probe(cudaStream_t s, const bm_ctx* c, const double2* z, int n, double2* h0, double2* h1) {

@@ -61,6 +61,27 @@ BM_HD void cfma(float2& a, float2 b, float2 c) {
     a.y = fmaf(b.x, c.y, fmaf(b.y, c.x, a.y));
 }
 
+// ---------------------------------------------------------------------------------------------
+// f32_rn(x) = (float)x rounded to nearest even (IEEE 754 binary64 -> binary32), by integer
+// arithmetic on the bit pattern, for kernels whose other work is FP32 and integer (the row norms);
+// it falls back to the hardware conversion where the result would not be a normal FP32 number
+// (zero, results below 2^-126 or from 2^127 on, infinities, NaN).  Measured: the packing kernels
+// were not faster with it (nor with an integer double-float split) than with the hardware
+// conversion, so they keep the latter.
+#ifdef __CUDACC__
+__device__ __forceinline__ float f32_rn(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int e = (int)((hi >> 20) & 0x7FF) - 1023 + 127;  // binary32 biased exponent
+    if (e < 1 || e > 253) return (float)x;
+    const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // top 23 of the 52 mantissa bits
+    const unsigned rest = lo & 0x1FFFFFFFu;                  // the 29 bits dropped
+    unsigned f = ((unsigned)e << 23) | m;
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;  // a carry moves to the exponent
+    return __uint_as_float(f | (hi & 0x80000000u));
+}
+#endif
+
 template <class R> struct cplx_of;
 template <> struct cplx_of<double> { using type = double2; };
 template <> struct cplx_of<float> { using type = float2; };

@@ -13,6 +13,7 @@ cudaError_t launch_plane_wave(cudaStream_t s, const bm_ctx* c, const double* d_a
 cudaError_t launch_far_field(cudaStream_t s, const bm_ctx* c, const double2* X, long ldx, int nrhs, const double* d_ang,
                              int M, double2* U, long ldu);
 cudaError_t launch_hankel_probe(cudaStream_t s, const bm_ctx* c, const double2* z, int n, double2* h0, double2* h1);
+cudaError_t launch_f32_convert(cudaStream_t s, const double* x, int n, float* rn);
 cudaError_t launch_pack_schur(cudaStream_t s, const bm_ctx* c, int split);  // Schur operands (in bm_factor)
 cudaError_t launch_pack_solve(cudaStream_t s, const bm_ctx* c, int split);  // [M13; M23] rows (assembly)
 cudaError_t launch_to_c32(cudaStream_t s, const double2* A, long lda, int m, int n, float* Fr, float* Fi, long ldf);

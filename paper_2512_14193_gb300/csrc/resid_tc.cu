@@ -410,12 +410,28 @@ __global__ void row_max_kernel(const double2* __restrict__ A, long lda, int rows
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows) return;
     const int j0 = blockIdx.y * 256, j1 = min(K, j0 + 256);
-    double m = 0.0;
-    for (int j = j0; j < j1; ++j) {
-        const double2 v = A[i + (long)j * lda];
-        m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    // |Re|, |Im| as bit patterns with the sign cleared (integer maximum: FP64 compares run on the
+    // narrow FP64 pipe).  NaN patterns (above that of infinity) count as zero, as fmax would skip them.
+    constexpr unsigned long long MAG = 0x7FFFFFFFFFFFFFFFull, INF = 0x7FF0000000000000ull;
+    auto mag = [](double d) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(d) & MAG;
+        return b > INF ? 0ull : b;
+    };
+    unsigned long long m = 0;
+    const double2* a = A + i;
+    int j = j0;
+    for (; j + 8 <= j1; j += 8) {
+        double2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = a[(long)(j + u) * lda];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m = max(m, max(mag(v[u].x), mag(v[u].y)));
     }
-    atomicMax(mx + i, (unsigned long long)__double_as_longlong(m));
+    for (; j < j1; ++j) {
+        const double2 v = a[(long)j * lda];
+        m = max(m, max(mag(v.x), mag(v.y)));
+    }
+    atomicMax(mx + i, m);
 }
 // e_i with max_j max(|Re|, |Im|) < 2^(e_i - 1) (0 for a zero row)
 __global__ void row_exponent_kernel(const unsigned long long* __restrict__ mx, int rows, int* __restrict__ e) {

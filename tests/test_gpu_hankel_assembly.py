@@ -11,8 +11,10 @@ import oracle as O
 
 
 def _zpoints():
+    # every zone and both sides of each boundary (series | Taylor at 3, Taylor | asymptotic at 80)
     r = np.concatenate([np.geomspace(1e-5, 2.99, 40), [2.9999999, 3.0, 3.0000001], np.linspace(3.01, 19.99, 120),
-                        [19.9999999, 20.0, 20.0000001], np.geomspace(20.01, 600.0, 40)])
+                        [19.9999999, 20.0, 20.0000001], np.linspace(20.01, 79.99, 120),
+                        [79.9999999, 80.0, 80.0000001], np.geomspace(80.01, 600.0, 30)])
     ang = np.deg2rad([-70.0, -30.0, -10.0, -2.0, 0.0, 3.0, 20.0, 45.0, 60.0])
     z = (r[:, None] * np.exp(1j * ang[None, :])).ravel()
     return z[np.abs(z.imag) <= 60.0]
@@ -27,6 +29,25 @@ def test_device_hankel_all_zones(bmlib, handle):
     e1 = np.abs(h1 - r1) / np.abs(r1)
     worst = np.argmax(np.maximum(e0, e1))
     assert max(e0.max(), e1.max()) < 2e-14, (z[worst], e0[worst], e1[worst])
+
+
+@pytest.mark.gpu
+def test_device_fp32_conversions_match_ieee(bmlib, handle):
+    # the integer FP64 -> FP32 rounding (row norms) against numpy's IEEE conversion: random
+    # magnitudes over the FP32 range and beyond, ties and near-ties of the 29 dropped bits, binade
+    # and range edges, values whose result is subnormal or overflows (the fallback path)
+    rng = np.random.default_rng(13)
+    x = [rng.standard_normal(100000) * 10.0 ** rng.uniform(-45, 40, 100000)]
+    base = (rng.standard_normal(4000) * 10.0 ** rng.uniform(-30, 30, 4000)).view(np.uint64) & ~np.uint64((1 << 29) - 1)
+    for off in (0, 1, (1 << 28) - 1, 1 << 28, (1 << 28) + 1, (1 << 29) - 1):
+        x.append((base | np.uint64(off)).view(np.float64))
+    x.append(np.array([0.0, -0.0, 1.0, -1.0, 3.4e38, 1.1754943508222875e-38, 1e-39, 1e-45, 1e-300,
+                       2.0 ** -126, 2.0 ** -126 * (1 - 2 ** -30), 2.0 ** 127, 1 + 2 ** -24, 1 + 3 * 2 ** -25]))
+    x = np.concatenate(x)
+    rn = bmlib.bm_f32_convert(handle, x)
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    assert np.array_equal(rn.view(np.uint32), ref.view(np.uint32))
 
 
 CASES = [
