@@ -331,6 +331,9 @@ def roofline_from_profile(prof, N: int, nrhs: int, prec: int, iters: int, peaks:
     fp32 = 152 * 128 * 2 * sm / 1e12                       # FP32 FMA TFLOP/s, unit counts x clock
     tf32 = peaks["bf16_tflops"] * (1.1 / 2.25)             # measured bf16 x nominal tf32/bf16 ratio
     hbm = peaks["hbm_gbs"]
+    # where each peak comes from ("of measured" or "of fallback" for the peaks file's own figures)
+    peak_src = {fp32: "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock",
+                tf32: f"{src} bf16 x nominal TF32/bf16 ratio 1.1/2.25", hbm: src}
     lw = lu_work(N)
     work = {
         "resid_df_kernel (+ split-K reduction)": ("alu", 8.0 * 4 * N * N * nrhs, fp32, "TFLOP/s",
@@ -370,7 +373,7 @@ def roofline_from_profile(prof, N: int, nrhs: int, prec: int, iters: int, peaks:
         rows.append({"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": achieved / peak, "traffic": None, "launches": launches, "ms_total": ms,
                      "ms_per_launch": ms / launches, "work_per_step": amount, "work": how,
-                     "frac_note": src})
+                     "frac_note": peak_src.get(peak, src)})
     top_name = prof[0][0] if prof else None
     roof = next((r for r in rows if r["kernel"] == top_name), rows[0] if rows else None)
     return roof, {"kernels": [r for r in rows if r is not roof]}
