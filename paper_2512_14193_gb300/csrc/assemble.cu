@@ -902,13 +902,12 @@ cudaError_t launch_far_field(cudaStream_t s, const bm_ctx* c, const double2* X, 
     if (at > 65535) return cudaErrorInvalidConfiguration;  // more than 524280 angles in one call
     // the shared-memory limit is a per-device attribute of the kernel (idempotent, so a race between
     // host threads only sets it twice)
-    static bool attr[64] = {};
-    const bool known = c->device >= 0 && c->device < 64;
-    if (!known || !attr[c->device]) {
+    static DeviceFlags attr;
+    if (attr.pending()) {
         cudaError_t e = cudaFuncSetAttribute(far_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)((2 * FF_JT * FF_MT + 2 * FF_JT * (FF_CT + 1)) * sizeof(double2)));
         if (e != cudaSuccess) return e;
-        if (known) attr[c->device] = true;
+        attr.done();
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(S, at, ct);

@@ -2,6 +2,7 @@
 // launch helpers and the handle layout.  Not part of the public ABI (include/bm.h is).
 #pragma once
 
+#include <atomic>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -81,6 +82,30 @@ __device__ __forceinline__ float f32_rn(double x) {
     return __uint_as_float(f | (hi & 0x80000000u));
 }
 #endif
+
+// Kernel attributes set with cudaFuncSetAttribute belong to one device.  A launcher keeps one
+// DeviceFlags (static storage, so zero-initialised) per attribute it sets: pending() stays true
+// until done() for the calling thread's current device; for a device index past 63, or when the
+// current device cannot be read, it is always true and the attribute is set on every launch.
+struct DeviceFlags {
+    std::atomic<bool> f[64];
+    static int dev() {
+        int d = -1;
+        if (cudaGetDevice(&d) != cudaSuccess) {
+            cudaGetLastError();
+            d = -1;
+        }
+        return d;
+    }
+    bool pending() const {
+        const int d = dev();
+        return d < 0 || d >= 64 || !f[d].load(std::memory_order_acquire);
+    }
+    void done() {
+        const int d = dev();
+        if (d >= 0 && d < 64) f[d].store(true, std::memory_order_release);
+    }
+};
 
 template <class R> struct cplx_of;
 template <> struct cplx_of<double> { using type = double2; };

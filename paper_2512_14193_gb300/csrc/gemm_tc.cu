@@ -463,12 +463,12 @@ template <int OUT>
 cudaError_t launch_tc(cudaStream_t s, dim3 grid, const void* tAr, const void* tAi, const void* tBr, const void* tBi,
                       float* Cr, float* Ci, double2* C64, long ldc, long zstride, int m, int n, int kext, int S,
                       float alpha, float beta, int* d_err) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static DeviceFlags attr_set;
+    if (attr_set.pending()) {
         cudaError_t e =
             cudaFuncSetAttribute(cgemm_tc_kernel<OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.done();
     }
     cgemm_tc_kernel<OUT><<<grid, tc_threads<OUT>(), SMEM_BYTES, s>>>(
         *reinterpret_cast<const CUtensorMap*>(tAr), *reinterpret_cast<const CUtensorMap*>(tAi),
@@ -621,12 +621,12 @@ size_t tc_batch_entry_bytes() { return sizeof(TcBatchEntry); }
 cudaError_t gemm_tc_batch(cudaStream_t s, int B, const void* const* maps, float* const* Cr, float* const* Ci,
                           const long* ldc, int m, int n, int kext, float alpha, void* d_entries, int* d_err) {
     if (B < 1 || m <= 0 || n <= 0 || kext <= 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
+    static DeviceFlags attr;
+    if (attr.pending()) {
         cudaError_t e = cudaFuncSetAttribute(cgemm_tc_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr.done();
     }
     std::vector<TcBatchEntry> h(B);
     for (int b = 0; b < B; ++b) {

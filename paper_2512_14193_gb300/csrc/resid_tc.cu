@@ -640,18 +640,18 @@ void rt_plan_splits(int nprod, const long* m, const long* K, int n, int nd, int 
 cudaError_t gemm_rt(cudaStream_t s, const RtArgs* prods, int nprod, int n, double alpha, int* d_err, int* launched,
                     int nd) {
     if (nprod < 1 || nprod > 2 || n <= 0 || (nd != 7 && nd != 9)) return cudaSuccess;
-    static bool attr7 = false, attr9 = false;
-    if (nd == 7 && !attr7) {
+    static DeviceFlags attr7, attr9;
+    if (nd == 7 && attr7.pending()) {
         cudaError_t e = cudaFuncSetAttribute(resid_tc_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              RtCfg<7>::SMEM);
         if (e != cudaSuccess) return e;
-        attr7 = true;
+        attr7.done();
     }
-    if (nd == 9 && !attr9) {
+    if (nd == 9 && attr9.pending()) {
         cudaError_t e = cudaFuncSetAttribute(resid_tc_kernel<9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              RtCfg<9>::SMEM);
         if (e != cudaSuccess) return e;
-        attr9 = true;
+        attr9.done();
     }
     RtJob J{};
     J.nprod = nprod;
