@@ -192,6 +192,22 @@ def test_far_field_matches_oracle(bmlib, handle):
 
 
 @pytest.mark.gpu
+def test_far_field_many_columns_and_ragged_angles(bmlib, handle):
+    # more columns than one CTA takes (two column tiles of the node contraction), an angle count
+    # that is not a multiple of the 8-angle tile, and enough nodes for 8-CTA clusters of node slices
+    curve, N = W.ellipse(1.0, 0.6), 600
+    bmlib.bm_assemble(handle, curve.kind, curve.params4(), N, 3.0 - 0.1j, 4.5 - 0.15j, bmlib.BM_MIXED,
+                      bmlib.make_opts(bmlib.BM_FP64))
+    g, P = O.nodes(curve, N), O.default_params(3.0 - 0.1j, 4.5 - 0.15j)
+    X = np.asfortranarray(W.gaussian_full(3 * N, 130, 5))
+    th = np.linspace(0.1, 2 * np.pi + 0.1, 70, endpoint=False)
+    U = np.zeros((th.size, X.shape[1]), dtype=np.complex128, order="F")
+    bmlib.bm_far_field(handle, X, th, U)
+    Ur = O.far_field(g, P.k0, P.eps0, X[:N], X[N:2 * N], th)
+    assert np.abs(U - Ur).max() / np.abs(Ur).max() < 1e-12
+
+
+@pytest.mark.gpu
 def test_device_arrays_and_repeat_calls(bmlib, handle):
     torch = pytest.importorskip("torch")
     curve, N = W.circle(1.0), 128
