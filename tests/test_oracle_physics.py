@@ -2,6 +2,7 @@
 paper states, the circle eigen-relation of §5.3, energy (optical theorem) and reciprocity of the
 far field, and agreement between the mixed (Eq. dis_mixedBM) and ordinary (Eq. dis_BM) systems."""
 import numpy as np
+import pytest
 from scipy import special as sp
 
 import workloads as W
@@ -35,6 +36,25 @@ def test_mie_first_order_convergence_both_formulations():
     for e in (errs_m, errs_o):
         assert e[-1] < 1e-2
         assert 1.8 < e[0] / e[1] < 2.2 and 1.8 < e[1] / e[2] < 2.2
+
+
+@pytest.mark.parametrize("omega, eps1", [(1.0, 2.0), (2.0, 5.0), (10.0, 10.0)])
+def test_mie_convergence_at_the_lu_experiment_parameters(omega, eps1):
+    # §5.1, Table tb:lu_parameters: unit circle, eps0 = 1, the three (omega, eps1) pairs, the
+    # first two sizes N = 100 * 2^i (i = 1, 2) and the plane wave exp(i k0 x1).  Fig. convLU_error
+    # shows both formulations approaching the Bessel-series solution at O(N^-1): the Eq. norm error
+    # halves from N = 200 to 400 for every pair, and on the circle the two systems give the same
+    # [u; q] to rounding.
+    errs_m, errs_o = [], []
+    for N in (200, 400):
+        g, P, Xm, Xo, u, q = _solve_circle(N, omega, omega * np.sqrt(eps1))
+        assert abs(P.eps1 - eps1) < 1e-12 and P.eps0 == 1.0
+        errs_m.append(_relerr(Xm, N, u, q))
+        errs_o.append(_relerr(Xo, N, u, q))
+        assert np.linalg.norm(Xm[:2 * N] - Xo) / np.linalg.norm(Xo) < 1e-11
+    for e in (errs_m, errs_o):
+        assert e[1] < 0.05
+        assert 1.9 < e[0] / e[1] < 2.1, e
 
 
 def test_literal_ordinary_reading_does_not_converge():
