@@ -32,25 +32,6 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 
-def profiled_traffic(summary: str, n: int):
-    """DRAM bytes per launch from a committed ncu summary under profiles/, scaled from the captured
-    N to n by the summary's rule ((n/N)^2 for operator-bound kernels), or None when the kernel's
-    source has changed since the counters were taken (hash recorded in the summary)."""
-    import hashlib
-    import re
-    try:
-        txt = open(os.path.join(ROOT, "profiles", summary)).read()
-        m = re.search(r"traffic_bytes_per_launch_n(\d+): (\d+)", txt)
-        src = re.search(r"^source: (\S+)", txt, re.M).group(1)
-        h = re.search(r"source_sha256_12: ([0-9a-f]+)", txt).group(1)
-        cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:12]
-        if m is None or cur != h:
-            return None
-        n0, b0 = int(m.group(1)), int(m.group(2))
-        return b0 * (n / n0) ** 2
-    except (OSError, AttributeError):
-        return None
-
 METRIC = "factor+solve ms, solves/s: direct-indirect vs ordinary BM on 1 GB300 @relerr 1e-9"
 UNIT = "solves/s"
 PREC = {"fp64": 0, "tf32": 1, "3xtf32": 2}
