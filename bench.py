@@ -515,7 +515,12 @@ def run_ours(args, ws, rank, local):
     # ---- accuracy against the FP64 path, and the other precisions / residual modes of config 2 ----
     extras = {}
     if ws == 1 and not args.no_extras:
-        extras["fp64_path"] = fp64_compare(bm, local, stream, w, Bm, Xm, torch, ev)
+        extras["fp64_path"], X64 = fp64_compare(bm, local, stream, w, Bm, Xm, torch, ev)
+        try:
+            extras["refined_to_1e-12"] = tight_refinement(bm, local, stream, w, Bm, X64, torch, ev, prec)
+        except Exception as e:  # reported, not fatal: the headline line above is already measured
+            extras["refined_to_1e-12"] = {"error": str(e)}
+        del X64
         extras["resid_fp64_all"] = mode_timing(bm, local, stream, w, Bm, torch, ev, prec, bm.BM_RESID_FP64_ALL)
     asm_evals = float(w.N) * (w.N - 1)          # (H0, H1) pairs: N(N-1)/2 unordered pairs x 2 wavenumbers
     phases["assembly_mixed_hankel_evals_per_s"] = asm_evals / (phases["assemble_mixed_ms"] * 1e-3)
@@ -586,12 +591,35 @@ def fp64_compare(bm, device, stream, w, Bm, Xm, torch, ev):
         bm.bm_assemble(h, w.curve.kind, w.curve.params4(), w.N, w.k_out, w.k_in, bm.BM_MIXED, bm.make_opts(0))
         X64 = colmajor_dev(3 * w.N, w.nrhs, torch)
         f, s, info = _time_factor_solve(bm, h, Bm, X64, stream, torch, ev, steps=3)
-        d = (Xm - X64).abs().pow(2).sum(0).sqrt() / X64.abs().pow(2).sum(0).sqrt()
+        d = _relerr_cols(Xm, X64)
         return {"factor_ms": f, "solve_ms": s, "ms": f + s, "solves_per_s": w.nrhs / ((f + s) * 1e-3),
                 "backward_error": info.backward_error,
                 "relerr_cf32_vs_fp64_max_col": float(d.max().item()),
                 "relerr_cf32_vs_fp64_plane_wave": float(d[0].item()),
-                "note": "relerr = ||x_cf32 - x_fp64||_2 / ||x_fp64||_2 per right-hand side over all 3N unknowns"}
+                "note": "relerr = ||x_cf32 - x_fp64||_2 / ||x_fp64||_2 per right-hand side over all 3N unknowns"}, X64
+    finally:
+        bm.bm_destroy(h)
+
+
+def _relerr_cols(X, Xref):
+    return (X - Xref).abs().pow(2).sum(0).sqrt() / Xref.abs().pow(2).sum(0).sqrt()
+
+
+def tight_refinement(bm, device, stream, w, Bm, X64, torch, ev, prec, tol: float = 1e-12):
+    """The benchmark's factor + solve refined further, to backward error `tol` instead of 1e-9: what
+    a forward relative error below 1e-9 against the FP64 path costs (the FP64 path's own forward
+    error is about cond x 1e-16)."""
+    h = bm.bm_create(device, stream.cuda_stream)
+    try:
+        bm.bm_assemble(h, w.curve.kind, w.curve.params4(), w.N, w.k_out, w.k_in, bm.BM_MIXED,
+                       bm.make_opts(prec, refine_tol=tol))
+        X = colmajor_dev(3 * w.N, w.nrhs, torch)
+        f, s, info = _time_factor_solve(bm, h, Bm, X, stream, torch, ev, steps=3)
+        d = _relerr_cols(X, X64)
+        return {"refine_tol": tol, "factor_ms": f, "solve_ms": s, "ms": f + s,
+                "solves_per_s": w.nrhs / ((f + s) * 1e-3), "iterations": info.iterations,
+                "backward_error": info.backward_error,
+                "relerr_cf32_vs_fp64_max_col": float(d.max().item())}
     finally:
         bm.bm_destroy(h)
 
