@@ -219,6 +219,62 @@ def oracle_sample(w: W.Workload, ncols: int):
             "seconds_measured": t_schur + t_cols + t_solve, "seconds_total": total}
 
 
+def oracle_other_configs():
+    """The oracle on two more workloads, measured directly (no scaling within a run): the circle
+    R = 1, N = 256, k_out = 2, k_in = 3, one plane wave (the section 5.1 shape; mixed Schur path and
+    ordinary 2N dense LU, factor + solve), and one contour point of the contour batch (ellipse
+    1.0/0.6, N = 1024, k_out = z_0 on the circle of centre 5 and radius 0.5, k_in = 1.5 k_out, 16
+    Gaussian probe columns; assembly, Schur-path factor and Corollary solve).  Every one of the 32
+    points has the same size and cost, so the batch total is given as 32 x that point, marked as
+    such."""
+    import oracle as O
+    from oracle.dense import lu_factor, lu_solve, schur_complement
+    from oracle.ssm import contour
+
+    def corollary_solve(blocks, LU, piv, B):
+        M13, M23, M31, M32 = blocks
+        n = M13.shape[1]
+        b1, b2, b3 = B[:n], B[n:2 * n], B[2 * n:]
+        z3 = lu_solve(LU, piv, b3 - M31 @ b1 - M32 @ b2)
+        return np.concatenate([b1 - M13 @ z3, b2 - M23 @ z3, z3], 0)
+
+    out = {}
+    g = O.nodes(W.circle(1.0), 256)
+    P = O.default_params(2.0, 3.0)
+    blocks = O.mixed_blocks(g, P)
+    Bm = O.rhs_plane_wave(g, P, [0.0], W.MIXED)
+    Ao = O.ordinary_matrix(g, P)
+    Bo = O.rhs_plane_wave(g, P, [0.0], W.ORDINARY)
+    t0 = time.perf_counter()
+    LU, piv = lu_factor(schur_complement(blocks))
+    corollary_solve(blocks, LU, piv, Bm)
+    t1 = time.perf_counter()
+    LUo, pivo = lu_factor(Ao)
+    lu_solve(LUo, pivo, Bo)
+    t2 = time.perf_counter()
+    out["circle_n256"] = {"mixed_ms": (t1 - t0) * 1e3, "ordinary_ms": (t2 - t1) * 1e3,
+                          "what": "factor + solve of one plane wave, FP64, measured directly"}
+    z, _, _ = contour(5.0, 0.5, 32)
+    V = W.gaussian_full(3 * 1024, 16, 0)
+    t0 = time.perf_counter()
+    g = O.nodes(W.ellipse(1.0, 0.6), 1024)
+    P = O.default_params(z[0], 1.5 * z[0])
+    blocks = O.mixed_blocks(g, P)
+    t1 = time.perf_counter()
+    LU, piv = lu_factor(schur_complement(blocks))
+    t2 = time.perf_counter()
+    corollary_solve(blocks, LU, piv, V)
+    t3 = time.perf_counter()
+    pt = t3 - t0
+    out["ssm_point_n1024"] = {"assemble_ms": (t1 - t0) * 1e3, "factor_ms": (t2 - t1) * 1e3,
+                              "solve_ms": (t3 - t2) * 1e3, "point_ms": pt * 1e3,
+                              "batch_of_32_ms_extrapolated": 32 * pt * 1e3,
+                              "what": "one contour point measured directly; the 32-point figure is 32 x it"}
+    out["cores"] = os.cpu_count()
+    out["kind"] = "oracle"
+    return out
+
+
 def run_reference(args, ws, rank):
     """The reference arm: the CPU oracle's whole factor + solve of the benchmark workload, measured
     directly (no extrapolation), split into --steps pieces of about equal LU work; --warmup untimed
@@ -530,6 +586,10 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, 64 if args.quick else 128)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "seconds_measured")}
+        try:
+            extras["cpu_oracle_other_configs"] = oracle_other_configs()
+        except Exception as e:  # a reported baseline only: never fatal for the measured line
+            extras["cpu_oracle_other_configs"] = {"error": str(e)}
 
     bm.bm_destroy(hm)
     bm.bm_destroy(ho)
