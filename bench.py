@@ -571,13 +571,16 @@ def run_ours(args, ws, rank, local):
     # ---- accuracy against the FP64 path, and the other precisions / residual modes of config 2 ----
     extras = {}
     if ws == 1 and not args.no_extras:
-        extras["fp64_path"], X64 = fp64_compare(bm, local, stream, w, Bm, Xm, torch, ev)
-        try:
-            extras["refined_to_1e-12"] = tight_refinement(bm, local, stream, w, Bm, X64, torch, ev, prec)
-        except Exception as e:  # reported, not fatal: the headline line above is already measured
-            extras["refined_to_1e-12"] = {"error": str(e)}
-        del X64
-        extras["resid_fp64_all"] = mode_timing(bm, local, stream, w, Bm, torch, ev, prec, bm.BM_RESID_FP64_ALL)
+        got = _guarded(lambda: fp64_compare(bm, local, stream, w, Bm, Xm, torch, ev))
+        if isinstance(got, tuple):
+            extras["fp64_path"], X64 = got
+            extras["refined_to_1e-12"] = _guarded(
+                lambda: tight_refinement(bm, local, stream, w, Bm, X64, torch, ev, prec))
+            del X64
+        else:
+            extras["fp64_path"] = got
+        extras["resid_fp64_all"] = _guarded(
+            lambda: mode_timing(bm, local, stream, w, Bm, torch, ev, prec, bm.BM_RESID_FP64_ALL))
     asm_evals = float(w.N) * (w.N - 1)          # (H0, H1) pairs: N(N-1)/2 unordered pairs x 2 wavenumbers
     phases["assembly_mixed_hankel_evals_per_s"] = asm_evals / (phases["assemble_mixed_ms"] * 1e-3)
     phases["assembly_mixed_write_gbs"] = 4.0 * w.N * w.N * 16 / (phases["assemble_mixed_ms"] * 1e-3) / 1e9
@@ -586,19 +589,16 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, 64 if args.quick else 128)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "seconds_measured")}
-        try:
-            extras["cpu_oracle_other_configs"] = oracle_other_configs()
-        except Exception as e:  # a reported baseline only: never fatal for the measured line
-            extras["cpu_oracle_other_configs"] = {"error": str(e)}
+        extras["cpu_oracle_other_configs"] = _guarded(oracle_other_configs)
 
     bm.bm_destroy(hm)
     bm.bm_destroy(ho)
     if ws == 1 and not args.no_extras:
-        extras["circle_n256"] = circle_latency(bm, local, stream, torch, ev)
+        extras["circle_n256"] = _guarded(lambda: circle_latency(bm, local, stream, torch, ev))
         if not args.quick:
-            extras["kite_n16384"] = kite_large(bm, local, stream, torch, ev, args.config5_fp64)
-    ssm = None if args.no_ssm else ssm_measure(bm, local)
-    serve = None if args.no_serve else serve_measure(bm, local, n_req=args.serve_requests)
+            extras["kite_n16384"] = _guarded(lambda: kite_large(bm, local, stream, torch, ev, args.config5_fp64))
+    ssm = None if args.no_ssm else _guarded(lambda: ssm_measure(bm, local))
+    serve = None if args.no_serve else _guarded(lambda: serve_measure(bm, local, n_req=args.serve_requests))
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -619,6 +619,16 @@ def run_ours(args, ws, rank, local):
     if serve is not None:
         line["serving"] = serve
     print(json.dumps(line), flush=True)
+
+
+def _guarded(fn):
+    """Run one of the secondary measurements (other configurations, precisions, the serving stream,
+    the CPU baselines).  A failure there is reported in the line as {"error": ...} instead of
+    losing the headline measurement, which is already taken when these run."""
+    try:
+        return fn()
+    except Exception as e:
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def _time_factor_solve(bm, h, B, X, stream, torch, ev, steps: int, warmup: int = 1):

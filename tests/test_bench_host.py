@@ -80,3 +80,12 @@ def test_roofline_fractions_recompute_from_the_profile():
         assert r["frac"] == pytest.approx(ach / peak, rel=1e-12)
         assert r["ms_per_launch"] * r["launches"] == pytest.approx(r["ms_total"], rel=1e-12)
         assert r["frac_note"]
+
+
+def test_secondary_measurements_cannot_lose_the_headline():
+    assert bench._guarded(lambda: {"ms": 1.0}) == {"ms": 1.0}
+
+    def fails():
+        raise RuntimeError("bm_solve: BM_ENOTCONV")
+
+    assert bench._guarded(fails) == {"error": "RuntimeError: bm_solve: BM_ENOTCONV"}
