@@ -158,6 +158,8 @@ def _check(st: int, where: str, ok=(BM_OK,)):
 # rows of the assembled system per handle (3N mixed, 2N ordinary), for the shape checks below: the
 # library sees leading dimensions only, so an array with too few rows or columns must be caught here
 _nsys = {}
+# order of the blocks bm_copy_block copies per handle (N mixed, 2N ordinary)
+_blk = {}
 
 
 def _hkey(h) -> int:
@@ -216,6 +218,7 @@ def bm_create(device: int = 0, stream: int | None = None, budget_bytes: int = 0)
 
 def bm_destroy(h) -> None:
     _nsys.pop(_hkey(h), None)
+    _blk.pop(_hkey(h), None)
     _check(lib().bm_destroy(h), "bm_destroy")
 
 
@@ -257,6 +260,7 @@ def bm_assemble(h, kind: int, params, N: int, k_out, k_in, formulation: int = BM
     _check(lib().bm_assemble(h, C.byref(cv), int(N), _c64(k_out), _c64(k_in), int(formulation),
                              C.byref(opts) if opts is not None else None), "bm_assemble")
     _nsys[_hkey(h)] = (3 if int(formulation) == BM_MIXED else 2) * int(N)
+    _blk[_hkey(h)] = (1 if int(formulation) == BM_MIXED else 2) * int(N)
 
 
 def bm_factor(h) -> int:
@@ -436,6 +440,9 @@ def bm_server_destroy(s) -> None:
 
 def bm_copy_block(h, which: int, dst) -> None:
     p, ld, _n, dev, _k = _colmajor(dst, 0, writable=True)
+    # the library copies a whole block (N x N mixed, 2N x 2N ordinary) at leading dimension ld
+    n = _blk.get(_hkey(h), 0)
+    _need(_k.shape[0] >= n and _n >= n, f"dst must hold the {n} x {n} block")
     _check(lib().bm_copy_block(h, int(which), p, ld, dev), "bm_copy_block")
 
 

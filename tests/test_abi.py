@@ -185,3 +185,14 @@ def test_binding_rejects_outputs_too_small_for_the_write(bmlib):
         bmlib.bm_rhs_plane_wave(None, [0.0, 1.0, 2.0], B)          # a column per angle
     with pytest.raises(ValueError):
         bmlib.bm_solve(None, B, np.zeros((30, 3), dtype=np.complex128, order="F"))
+    # bm_copy_block writes the whole block: dst must have its rows and its columns
+    key = bmlib._hkey(None)
+    bmlib._blk[key] = 30
+    try:
+        for shape in ((30, 29), (29, 30), (30, 1)):
+            with pytest.raises(ValueError):
+                bmlib.bm_copy_block(None, 0, np.zeros(shape, dtype=np.complex128, order="F"))
+            with pytest.raises(ValueError):
+                bmlib.bm_copy_block(None, 0, torch.zeros(shape[::-1], dtype=torch.complex128).t())
+    finally:
+        bmlib._blk.pop(key, None)
