@@ -160,6 +160,8 @@ def _check(st: int, where: str, ok=(BM_OK,)):
 _nsys = {}
 # order of the blocks bm_copy_block copies per handle (N mixed, 2N ordinary)
 _blk = {}
+# host arrays of queued serving requests, by (server, ticket), until the request is collected
+_in_flight = {}
 
 
 def _hkey(h) -> int:
@@ -397,8 +399,8 @@ def bm_server_create(device: int = 0, slots: int = 4, budget_bytes: int = 0, opt
 
 
 def bm_server_submit(s, kind: int, params, N: int, k_out, k_in, formulation: int, B: np.ndarray, X: np.ndarray) -> int:
-    """Queue a solve; B and X are Fortran-ordered host complex128 arrays kept alive by the caller
-    until bm_server_wait returns for the ticket."""
+    """Queue a solve; B and X are Fortran-ordered host complex128 arrays.  The binding holds them
+    until bm_server_wait returns for the ticket (or bm_server_destroy); X holds the solution then."""
     pb, ldb, nb, devb, _kb = _colmajor(B, 0, writable=False)
     px, ldx, nx, devx, _kx = _colmajor(X, 0, writable=True)
     if devb or devx or nb != nx:
@@ -418,12 +420,16 @@ def bm_server_submit(s, kind: int, params, N: int, k_out, k_in, formulation: int
     r.B, r.ldb, r.X, r.ldx = pb, ldb, px, ldx
     t = C.c_ulonglong(0)
     _check(lib().bm_server_submit(s, C.byref(r), C.byref(t)), "bm_server_submit")
+    # the worker reads B and writes X until the request is collected: hold them until then
+    _in_flight[(_hkey(s), int(t.value))] = (B, X)
     return int(t.value)
 
 
 def bm_server_wait(s, ticket: int) -> bm_result:
     res = bm_result()
     st = lib().bm_server_wait(s, C.c_ulonglong(ticket), C.byref(res))
+    if st != BM_EINVAL:  # BM_EINVAL: unknown or already collected ticket, nothing was running
+        _in_flight.pop((_hkey(s), int(ticket)), None)
     _check(st, "bm_server_wait")
     return res
 
@@ -435,7 +441,11 @@ def bm_server_stats_get(s) -> bm_server_stats:
 
 
 def bm_server_destroy(s) -> None:
-    _check(lib().bm_server_destroy(s), "bm_server_destroy")
+    st = lib().bm_server_destroy(s)
+    key = _hkey(s)
+    for k in [k for k in _in_flight if k[0] == key]:  # every request has finished by now
+        del _in_flight[k]
+    _check(st, "bm_server_destroy")
 
 
 def bm_copy_block(h, which: int, dst) -> None:

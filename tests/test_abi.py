@@ -196,3 +196,46 @@ def test_binding_rejects_outputs_too_small_for_the_write(bmlib):
                 bmlib.bm_copy_block(None, 0, torch.zeros(shape[::-1], dtype=torch.complex128).t())
     finally:
         bmlib._blk.pop(key, None)
+
+
+def test_binding_holds_serving_arrays_until_collected(bmlib, monkeypatch):
+    # A queued request's worker reads B and writes X on another thread until the request is
+    # collected, so the binding keeps both arrays alive until bm_server_wait (or bm_server_destroy)
+    # returns, whatever the caller does with its own references.  A stand-in library records the
+    # calls; no GPU is needed.
+    import ctypes
+    import gc
+    import weakref
+
+    class FakeLib:
+        def bm_server_submit(self, s, req, ticket):
+            ctypes.cast(ticket, ctypes.POINTER(ctypes.c_ulonglong))[0] = 7
+            return bmlib.BM_OK
+
+        def bm_server_wait(self, s, ticket, res):
+            return bmlib.BM_OK
+
+        def bm_server_destroy(self, s):
+            return bmlib.BM_OK
+
+    monkeypatch.setattr(bmlib, "lib", lambda: FakeLib())
+    s = ctypes.c_void_p(12345)
+    B = np.ones((24, 2), dtype=np.complex128, order="F")
+    X = np.zeros((24, 2), dtype=np.complex128, order="F")
+    refs = [weakref.ref(B), weakref.ref(X)]
+    t = bmlib.bm_server_submit(s, 0, (1.0, 0, 0, 0), 8, 2.0, 3.0, bmlib.BM_MIXED, B, X)
+    assert t == 7
+    del B, X
+    gc.collect()
+    assert all(r() is not None for r in refs)          # still held while in flight
+    bmlib.bm_server_wait(s, t)
+    gc.collect()
+    assert all(r() is None for r in refs)              # released once collected
+    B = np.ones((24, 1), dtype=np.complex128, order="F")
+    r2 = weakref.ref(B)
+    bmlib.bm_server_submit(s, 0, (1.0, 0, 0, 0), 8, 2.0, 3.0, bmlib.BM_MIXED, B,
+                           np.zeros((24, 1), dtype=np.complex128, order="F"))
+    del B
+    bmlib.bm_server_destroy(s)                          # every request has finished by then
+    gc.collect()
+    assert r2() is None and not bmlib._in_flight
