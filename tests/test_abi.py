@@ -26,6 +26,19 @@ def test_library_exports_every_declared_symbol(bmlib):
     assert not missing, missing
 
 
+def test_every_exported_entry_point_is_declared(bmlib):
+    # the other direction: no bm_* symbol leaves the library without a declaration in bm.h
+    import shutil
+    import subprocess
+    if shutil.which("nm") is None:
+        pytest.skip("nm is not installed")
+    out = subprocess.run(["nm", "-D", "--defined-only", bmlib.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = sorted({ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("bm_")})
+    assert exported
+    assert sorted(set(exported) - set(_declared())) == []
+
+
 def test_strerror_names_every_status(bmlib):
     for s in range(9):
         assert bmlib.bm_strerror(s).startswith("BM_")
