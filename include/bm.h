@@ -375,7 +375,8 @@ bm_status bm_server_create(bm_server** out, int device, const bm_server_opts* op
 /* Queue a request; returns at once with its ticket.  BM_ENOMEM if it alone exceeds the budget,
  * BM_EINVAL for bad sizes or pointers. */
 bm_status bm_server_submit(bm_server* s, const bm_request* req, unsigned long long* ticket);
-/* Wait for a request and collect its result (each ticket once). */
+/* Wait for a request and collect its result (each ticket once: a call for a ticket that is already
+ * collected, or that another thread collects while this one waits, returns BM_EINVAL). */
 bm_status bm_server_wait(bm_server* s, unsigned long long ticket, bm_result* res);
 bm_status bm_server_stats_get(bm_server* s, bm_server_stats* st);
 /* Finish every queued request, stop the workers, release the handles. */

@@ -168,10 +168,17 @@ extern "C" bm_status bm_server_wait(bm_server* s, unsigned long long ticket, bm_
         bm_set_error("bm_server_wait: unknown or already collected ticket");
         return BM_EINVAL;
     }
-    s->cv_done.wait(lk, [&]() { return s->done.count(ticket) != 0; });
+    // a second waiter on the same ticket wakes when the first one collects it, instead of waiting
+    // for a result that will never come back
+    s->cv_done.wait(lk, [&]() { return s->done.count(ticket) != 0 || s->collected.count(ticket) != 0; });
+    if (s->done.count(ticket) == 0) {
+        bm_set_error("bm_server_wait: ticket collected by another waiter");
+        return BM_EINVAL;
+    }
     bm_result r = s->done[ticket];
     s->done.erase(ticket);
     s->collected[ticket] = true;
+    s->cv_done.notify_all();  // any other waiter on this ticket returns BM_EINVAL
     if (res) *res = r;
     if (r.status != BM_OK) bm_set_error("bm_server: request " + std::to_string(ticket) + " failed with status " +
                                         std::to_string(r.status));
